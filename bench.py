@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the generalized sparse contraction path on one B300.
+
+Workload (default ``rmat18``): R-MAT scale 18 (262,144 vertices, edge factor 16,
+a/b/c/d = 0.57/0.19/0.19/0.05, self-loops and duplicates removed), weights
+uniform (0,1] as (m+1)*2^-24.  One step is the whole path over that graph:
+(+,x) SpGEMM C = A.A in fp64, the same in fp32, and Bellman-Ford single-source
+shortest paths from vertex 0 over the (min,+) fp32 semiring.  The metric is
+semiring operations per second: the products of the two SpGEMMs (each one
+multiply and one add of the algebra) plus the edge relaxations of Bellman-Ford,
+divided by the step time.  ``er4096`` is the small (min,+) int32 SpGEMM case.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SpGEMM semiring-ops/s & MFBC GTEPS, learned+batched vs plain form on one B300"
+UNIT = "semiring-ops/s"
+L2_BYTES = 126 * 1024 * 1024
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def build_workload(name: str):
+    if name == "rmat18":
+        A = W.rmat(18, seed=0)
+        w = W.weights_unit01(A.nnz, seed=0)
+        g = W.weights_unit01(A.nnz, seed=1).astype(np.float32)
+        return {"A": A, "w64": w, "w32": w.astype(np.float32), "g32": g, "scale": 18}
+    if name == "er4096":
+        A = W.er_fixed_degree(4096, 8, seed=0)
+        return {"A": A, "wi32": W.weights_int(A.nnz, 1, 1000, seed=0), "scale": None}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def products(A: W.Csr, rows=None) -> int:
+    lens = np.diff(A.rowptr)
+    if rows is None:
+        return int(lens[A.col].sum())
+    return int(sum(lens[A.col[A.rowptr[i]:A.rowptr[i + 1]]].sum() for i in rows))
+
+
+def csr_bytes(n, nnz, s):
+    return 8 * (n + 1) + (4 + s) * nnz
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+
+def oracle_sample(wl, budget_rows_stride=16):
+    """Time the oracle on a bounded sample of the workload; returns (ops, seconds, desc)."""
+    import oracle as O
+    A = wl["A"]
+    if wl["scale"] is None:
+        a = A.with_val(wl["wi32"])
+        t = time.perf_counter()
+        O.spgemm(O.MP_I32, a, a)
+        dt = time.perf_counter() - t
+        return products(A), dt, "full er4096 (min,+) SpGEMM"
+    nz = np.nonzero(np.diff(A.rowptr) > 0)[0]
+    rows = nz[::budget_rows_stride]
+    ops = 0
+    t = time.perf_counter()
+    a64 = A.with_val(wl["w64"])
+    O.spgemm(O.PT_F64, a64, a64, rows=rows)
+    a32 = A.with_val(wl["w32"])
+    O.spgemm(O.PT_F32, a32, a32, rows=rows)
+    g = A.with_val(wl["g32"])
+    _, _, relax = O.bellman_ford(O.MP_F32, g, 0, with_relaxations=True)
+    dt = time.perf_counter() - t
+    ops = 2 * products(A, rows) + relax
+    desc = (f"every {budget_rows_stride}th non-empty row of both (+,x) SpGEMMs "
+            f"({rows.size} rows) plus full Bellman-Ford (full relaxation rounds)")
+    return ops, dt, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    wl = build_workload(args.workload)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample(wl)
+    tot_ops, tot_t = 0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        ops, dt, desc = oracle_sample(wl)
+        tot_ops += ops
+        tot_t += dt
+    v = tot_ops / tot_t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_stc(args):
+    import torch
+    import paper_1512_00066_b300 as stc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = build_workload(args.workload)
+    A = wl["A"]
+    H = stc.Handle()
+    H.set_timing(True)
+    dev = torch.device("cuda", local)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    if wl["scale"] is None:
+        ops_step = products(A)
+        dA = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["wi32"])
+
+        def step():
+            C = H.spgemm(stc.MIN_PLUS_I32, dA, dA)
+            t = H.phase_times()
+            return ops_step, {"numeric_ms": t[4], "nnzC": C.nnz, "s": 4}
+        dom_val_bytes = 4
+    else:
+        nprod = products(A)
+        d64 = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["w64"])
+        d32 = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["w32"])
+        dg = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["g32"])
+
+        def step():
+            C = H.spgemm(stc.PLUS_TIMES_F64, d64, d64)
+            t64 = H.phase_times()
+            nnz64 = C.nnz
+            del C
+            C = H.spgemm(stc.PLUS_TIMES_F32, d32, d32)
+            t32 = H.phase_times()
+            del C
+            dist_, rounds = H.bellman_ford(stc.MIN_PLUS_F32, dg, 0, persistent=True)
+            tbf = H.phase_times()
+            relax = H.last_relaxations
+            return 2 * nprod + relax, {"numeric_ms": t64[4], "phases64": t64, "phases32": t32,
+                                       "bf_ms": tbf, "nnzC": nnz64, "rounds": rounds,
+                                       "relax": relax, "s": 8}
+        dom_val_bytes = 8
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos, ops_total = [], 0
+    launches0 = H.kernel_launches()
+    barrier()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict L2 between timed steps (outside the timed span)
+            ev[k][0].record()
+            ops, info = step()
+            ev[k][1].record()
+            ops_total += ops
+            infos.append(info)
+        barrier()
+    launches = H.kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = world * ops_total / t_total
+
+    # roofline of the dominant kernel (numeric pass of the first SpGEMM)
+    n, nnzA = A.nrows, A.nnz
+    nnzC = infos[0]["nnzC"]
+    s = dom_val_bytes
+    W_cols = 8192 if s == 8 else 16384
+    nwin = max(1, -(-A.ncols // W_cols))
+    compulsory = (csr_bytes(n, nnzA, s) * 2 + (4 * A.nrows * (nwin + 1) if nwin > 1 else 0)
+                  + 8 * (n + 1) + (4 + s) * nnzC)
+    num_ms = statistics.mean(i["numeric_ms"] for i in infos)
+    hbm, peak_kind = peaks()
+    achieved = compulsory / (num_ms / 1e3) / 1e9
+    gather_model = csr_bytes(n, nnzA, s) + 8 * nnzA + (4 + s) * products(A) + csr_bytes(n, nnzC, s)
+
+    # end to end: host (pinned) inputs -> device -> the same step -> results back to host
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, stc, H, wl, dev)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32" if wl["scale"] else "int32",
+            "data": "synthetic",
+            "config": {"workload": ("rmat18: (+,x) SpGEMM A.A fp64 and fp32 + Bellman-Ford (min,+) fp32 "
+                                    "from vertex 0" if wl["scale"] else "er4096: (min,+) int32 SpGEMM A(x)A"),
+                       "n": A.nrows, "nnz": A.nnz, "nnzC": nnzC, "parallelism": "replicas" if world > 1 else "1gpu",
+                       "l2": "flushed between timed steps (write of 2x L2)",
+                       "ops_per_step": ops_total // args.steps},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "k_numeric (fp64 SpGEMM numeric pass)",
+                         "peak_source": peak_kind, "algorithmic_bytes": compulsory, "kernel_ms": num_ms,
+                         "gather_model_bytes": gather_model},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "phases_ms": infos[-1],
+        }
+        if e2e is not None:
+            out["e2e"] = e2e
+        if not args.no_cpu_baseline and world == 1:
+            import oracle as O
+            cores = len(os.sched_getaffinity(0))
+            O.set_threads(cores)
+            ops, dt, desc = oracle_sample(wl)
+            out["cpu_baseline"] = {"value": ops / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measure_e2e(args, stc, H, wl, dev):
+    """Same metric through the public API with host inputs and host results."""
+    import torch
+    A = wl["A"]
+    if wl["scale"] is None:
+        return None
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_ptr, h_col = pin(A.rowptr), pin(A.col)
+    h_w64, h_w32, h_g = pin(wl["w64"]), pin(wl["w32"]), pin(wl["g32"])
+    nprod = products(A)
+    h2d = 3 * (h_ptr.numel() * 8 + h_col.numel() * 4) + h_w64.numel() * 8 + h_w32.numel() * 4 + h_g.numel() * 4
+    out_bufs = {}
+
+    def host_buf(key, t):
+        b = out_bufs.get(key)
+        if b is None or b.numel() < t.numel() or b.dtype != t.dtype:
+            b = out_bufs[key] = torch.empty(t.numel(), dtype=t.dtype).pin_memory()
+        return b[: t.numel()]
+
+    def one():
+        d2h = 0
+        ptr_d = h_ptr.to(dev, non_blocking=True)
+        col_d = h_col.to(dev, non_blocking=True)
+        C = H.spgemm(stc.PLUS_TIMES_F64, stc.DeviceCsr(A.nrows, A.ncols, ptr_d, col_d, h_w64.to(dev, non_blocking=True)),
+                     stc.DeviceCsr(A.nrows, A.ncols, ptr_d, col_d, h_w64.to(dev, non_blocking=True)))
+        for key, t in (("p64", C.rowptr), ("c64", C.col), ("v64", C.val)):
+            host_buf(key, t).copy_(t, non_blocking=True)
+            d2h += t.numel() * t.element_size()
+        del C
+        ptr_d = h_ptr.to(dev, non_blocking=True)
+        col_d = h_col.to(dev, non_blocking=True)
+        v32 = h_w32.to(dev, non_blocking=True)
+        C = H.spgemm(stc.PLUS_TIMES_F32, stc.DeviceCsr(A.nrows, A.ncols, ptr_d, col_d, v32),
+                     stc.DeviceCsr(A.nrows, A.ncols, ptr_d, col_d, v32))
+        for key, t in (("p32", C.rowptr), ("c32", C.col), ("v32", C.val)):
+            host_buf(key, t).copy_(t, non_blocking=True)
+            d2h += t.numel() * t.element_size()
+        del C
+        ptr_d = h_ptr.to(dev, non_blocking=True)
+        col_d = h_col.to(dev, non_blocking=True)
+        G = stc.DeviceCsr(A.nrows, A.ncols, ptr_d, col_d, h_g.to(dev, non_blocking=True))
+        d, _ = H.bellman_ford(stc.MIN_PLUS_F32, G, 0)
+        host_buf("dist", d).copy_(d, non_blocking=True)
+        d2h += d.numel() * 4
+        torch.cuda.synchronize()
+        return 2 * nprod + H.last_relaxations, d2h
+
+    one()  # warm (allocates the pinned result buffers)
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ops = 0
+    d2h = 0
+    for _ in range(steps):
+        o, d2h = one()
+        ops += o
+    dt = time.perf_counter() - t
+    return {"value": ops / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="stc", choices=["stc", "reference"])
+    ap.add_argument("--workload", default="rmat18", choices=["rmat18", "er4096"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_stc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * stc.h -- generalized sparse contraction on one B300 (sm_103a), C ABI.
+ *
+ * The library computes contractions
+ *
+ *     C[i,j]  (+)=  f( A[i,k], B[k,j] )      summed over k,
+ *
+ * where (+) is the additive operator of an algebraic structure and f is the
+ * multiplicative operator or, more generally, a pairwise function whose operand
+ * types may differ from the output type.  This is the contraction of Solomonik &
+ * Hoefler, "Sparse Tensor Algebra as a Parallel Programming Model": algebraic
+ * structures with an additive operator, its identity and a multiplicative
+ * operator (Section 3.1, Table 1); contractions written as index expressions
+ * (Section 3.3.1, C["ij"] = A["ik"]*B["kj"]); pairwise functions of the form
+ * (type_C) <- (type_A, type_B) whose results are summed with the output's
+ * additive operator (Section 3.3.2).  Bellman-Ford is the repeated tropical
+ * matrix-vector product of Section 4.2.
+ *
+ * Three forms are provided: sparse x sparse (SpGEMM), sparse x dense block
+ * (SpMM) and sparse x dense vector (SpMV), plus Bellman-Ford single-source
+ * shortest paths built on the tropical product.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers (memory of the current CUDA device)
+ *    unless stated otherwise.  Inputs are owned by the caller and only read.
+ *  - CSR layout: rowptr int64[nrows+1] with rowptr[0] == 0, non-decreasing and
+ *    rowptr[nrows] == nnz; col int32[nnz], ascending and unique within each row,
+ *    each in [0, ncols); val: nnz elements of the algebra's operand type.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream).  Calls return once the work is enqueued, except where a result size
+ *    must be known on the host (documented per call): those synchronise `stream`
+ *    once.
+ *  - Errors never abort the process.  A bad argument is reported before any
+ *    work is enqueued; malformed CSR contents detected on the device are reported
+ *    by the call's single synchronisation (or by stc_check_device_status for
+ *    calls without one).  After an error no output is valid.
+ *  - Memory the library needs (scratch and results) is obtained from the
+ *    handle's allocator: callbacks passed to stc_create, or, when those are
+ *    NULL, stream-ordered cudaMallocAsync/cudaFreeAsync.
+ */
+#ifndef STC_H
+#define STC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define STC_API __attribute__((visibility("default")))
+#else
+#define STC_API
+#endif
+
+typedef struct CUstream_st* stc_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    STC_OK = 0,
+    STC_ERR_INVALID_ARG = 1, /* NULL pointer, negative size, unknown option        */
+    STC_ERR_SHAPE = 2,       /* inner dimensions disagree, rowptr not monotone,
+                                rowptr[0] != 0 or rowptr[nrows] != nnz            */
+    STC_ERR_UNSORTED = 3,    /* columns not strictly ascending within a row,
+                                or a column outside [0, ncols)                   */
+    STC_ERR_ALGEBRA = 4,     /* algebra not supported by this entry point         */
+    STC_ERR_OOM = 5,         /* the allocator returned NULL                       */
+    STC_ERR_CUDA = 6,        /* a CUDA runtime call failed                        */
+    STC_ERR_NEG_CYCLE = 7,   /* Bellman-Ford still relaxing after |V| rounds      */
+    STC_ERR_TIMEOUT = 8      /* a bounded device-side wait gave up                */
+} stc_status;
+
+/*
+ * Algebras (Section 3.1, Table 1; Section 3.3.2 for the mixed-type function).
+ * Operand element types are given as A / B / C.
+ *
+ *  STC_PLUS_TIMES_F32   (+,x) field. float / float / float.  Products and sums
+ *                       are formed in fp64 and rounded to fp32 once per output.
+ *  STC_PLUS_TIMES_F64   (+,x) field. double / double / double.
+ *  STC_MIN_PLUS_I32     tropical semiring, (+) = min, f = integer +, additive
+ *                       identity INT_MAX/2 = 1073741823 (Section 3.1: half of the
+ *                       largest int, so that adding two identities cannot
+ *                       overflow; no overflow check is made).  int32 throughout.
+ *  STC_MIN_PLUS_F32     tropical semiring in fp32, identity +inf, f = fp32 add
+ *                       (round to nearest even).  float throughout.
+ *  STC_OR_AND_BOOL      boolean semiring, (+) = or, f = and.  uint8 0/1.
+ *  STC_MULTPATH_I32_F64 (distance, multiplicity) monoid reached through the
+ *                       pairwise function f(a, (d, s)) = (a + d, s): A holds
+ *                       int32 edge lengths, B and C hold stc_dsig.
+ *                       (d1,s1) (+) (d2,s2) = the pair with the smaller d, or
+ *                       (d, s1 + s2) when d1 == d2.  Identity (INT_MAX/2, 0).
+ */
+typedef enum {
+    STC_PLUS_TIMES_F32 = 0,
+    STC_PLUS_TIMES_F64 = 1,
+    STC_MIN_PLUS_I32 = 2,
+    STC_MIN_PLUS_F32 = 3,
+    STC_OR_AND_BOOL = 4,
+    STC_MULTPATH_I32_F64 = 5
+} stc_algebra;
+
+#define STC_MIN_PLUS_I32_IDENTITY 1073741823
+
+/* Element of the (distance, multiplicity) monoid: 16 bytes, sigma 8-aligned. */
+typedef struct {
+    int32_t d;
+    int32_t pad;
+    double sigma;
+} stc_dsig;
+
+/* A CSR matrix.  rowptr/col/val are device pointers.  For outputs the library
+ * fills every field and allocates the three arrays with the handle's allocator;
+ * release them with stc_free (or the matching user free callback). */
+typedef struct {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    int64_t* rowptr;
+    int32_t* col;
+    void* val;
+} stc_csr;
+
+/* Allocator callbacks.  alloc returns device memory of at least `bytes` bytes
+ * usable in stream order on `stream`, or NULL on failure (reported as
+ * STC_ERR_OOM).  free receives a pointer from alloc and the stream after whose
+ * queued work the memory may be reused. */
+typedef void* (*stc_alloc_fn)(size_t bytes, void* ctx, stc_stream stream);
+typedef void (*stc_free_fn)(void* ptr, void* ctx, stc_stream stream);
+
+typedef struct stc_handle stc_handle;
+
+/* Options of the SpGEMM call.  Pass NULL for the defaults (all zero). */
+typedef struct {
+    int32_t skip_validation; /* 1: trust the CSR contents (no device checks)     */
+    int32_t window_cols;     /* 0: automatic; else the column-window width of the
+                                numeric accumulator (power of two, >= 1024)      */
+    int32_t reserved[6];     /* must be zero                                     */
+} stc_opts;
+
+/* Create a handle bound to the current CUDA device.  alloc/free may both be
+ * NULL (stream-ordered cudaMallocAsync/cudaFreeAsync) or both non-NULL.
+ * ctx is passed back to the callbacks unchanged. */
+STC_API stc_status stc_create(stc_handle** out, stc_alloc_fn alloc, stc_free_fn free_fn, void* ctx);
+
+/* Release the handle and its pinned host staging buffer.  Outputs returned by
+ * earlier calls stay valid and must still be released with the allocator. */
+STC_API void stc_destroy(stc_handle* h);
+
+/* Release memory returned in an output of this library (stream-ordered). */
+STC_API void stc_free(stc_handle* h, void* ptr, stc_stream stream);
+
+/* Text for a status code (static storage). */
+STC_API const char* stc_status_str(stc_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+STC_API int32_t stc_version(void);
+
+/*
+ * SpGEMM: C = A (x) B over `alg` (Section 3.3.1 contraction C["ij"] = A["ik"]*B["kj"]
+ * with the structure of Section 3.1 / function of Section 3.3.2).
+ *
+ * A is nrows x K, B is K x ncols (A->ncols must equal B->nrows).  On success C
+ * receives nrows = A->nrows, ncols = B->ncols, nnz, and newly allocated rowptr,
+ * col (ascending within each row) and val arrays.  The output structure is the
+ * symbolic union of the input structures: an entry is present when at least one
+ * product contributes to it, whatever its value (a (+,x) sum that cancels to 0
+ * or a boolean 0 stays present).
+ *
+ * The call runs the plain two-pass method: row analysis and binning, an exact
+ * symbolic pass that counts each output row, a scan into C->rowptr, then the
+ * numeric pass.  It synchronises `stream` once, after the symbolic pass, to
+ * learn nnz(C) and allocate C->col / C->val.
+ *
+ * opts may be NULL.  Errors: STC_ERR_INVALID_ARG, STC_ERR_SHAPE,
+ * STC_ERR_UNSORTED (device checks, skipped when opts->skip_validation),
+ * STC_ERR_ALGEBRA, STC_ERR_OOM, STC_ERR_CUDA.
+ */
+STC_API stc_status stc_contract_spgemm(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
+                               stc_csr* C, const stc_opts* opts, stc_stream stream);
+
+/*
+ * SpMM: Y = A (x) X, or Y = Y (+) (A (x) X) when accumulate != 0
+ * (Section 3.3.1 contraction with a dense operand).
+ *
+ * X is a dense A->ncols x ncol block, row-major with leading dimension ldx
+ * (elements, ldx >= ncol); Y is A->nrows x ncol with leading dimension ldy.
+ * Element types: A as in the algebra; X and Y the B/C type, except that
+ * STC_PLUS_TIMES_F32 reads and writes float.  Without accumulate, a row of A
+ * with no stored entry yields the additive identity.  SpMV is ncol == 1.
+ * Asynchronous; malformed CSR contents are reported through
+ * stc_check_device_status.
+ */
+STC_API stc_status stc_contract_spmm(stc_handle* h, stc_algebra alg, const stc_csr* A, const void* X,
+                             int64_t ldx, int32_t ncol, void* Y, int64_t ldy, int32_t accumulate,
+                             stc_stream stream);
+
+/* SpMV: y = A (x) x, or y (+)= A (x) x.  Same rules as stc_contract_spmm with ncol 1. */
+STC_API stc_status stc_contract_spmv(stc_handle* h, stc_algebra alg, const stc_csr* A, const void* x,
+                             void* y, int32_t accumulate, stc_stream stream);
+
+/* Read and clear the handle's device-side error flags raised by asynchronous
+ * calls (synchronises `stream`).  Returns STC_OK when none was raised. */
+STC_API stc_status stc_check_device_status(stc_handle* h, stc_stream stream);
+
+/*
+ * Bellman-Ford single-source shortest paths (Section 4.2): repeated tropical
+ * products P <- P (+) A (x) P with A_ii = 0 until no distance changes.
+ *
+ * G is the graph in OUT-EDGE CSR: row u lists the edges u -> v with lengths
+ * G->val (the transpose of the paper's A, whose A_ij is the length of edge
+ * j -> i).  alg is STC_MIN_PLUS_I32 (int32 lengths and distances, unreached =
+ * INT_MAX/2) or STC_MIN_PLUS_F32 (float, unreached = +inf).  A vertex at the
+ * additive identity relaxes nothing.  dist_out (device, G->nrows elements)
+ * receives the distances; *rounds_out (host, may be NULL) the number of rounds
+ * in which some distance decreased; *relaxations_out (host, may be NULL) the
+ * number of edge relaxations performed (the tropical products evaluated).
+ *
+ * Each round relaxes only the out-edges of vertices whose distance decreased in
+ * the previous round (frontier), which reaches the same fixed point as full
+ * relaxation: for fp32 the minimum over paths of the left-to-right rounded path
+ * sums, bit for bit.  `persistent` = 1 runs all rounds inside one cooperative
+ * launch with a device-side convergence test; 0 launches one kernel per round
+ * and reads the frontier size on the host each round.  Synchronises `stream`.
+ * Errors: STC_ERR_NEG_CYCLE when round |V| still lowers a distance (a negative
+ * cycle is reachable), STC_ERR_TIMEOUT when a bounded grid barrier gives up,
+ * plus the argument and CSR errors above.
+ */
+STC_API stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc_csr* G, int32_t source,
+                            void* dist_out, int32_t* rounds_out, int64_t* relaxations_out,
+                            int32_t persistent, stc_stream stream);
+
+/*
+ * Instrumentation (no counterpart in the paper, which reports only the share of
+ * time spent in local kernels).
+ *
+ * stc_set_timing: when enable != 0, later calls record CUDA events on their
+ * stream at phase boundaries.  stc_phase_times synchronises on the last event of
+ * the most recent timed call and writes up to max_phases durations in
+ * milliseconds; it returns the number of phases of that call (0 if none).
+ *   SpGEMM phases: 0 validation, 1 row analysis + binning + window table,
+ *                  2 symbolic, 3 scan, 4 numeric.
+ *   Bellman-Ford phases: 0 validation + initialisation, 1 all relaxation rounds.
+ * stc_kernel_launches: number of kernels this handle has launched so far.
+ */
+STC_API stc_status stc_set_timing(stc_handle* h, int32_t enable);
+STC_API int32_t stc_phase_times(stc_handle* h, float* ms_out, int32_t max_phases);
+STC_API int64_t stc_kernel_launches(const stc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STC_H */

@@ -59,7 +59,7 @@ def lib():
                                           _p, _i64, _p, _p, _p, _p]
             L.orc_spmm.argtypes = [ctypes.c_int, _i64, _p, _p, _p, _p, _i64, _i32, _p, _i64,
                                    ctypes.c_int]
-            L.orc_bellman_ford.argtypes = [ctypes.c_int, _i64, _p, _p, _p, _i32, _p]
+            L.orc_bellman_ford.argtypes = [ctypes.c_int, _i64, _p, _p, _p, _i32, _p, _p]
             L.orc_bellman_ford.restype = _i64
             L.orc_dijkstra.argtypes = [ctypes.c_int, _i64, _p, _p, _p, _i32, _p]
             L.orc_floyd_warshall_i32.argtypes = [_i64, _p]
@@ -154,12 +154,16 @@ def spmv(alg: int, A: Csr, x: np.ndarray, y0: np.ndarray = None) -> np.ndarray:
     return spmm(alg, A, x.reshape(-1), y0)
 
 
-def bellman_ford(alg: int, G: Csr, source: int):
-    """Returns (dist, rounds); rounds == -1 signals a reachable negative cycle."""
+def bellman_ford(alg: int, G: Csr, source: int, with_relaxations: bool = False):
+    """Returns (dist, rounds); rounds == -1 signals a reachable negative cycle.
+    With with_relaxations, returns (dist, rounds, number of edge relaxations)."""
     d = np.zeros(G.nrows, dtype=np.int32 if alg == MP_I32 else np.float32)
     w = _c(G.val, d.dtype)
+    relax = np.zeros(1, dtype=np.int64)
     r = lib().orc_bellman_ford(alg, G.nrows, _ptr(_c(G.rowptr, np.int64)), _ptr(_c(G.col, np.int32)),
-                               _ptr(w), int(source), _ptr(d))
+                               _ptr(w), int(source), _ptr(d), _ptr(relax))
+    if with_relaxations:
+        return d, int(r), int(relax[0])
     return d, int(r)
 
 

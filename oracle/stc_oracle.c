@@ -289,10 +289,11 @@ void orc_spmm(int alg, int64_t nrows, const int64_t* a_ptr, const int32_t* a_col
  * changed something (0 if the source has no out-edge), or -1 when round |V|
  * still changed something: a shortest path has at most |V|-1 edges, so a
  * change in round |V| means a reachable negative cycle.
- * alg: 2 -> int32 distances, 3 -> fp32 distances. */
+ * alg: 2 -> int32 distances, 3 -> fp32 distances.  *relax_out (may be NULL)
+ * receives the number of edge relaxations evaluated. */
 int64_t orc_bellman_ford(int alg, int64_t n, const int64_t* ptr, const int32_t* col,
-                         const void* w, int32_t source, void* dist_out) {
-    int64_t rounds = 0;
+                         const void* w, int32_t source, void* dist_out, int64_t* relax_out) {
+    int64_t rounds = 0, relax = 0;
     if (alg == ORC_MP_I32) {
         int32_t* P = (int32_t*)dist_out;
         int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
@@ -303,6 +304,7 @@ int64_t orc_bellman_ford(int alg, int64_t n, const int64_t* ptr, const int32_t* 
             int changed = 0;
             for (int64_t u = 0; u < n; ++u) {
                 if (Q[u] == ORC_TROP_I32_ID) continue;
+                relax += ptr[u + 1] - ptr[u];
                 for (int64_t p = ptr[u]; p < ptr[u + 1]; ++p) {
                     int32_t v = col[p];
                     int32_t x = Q[u] + ((const int32_t*)w)[p];
@@ -324,6 +326,7 @@ int64_t orc_bellman_ford(int alg, int64_t n, const int64_t* ptr, const int32_t* 
             int changed = 0;
             for (int64_t u = 0; u < n; ++u) {
                 if (Q[u] == INFINITY) continue;
+                relax += ptr[u + 1] - ptr[u];
                 for (int64_t p = ptr[u]; p < ptr[u + 1]; ++p) {
                     int32_t v = col[p];
                     float x = Q[u] + ((const float*)w)[p];
@@ -336,6 +339,7 @@ int64_t orc_bellman_ford(int alg, int64_t n, const int64_t* ptr, const int32_t* 
         }
         free(Q);
     }
+    if (relax_out) *relax_out = relax;
     return rounds;
 }
 

@@ -1,0 +1,313 @@
+"""Python binding of ``libstc.so``: generalized sparse contraction on one B300.
+
+Argument marshalling only.  Every step of every call runs in the CUDA library
+(``csrc/``); this module passes device pointers of torch tensors, the current
+CUDA stream and sizes through the C ABI declared in ``include/stc.h``, and maps
+status codes to exceptions.  There is no CPU fallback: if the library cannot be
+loaded, or no CUDA device is present, the calls raise.
+
+Memory the library asks for (scratch and results) comes from torch's caching
+allocator through the allocator callbacks of ``stc_create``, so results are
+ordinary torch tensors.
+
+Algebras (Solomonik & Hoefler, Section 3.1 Table 1 and Section 3.3.2):
+``PLUS_TIMES_F32``, ``PLUS_TIMES_F64``, ``MIN_PLUS_I32``, ``MIN_PLUS_F32``,
+``OR_AND_BOOL``, ``MULTPATH_I32_F64``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+PLUS_TIMES_F32, PLUS_TIMES_F64, MIN_PLUS_I32, MIN_PLUS_F32, OR_AND_BOOL, MULTPATH_I32_F64 = range(6)
+MIN_PLUS_I32_IDENTITY = 1073741823
+ALGEBRA_NAMES = {0: "plus_times_f32", 1: "plus_times_f64", 2: "min_plus_i32", 3: "min_plus_f32",
+                 4: "or_and_bool", 5: "multpath_i32_f64"}
+
+STATUS = {0: "STC_OK", 1: "STC_ERR_INVALID_ARG", 2: "STC_ERR_SHAPE", 3: "STC_ERR_UNSORTED",
+          4: "STC_ERR_ALGEBRA", 5: "STC_ERR_OOM", 6: "STC_ERR_CUDA", 7: "STC_ERR_NEG_CYCLE",
+          8: "STC_ERR_TIMEOUT"}
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libstc.so")
+
+# element types: (A, B/X, C/Y) as torch dtypes; multiplicity pairs are 16 raw bytes
+_DT = {
+    PLUS_TIMES_F32: (torch.float32, torch.float32, torch.float32),
+    PLUS_TIMES_F64: (torch.float64, torch.float64, torch.float64),
+    MIN_PLUS_I32: (torch.int32, torch.int32, torch.int32),
+    MIN_PLUS_F32: (torch.float32, torch.float32, torch.float32),
+    OR_AND_BOOL: (torch.uint8, torch.uint8, torch.uint8),
+    MULTPATH_I32_F64: (torch.int32, "dsig", "dsig"),
+}
+DSIG_BYTES = 16
+
+
+class StcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_status_text(status)})")
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("skip_validation", ctypes.c_int32), ("window_cols", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def lib():
+    """Load libstc.so (building it with nvcc first if it is absent)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                from . import build as _b
+                _b.build()
+            L = ctypes.CDLL(LIB_PATH)
+            p, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            L.stc_create.argtypes = [ctypes.POINTER(p), _ALLOC_FN, _FREE_FN, p]
+            L.stc_create.restype = ctypes.c_int
+            L.stc_destroy.argtypes = [p]
+            L.stc_free.argtypes = [p, p, p]
+            L.stc_status_str.argtypes = [ctypes.c_int]
+            L.stc_status_str.restype = ctypes.c_char_p
+            L.stc_version.restype = i32
+            L.stc_contract_spgemm.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr),
+                                              ctypes.POINTER(_Csr), ctypes.POINTER(_Opts), p]
+            L.stc_contract_spgemm.restype = ctypes.c_int
+            L.stc_contract_spmm.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), p, i64, i32, p, i64, i32, p]
+            L.stc_contract_spmm.restype = ctypes.c_int
+            L.stc_contract_spmv.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), p, p, i32, p]
+            L.stc_contract_spmv.restype = ctypes.c_int
+            L.stc_check_device_status.argtypes = [p, p]
+            L.stc_check_device_status.restype = ctypes.c_int
+            L.stc_bellman_ford.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), i32, p,
+                                           ctypes.POINTER(i32), ctypes.POINTER(i64), i32, p]
+            L.stc_bellman_ford.restype = ctypes.c_int
+            L.stc_set_timing.argtypes = [p, i32]
+            L.stc_set_timing.restype = ctypes.c_int
+            L.stc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_float), i32]
+            L.stc_phase_times.restype = i32
+            L.stc_kernel_launches.argtypes = [p]
+            L.stc_kernel_launches.restype = i64
+            _lib = L
+    return _lib
+
+
+def _status_text(s: int) -> str:
+    try:
+        return lib().stc_status_str(int(s)).decode()
+    except Exception:  # pragma: no cover - library not loadable
+        return "?"
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise StcError(st, where)
+
+
+def _stream_ptr(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+# ----------------------------------------------------------------- device CSR
+
+@dataclass
+class DeviceCsr:
+    """CSR matrix held in torch tensors on one CUDA device."""
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor  # int64[nrows+1]
+    col: torch.Tensor     # int32[nnz]
+    val: Optional[torch.Tensor]  # typed [nnz], or uint8 [nnz, 16] for multiplicity pairs
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def _c(self) -> _Csr:
+        return _Csr(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
+                    self.val.data_ptr() if self.val is not None and self.val.numel() else None)
+
+    @staticmethod
+    def from_host(nrows, ncols, rowptr, col, val=None, device="cuda") -> "DeviceCsr":
+        rp = torch.from_numpy(np.ascontiguousarray(rowptr, dtype=np.int64)).to(device)
+        cl = torch.from_numpy(np.ascontiguousarray(col, dtype=np.int32)).to(device)
+        v = None if val is None else values_to_device(val, device)
+        return DeviceCsr(int(nrows), int(ncols), rp, cl, v)
+
+    def to_host(self):
+        """(rowptr, col, val) as numpy arrays; multiplicity pairs as raw uint8 [nnz, 16]."""
+        return (self.rowptr.cpu().numpy(), self.col.cpu().numpy(),
+                None if self.val is None else self.val.cpu().numpy())
+
+
+def values_to_device(val: np.ndarray, device="cuda") -> torch.Tensor:
+    a = np.ascontiguousarray(val)
+    if a.dtype.names is not None or a.dtype.itemsize == DSIG_BYTES and a.dtype.kind == "V":
+        raw = a.view(np.uint8).reshape(-1, DSIG_BYTES)
+        return torch.from_numpy(raw.copy()).to(device)
+    return torch.from_numpy(a).to(device)
+
+
+# ----------------------------------------------------------------- handle
+
+class Handle:
+    """An stc_handle whose allocations come from torch's caching allocator."""
+
+    def __init__(self, device: Optional[int] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("stc: no CUDA device available (the library has no CPU path)")
+        self.device = torch.cuda.current_device() if device is None else device
+        self._live = {}
+        self._alloc_cb = _ALLOC_FN(self._alloc)
+        self._free_cb = _FREE_FN(self._free)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().stc_create(ctypes.byref(h), self._alloc_cb, self._free_cb, None), "stc_create")
+        self._h = h
+
+    def _alloc(self, nbytes, ctx, stream):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=f"cuda:{self.device}")
+        except Exception:
+            return None
+        ptr = t.data_ptr()
+        self._live[ptr] = t
+        return ptr
+
+    def _free(self, ptr, ctx, stream):
+        self._live.pop(ptr, None)
+
+    def _take(self, ptr: int) -> torch.Tensor:
+        return self._live.pop(ptr)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().stc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- calls
+
+    def spgemm(self, alg: int, A: DeviceCsr, B: DeviceCsr, skip_validation: bool = False,
+               window_cols: int = 0, stream=None) -> DeviceCsr:
+        """C = A (x) B (plain two-pass SpGEMM); synchronises the stream once."""
+        C = _Csr()
+        opts = _Opts(1 if skip_validation else 0, int(window_cols))
+        a, b = A._c(), B._c()
+        st = lib().stc_contract_spgemm(self._h, alg, ctypes.byref(a), ctypes.byref(b), ctypes.byref(C),
+                                       ctypes.byref(opts), _stream_ptr(stream))
+        _check(st, "stc_contract_spgemm")
+        nnz = int(C.nnz)
+        rowptr = self._take(C.rowptr).view(torch.int64)[: C.nrows + 1]
+        col = self._take(C.col).view(torch.int32)[:nnz]
+        raw = self._take(C.val)
+        ct = _DT[alg][2]
+        if ct == "dsig":
+            val = raw[: nnz * DSIG_BYTES].view(nnz, DSIG_BYTES)
+        else:
+            val = raw.view(ct)[:nnz]
+        return DeviceCsr(int(C.nrows), int(C.ncols), rowptr, col, val)
+
+    def spmm(self, alg: int, A: DeviceCsr, X: torch.Tensor, Y: Optional[torch.Tensor] = None,
+             accumulate: bool = False, stream=None) -> torch.Tensor:
+        """Y = A (x) X, or Y (+)= A (x) X; X is [A.ncols, ncol] (or a vector)."""
+        vec = X.dim() == 1 or (_DT[alg][1] == "dsig" and X.dim() == 2 and X.shape[-1] == DSIG_BYTES
+                               and X.dtype == torch.uint8)
+        if _DT[alg][1] == "dsig":
+            ncol = 1 if vec else X.shape[1]
+            ldx = ncol
+        else:
+            ncol = 1 if X.dim() == 1 else X.shape[1]
+            ldx = ncol if X.dim() == 1 else X.stride(0)
+        if Y is None:
+            if accumulate:
+                raise ValueError("accumulate needs Y")
+            if _DT[alg][2] == "dsig":
+                Y = torch.empty((A.nrows, DSIG_BYTES) if vec else (A.nrows, ncol, DSIG_BYTES),
+                                dtype=torch.uint8, device=X.device)
+            else:
+                Y = torch.empty((A.nrows,) if vec else (A.nrows, ncol), dtype=_DT[alg][2], device=X.device)
+        ldy = ncol if (vec or _DT[alg][2] == "dsig") else Y.stride(0)
+        a = A._c()
+        st = lib().stc_contract_spmm(self._h, alg, ctypes.byref(a), X.data_ptr(), ldx, ncol, Y.data_ptr(),
+                                     ldy, 1 if accumulate else 0, _stream_ptr(stream))
+        _check(st, "stc_contract_spmm")
+        return Y
+
+    def spmv(self, alg: int, A: DeviceCsr, x: torch.Tensor, y: Optional[torch.Tensor] = None,
+             accumulate: bool = False, stream=None) -> torch.Tensor:
+        return self.spmm(alg, A, x, y, accumulate, stream)
+
+    def check_device_status(self, stream=None):
+        _check(lib().stc_check_device_status(self._h, _stream_ptr(stream)), "stc_check_device_status")
+
+    def bellman_ford(self, alg: int, G: DeviceCsr, source: int, persistent: bool = True,
+                     dist: Optional[torch.Tensor] = None, stream=None):
+        """Shortest distances from `source` over out-edge CSR G; returns (dist, rounds)."""
+        if dist is None:
+            dist = torch.empty(G.nrows, dtype=torch.int32 if alg == MIN_PLUS_I32 else torch.float32,
+                               device=G.col.device)
+        rounds = ctypes.c_int32(0)
+        relax = ctypes.c_int64(0)
+        g = G._c()
+        st = lib().stc_bellman_ford(self._h, alg, ctypes.byref(g), int(source), dist.data_ptr(),
+                                    ctypes.byref(rounds), ctypes.byref(relax), 1 if persistent else 0,
+                                    _stream_ptr(stream))
+        _check(st, "stc_bellman_ford")
+        self.last_relaxations = int(relax.value)
+        return dist, int(rounds.value)
+
+    # -------------------------------------------------------------- instrumentation
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().stc_set_timing(self._h, 1 if enable else 0), "stc_set_timing")
+
+    def phase_times(self):
+        """Durations (ms) of the phases of the last timed call (synchronises)."""
+        buf = (ctypes.c_float * 8)()
+        n = lib().stc_phase_times(self._h, buf, 8)
+        return [float(buf[i]) for i in range(n)]
+
+    def kernel_launches(self) -> int:
+        return int(lib().stc_kernel_launches(self._h))
+
+
+_default = {}
+
+
+def handle() -> Handle:
+    """Process-wide handle for the current device."""
+    dev = torch.cuda.current_device()
+    h = _default.get(dev)
+    if h is None:
+        h = _default[dev] = Handle(dev)
+    return h
+
+
+def version() -> int:
+    return int(lib().stc_version())

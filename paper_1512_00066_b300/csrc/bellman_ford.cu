@@ -1,0 +1,268 @@
+// Bellman-Ford single-source shortest paths (Section 4.2): repeated tropical
+// matrix-vector products P <- P (+) A (x) P, with A_ii = 0 keeping P's own
+// entries, until no distance changes; a change in round |V| means a reachable
+// negative cycle.
+//
+// The product is applied to the frontier only: in each round the out-edges of
+// the vertices whose distance decreased in the previous round are relaxed with
+// an atomic minimum on the distance vector, and a vertex whose distance
+// decreased joins the next frontier once (a per-vertex round stamp).  Vertices
+// at the additive identity never relax, so the fixed point is the one of full
+// relaxation; for fp32 it is the minimum over paths of the rounded left-to-right
+// path sums, because a rounded add is monotone in each operand.
+//
+// Two drivers: a host loop with one launch per round that reads the frontier
+// size back each round, and one cooperative launch that runs every round with a
+// grid barrier (bounded spin) and tests convergence on the device.
+#include <cooperative_groups.h>
+
+#include "stc_internal.cuh"
+
+namespace {
+
+constexpr int BF_NT = 512;
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 22;  // iterations of ~0.5 us each (~2 s)
+
+template <int ALG> struct BfT;
+template <> struct BfT<ALG_MP_I32> {
+    using W = int; using D = int;  // stored distance representation
+    static __device__ __forceinline__ D init() { return STC_MIN_PLUS_I32_IDENTITY; }
+    static __device__ __forceinline__ D zero() { return 0; }
+    static __device__ __forceinline__ D relax(D du, W w) { return du + w; }
+    static __device__ __forceinline__ D amin(D* p, D v) { return atomicMin(p, v); }
+    static __device__ __forceinline__ bool less(D a, D b) { return a < b; }
+};
+template <> struct BfT<ALG_MP_F32> {
+    using W = float; using D = unsigned;  // order-preserving key of the fp32 distance
+    static __device__ __forceinline__ D init() { return f32_to_ordered(__int_as_float(0x7f800000)); }
+    static __device__ __forceinline__ D zero() { return f32_to_ordered(0.0f); }
+    static __device__ __forceinline__ D relax(D du, W w) {
+        return f32_to_ordered(__fadd_rn(ordered_to_f32(du), w));
+    }
+    static __device__ __forceinline__ D amin(D* p, D v) { return atomicMin(p, v); }
+    static __device__ __forceinline__ bool less(D a, D b) { return a < b; }
+};
+
+struct BfArgs {
+    int64_t n, nnz;
+    const int64_t* __restrict__ ptr;
+    const int32_t* __restrict__ col;
+    const void* __restrict__ w;
+    int32_t* frontier[2];
+    int* stamp;
+    int* cnt;  // three rotating frontier counters
+    unsigned long long* relax;  // edge relaxations performed
+};
+
+template <int ALG>
+__global__ void k_bf_init(BfArgs a, typename BfT<ALG>::D* dist, int32_t source) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < a.n;
+         v += int64_t(gridDim.x) * blockDim.x) {
+        dist[v] = v == source ? BfT<ALG>::zero() : BfT<ALG>::init();
+        a.stamp[v] = -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.frontier[0][0] = source;
+        a.cnt[0] = 1;
+        a.cnt[1] = 0;
+        a.cnt[2] = 0;
+    }
+}
+
+// Relax the out-edges of frontier entries [0, cnt_cur); one warp per frontier
+// vertex, lanes over its edges.  Warps are numbered across the grid.
+template <int ALG>
+__device__ __forceinline__ void relax_round(const BfArgs& a, typename BfT<ALG>::D* dist, int r,
+                                            const int32_t* __restrict__ cur, int ncur,
+                                            int32_t* __restrict__ next, int* cnt_next) {
+    using T = BfT<ALG>;
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const auto* W = static_cast<const typename T::W*>(a.w);
+    unsigned long long nrelax = 0;
+    for (int64_t e = warp; e < ncur; e += nwarps) {
+        int32_t u = cur[e];
+        int64_t lo, hi;
+        row_range(a.ptr, u, a.nnz, lo, hi);
+        nrelax += (unsigned long long)(hi - lo);
+        typename T::D du = *(volatile typename T::D*)&dist[u];
+        for (int64_t p = lo + lane; p < hi; p += 32) {
+            int32_t v = a.col[p];
+            if ((uint64_t)v >= (uint64_t)a.n) continue;
+            typename T::D cand = T::relax(du, W[p]);
+            typename T::D old = T::amin(&dist[v], cand);
+            if (T::less(cand, old)) {
+                if (atomicExch(&a.stamp[v], r) != r) next[atomicAdd(cnt_next, 1)] = v;
+            }
+        }
+    }
+    if (lane == 0 && nrelax) atomicAdd(a.relax, nrelax);
+}
+
+template <int ALG>
+__global__ void __launch_bounds__(BF_NT) k_bf_round(BfArgs a, typename BfT<ALG>::D* dist, int r) {
+    const int ncur = a.cnt[r % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt[(r + 2) % 3] = 0;  // counter of round r+2's frontier
+    relax_round<ALG>(a, dist, r, a.frontier[r & 1], ncur, a.frontier[(r + 1) & 1], &a.cnt[(r + 1) % 3]);
+}
+
+// Grid-wide barrier with a bounded spin.  Returns false (and raises
+// STC_FLAG_TIMEOUT) if the other blocks did not arrive in time.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* flags, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned g0 = *(volatile unsigned*)gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == gridDim.x - 1) {
+            *(volatile unsigned*)count = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*(volatile unsigned*)gen == g0) {
+                if (++spins > BARRIER_SPIN_LIMIT) {
+                    ok = 0;
+                    atomicOr(flags, STC_FLAG_TIMEOUT);
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <int ALG>
+__global__ void __launch_bounds__(BF_NT) k_bf_persistent(BfArgs a, typename BfT<ALG>::D* dist,
+                                                         unsigned* bar, int* flags, int* rounds_out) {
+    __shared__ int s_ok;
+    int r = 0;
+    int changed_rounds = 0;
+    for (;;) {
+        const int ncur = *(volatile int*)&a.cnt[r % 3];
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt[(r + 2) % 3] = 0;
+        relax_round<ALG>(a, dist, r, a.frontier[r & 1], ncur, a.frontier[(r + 1) & 1],
+                         &a.cnt[(r + 1) % 3]);
+        if (!grid_barrier(&bar[0], &bar[1], flags, &s_ok)) return;
+        const int nnext = *(volatile int*)&a.cnt[(r + 1) % 3];
+        if (nnext == 0) break;
+        ++changed_rounds;
+        ++r;
+        if (int64_t(changed_rounds) >= a.n) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, STC_FLAG_NEG_CYCLE);
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rounds_out = changed_rounds;
+}
+
+template <int ALG>
+__global__ void k_bf_finish(int64_t n, const typename BfT<ALG>::D* key, void* out) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+         v += int64_t(gridDim.x) * blockDim.x) {
+        if (ALG == ALG_MP_F32)
+            static_cast<float*>(out)[v] = ordered_to_f32(static_cast<unsigned>(key[v]));
+    }
+}
+
+template <int ALG>
+stc_status run_bf(stc_handle* h, const stc_csr* G, int32_t source, void* dist_out, int32_t* rounds_out,
+                  int64_t* relax_out, int persistent, stc_stream s) {
+    using D = typename BfT<ALG>::D;
+    StcScratch sc(h, s);
+    const int64_t n = G->nrows;
+    BfArgs a;
+    a.n = n;
+    a.nnz = G->nnz;
+    a.ptr = G->rowptr;
+    a.col = G->col;
+    a.w = G->val;
+    a.frontier[0] = sc.get<int32_t>(size_t(n));
+    a.frontier[1] = sc.get<int32_t>(size_t(n));
+    a.stamp = sc.get<int>(size_t(n));
+    int* ints = sc.get<int>(16);  // [0..2] counters, [4..5] barrier, [6] rounds, [8..9] relaxations
+    D* dist = ALG == ALG_MP_I32 ? reinterpret_cast<D*>(dist_out) : sc.get<D>(size_t(n));
+    if (sc.failed) return STC_ERR_OOM;
+    a.cnt = ints;
+    a.relax = reinterpret_cast<unsigned long long*>(ints + 8);
+    stc_mark(h, s, 0);
+    STC_CUDA_TRY(cudaMemsetAsync(ints, 0, 16 * sizeof(int), s));
+    stc_status st = stc_validate_csr_async(h, G, s);
+    if (st != STC_OK) return st;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > int64_t(h->num_sms) * 8) blocks = int64_t(h->num_sms) * 8;
+    k_bf_init<ALG><<<unsigned(blocks), 256, 0, s>>>(a, dist, source);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    stc_mark(h, s, 1);
+
+    int rounds = 0;
+    if (persistent) {
+        int per_sm = 0;
+        STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bf_persistent<ALG>, BF_NT, 0));
+        if (per_sm < 1) return STC_ERR_CUDA;
+        int grid = per_sm * h->num_sms;
+        unsigned* bar = reinterpret_cast<unsigned*>(ints + 4);
+        int* flags = h->d_flags;
+        int* d_rounds = ints + 6;
+        void* args[] = {&a, &dist, &bar, &flags, &d_rounds};
+        STC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bf_persistent<ALG>, dim3(grid), dim3(BF_NT),
+                                                 args, 0, s));
+        stc_count(h);
+        stc_mark(h, s, 2);
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[0], d_rounds, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[2], a.relax, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[1], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaStreamSynchronize(s));
+        rounds = reinterpret_cast<int*>(&h->h_stage[0])[0];
+    } else {
+        // plain form: one launch per round, frontier size read back each round
+        int grid = h->num_sms * 4;
+        int* h_cnt = reinterpret_cast<int*>(&h->h_stage[0]);
+        for (int r = 0;; ++r) {
+            k_bf_round<ALG><<<grid, BF_NT, 0, s>>>(a, dist, r);
+            STC_LAUNCH_CHECK();
+            stc_count(h);
+            STC_CUDA_TRY(cudaMemcpyAsync(h_cnt, &a.cnt[(r + 1) % 3], sizeof(int), cudaMemcpyDeviceToHost, s));
+            STC_CUDA_TRY(cudaStreamSynchronize(s));
+            if (*h_cnt == 0) break;
+            ++rounds;
+            if (int64_t(rounds) >= n) {
+                int f = STC_FLAG_NEG_CYCLE;
+                STC_CUDA_TRY(cudaMemcpyAsync(h->d_flags, &f, sizeof(int), cudaMemcpyHostToDevice, s));
+                break;
+            }
+        }
+        stc_mark(h, s, 2);
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[1], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[2], a.relax, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (ALG == ALG_MP_F32) {
+        k_bf_finish<ALG><<<unsigned(blocks), 256, 0, s>>>(n, dist, dist_out);
+        STC_LAUNCH_CHECK();
+        stc_count(h);
+    }
+    if (rounds_out) *rounds_out = rounds;
+    if (relax_out) *relax_out = h->h_stage[2];
+    int flags = reinterpret_cast<int*>(&h->h_stage[1])[0];
+    if (flags) {
+        STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+        return stc_flags_to_status(flags);
+    }
+    return STC_OK;
+}
+
+}  // namespace
+
+stc_status stc_bellman_ford_impl(stc_handle* h, int alg, const stc_csr* G, int32_t source, void* dist,
+                                 int32_t* rounds, int64_t* relax, int32_t persistent, stc_stream s) {
+    if (alg == ALG_MP_I32) return run_bf<ALG_MP_I32>(h, G, source, dist, rounds, relax, persistent, s);
+    return run_bf<ALG_MP_F32>(h, G, source, dist, rounds, relax, persistent, s);
+}

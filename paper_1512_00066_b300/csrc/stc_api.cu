@@ -1,0 +1,341 @@
+// C-ABI entry points, handle, allocator plumbing, CSR validation and the
+// device-wide scan used to turn per-row counts into row pointers.
+#include <cstdio>
+#include <cstring>
+
+#include "stc_internal.cuh"
+
+// ----------------------------------------------------------------- statuses
+
+static const char* k_status_text[] = {
+    "ok",
+    "invalid argument",
+    "shape mismatch or malformed row pointers",
+    "columns not strictly ascending or out of range",
+    "algebra not supported by this entry point",
+    "allocation failed",
+    "CUDA runtime error",
+    "negative cycle reachable from the source",
+    "bounded device-side wait timed out",
+};
+
+extern "C" const char* stc_status_str(stc_status s) {
+    int i = static_cast<int>(s);
+    if (i < 0 || i >= static_cast<int>(sizeof(k_status_text) / sizeof(k_status_text[0])))
+        return "unknown status";
+    return k_status_text[i];
+}
+
+extern "C" int32_t stc_version(void) { return 100; }
+
+stc_status stc_flags_to_status(int f) {
+    if (f & STC_FLAG_SHAPE) return STC_ERR_SHAPE;
+    if (f & STC_FLAG_UNSORTED) return STC_ERR_UNSORTED;
+    if (f & STC_FLAG_TIMEOUT) return STC_ERR_TIMEOUT;
+    if (f & STC_FLAG_NEG_CYCLE) return STC_ERR_NEG_CYCLE;
+    if (f & STC_FLAG_INTERNAL) return STC_ERR_CUDA;
+    return STC_OK;
+}
+
+size_t stc_val_bytes(int alg, char operand) {
+    switch (alg) {
+    case ALG_PT_F32: return 4;
+    case ALG_PT_F64: return 8;
+    case ALG_MP_I32: return 4;
+    case ALG_MP_F32: return 4;
+    case ALG_BOOL: return 1;
+    case ALG_MULTPATH: return operand == 'A' ? 4 : 16;
+    default: return 0;
+    }
+}
+
+// ----------------------------------------------------------------- handle
+
+extern "C" stc_status stc_create(stc_handle** out, stc_alloc_fn alloc, stc_free_fn free_fn,
+                                 void* ctx) {
+    if (!out) return STC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return STC_ERR_INVALID_ARG;
+    stc_handle* h = new stc_handle();
+    h->alloc = alloc;
+    h->free_fn = free_fn;
+    h->ctx = ctx;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) !=
+            cudaSuccess ||
+        cudaMalloc(&h->d_flags, 64) != cudaSuccess ||
+        cudaMemset(h->d_flags, 0, 64) != cudaSuccess ||
+        cudaMallocHost(&h->h_stage, 64 * sizeof(int64_t)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (h->d_flags) cudaFree(h->d_flags);
+        delete h;
+        return STC_ERR_CUDA;
+    }
+    *out = h;
+    return STC_OK;
+}
+
+extern "C" void stc_destroy(stc_handle* h) {
+    if (!h) return;
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->d_flags) cudaFree(h->d_flags);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    delete h;
+}
+
+void* stc_alloc_bytes(stc_handle* h, size_t bytes, stc_stream s) {
+    if (bytes == 0) bytes = 16;
+    if (h->alloc) return h->alloc(bytes, h->ctx, s);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void stc_free_bytes(stc_handle* h, void* p, stc_stream s) {
+    if (!p) return;
+    if (h->free_fn) h->free_fn(p, h->ctx, s);
+    else (void)cudaFreeAsync(p, s);
+}
+
+extern "C" void stc_free(stc_handle* h, void* ptr, stc_stream stream) {
+    if (h) stc_free_bytes(h, ptr, stream);
+}
+
+extern "C" stc_status stc_check_device_status(stc_handle* h, stc_stream s) {
+    if (!h) return STC_ERR_INVALID_ARG;
+    int f = 0;
+    STC_CUDA_TRY(cudaMemcpyAsync(&f, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+    return stc_flags_to_status(f);
+}
+
+// ----------------------------------------------------------------- instrumentation
+
+void stc_mark(stc_handle* h, stc_stream s, int idx) {
+    if (!h->timing || idx < 0 || idx >= 9) return;
+    if (!h->ev[idx] && cudaEventCreate(&h->ev[idx]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    if (cudaEventRecord(h->ev[idx], s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    h->nphases = idx;
+}
+
+extern "C" stc_status stc_set_timing(stc_handle* h, int32_t enable) {
+    if (!h) return STC_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    h->nphases = 0;
+    return STC_OK;
+}
+
+extern "C" int32_t stc_phase_times(stc_handle* h, float* ms_out, int32_t max_phases) {
+    if (!h || !h->timing || h->nphases <= 0) return 0;
+    int n = h->nphases;
+    if (cudaEventSynchronize(h->ev[n]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    for (int i = 0; i < n && i < max_phases; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ms = -1.f;
+        }
+        if (ms_out) ms_out[i] = ms;
+    }
+    return n;
+}
+
+extern "C" int64_t stc_kernel_launches(const stc_handle* h) { return h ? h->launches : 0; }
+
+// ----------------------------------------------------------------- CSR validation
+
+stc_status stc_check_csr_host(const stc_csr* m) {
+    if (!m) return STC_ERR_INVALID_ARG;
+    if (m->nrows < 0 || m->ncols < 0 || m->nnz < 0) return STC_ERR_INVALID_ARG;
+    if (m->nrows >= INT32_MAX || m->ncols > INT32_MAX) return STC_ERR_INVALID_ARG;
+    if (!m->rowptr) return STC_ERR_INVALID_ARG;
+    if (m->nnz > 0 && (!m->col || !m->val)) return STC_ERR_INVALID_ARG;
+    return STC_OK;
+}
+
+// One warp per row: rowptr bounds and monotonicity, column range and strict order.
+__global__ void k_validate_csr(int64_t nrows, int64_t ncols, int64_t nnz,
+                               const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                               int* flags) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    if (warp == 0 && lane == 0) {
+        if (ptr[0] != 0 || ptr[nrows] != nnz) atomicOr(flags, STC_FLAG_SHAPE);
+    }
+    int bad = 0;
+    for (int64_t i = warp; i < nrows; i += nwarps) {
+        int64_t lo = ptr[i], hi = ptr[i + 1];
+        if (lo < 0 || hi < lo || hi > nnz) {
+            bad |= STC_FLAG_SHAPE;
+            continue;
+        }
+        for (int64_t p = lo + lane; p < hi; p += 32) {
+            int32_t c = col[p];
+            if (c < 0 || c >= ncols) bad |= STC_FLAG_UNSORTED;
+            if (p > lo && col[p - 1] >= c) bad |= STC_FLAG_UNSORTED;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane == 0 && bad) atomicOr(flags, bad);
+}
+
+stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s) {
+    int64_t warps_needed = m->nrows > 0 ? m->nrows : 1;
+    int64_t blocks = (warps_needed * 32 + 255) / 256;
+    int64_t cap = int64_t(h->num_sms) * 8;
+    if (blocks > cap) blocks = cap;
+    k_validate_csr<<<(unsigned)blocks, 256, 0, s>>>(m->nrows, m->ncols, m->nnz, m->rowptr, m->col,
+                                                    h->d_flags);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return STC_OK;
+}
+
+// ----------------------------------------------------------------- scan
+
+constexpr int SCAN_NT = 512;
+constexpr int SCAN_PER_THREAD = 8;
+constexpr int SCAN_TILE = SCAN_NT * SCAN_PER_THREAD;
+
+// Phase 1: inclusive scan of each tile in place; tile totals to `part`.
+__global__ void __launch_bounds__(SCAN_NT) k_scan_tiles(int64_t* data, int64_t n, int64_t* part) {
+    __shared__ int64_t s_warp[SCAN_NT / 32 + 1];
+    int64_t base = int64_t(blockIdx.x) * SCAN_TILE + int64_t(threadIdx.x) * SCAN_PER_THREAD;
+    int64_t v[SCAN_PER_THREAD];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
+        int64_t idx = base + j;
+        v[j] = idx < n ? data[idx] : 0;
+        sum += v[j];
+        v[j] = sum;
+    }
+    int64_t total;
+    int64_t excl = block_exclusive_scan<SCAN_NT, int64_t>(sum, s_warp, total);
+#pragma unroll
+    for (int j = 0; j < SCAN_PER_THREAD; ++j) {
+        int64_t idx = base + j;
+        if (idx < n) data[idx] = v[j] + excl;
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// Phase 2: one block turns the tile totals into exclusive tile offsets.
+__global__ void __launch_bounds__(SCAN_NT) k_scan_parts(int64_t* part, int64_t nparts) {
+    __shared__ int64_t s_warp[SCAN_NT / 32 + 1];
+    __shared__ int64_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < nparts; b += SCAN_NT) {
+        int64_t idx = b + threadIdx.x;
+        int64_t v = idx < nparts ? part[idx] : 0;
+        int64_t total;
+        int64_t excl = block_exclusive_scan<SCAN_NT, int64_t>(v, s_warp, total);
+        int64_t carry = s_carry;
+        if (idx < nparts) part[idx] = carry + excl;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + total;
+        __syncthreads();
+    }
+}
+
+// Phase 3: add each tile's offset.
+__global__ void __launch_bounds__(SCAN_NT) k_scan_add(int64_t* data, int64_t n, const int64_t* part) {
+    if (blockIdx.x == 0) return;
+    int64_t off = part[blockIdx.x];
+    int64_t base = int64_t(blockIdx.x) * SCAN_TILE;
+    for (int j = threadIdx.x; j < SCAN_TILE; j += SCAN_NT) {
+        int64_t idx = base + j;
+        if (idx < n) data[idx] += off;
+    }
+}
+
+stc_status stc_inclusive_scan_i64(stc_handle* h, StcScratch& sc, int64_t* data, int64_t n,
+                                  stc_stream s) {
+    if (n <= 0) return STC_OK;
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int64_t* part = sc.get<int64_t>(size_t(tiles));
+    if (!part) return STC_ERR_OOM;
+    k_scan_tiles<<<(unsigned)tiles, SCAN_NT, 0, s>>>(data, n, part);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    if (tiles > 1) {
+        k_scan_parts<<<1, SCAN_NT, 0, s>>>(part, tiles);
+        STC_LAUNCH_CHECK();
+        k_scan_add<<<(unsigned)tiles, SCAN_NT, 0, s>>>(data, n, part);
+        STC_LAUNCH_CHECK();
+        stc_count(h, 2);
+    }
+    return STC_OK;
+}
+
+// ----------------------------------------------------------------- public entry points
+
+static bool alg_valid(int alg) { return alg >= 0 && alg <= ALG_MULTPATH; }
+
+extern "C" stc_status stc_contract_spgemm(stc_handle* h, stc_algebra alg, const stc_csr* A,
+                                          const stc_csr* B, stc_csr* C, const stc_opts* opts,
+                                          stc_stream stream) {
+    if (!h || !C) return STC_ERR_INVALID_ARG;
+    if (!alg_valid(alg)) return STC_ERR_ALGEBRA;
+    stc_status st = stc_check_csr_host(A);
+    if (st != STC_OK) return st;
+    if ((st = stc_check_csr_host(B)) != STC_OK) return st;
+    if (A->ncols != B->nrows) return STC_ERR_SHAPE;
+    if (opts) {
+        for (int r : opts->reserved)
+            if (r != 0) return STC_ERR_INVALID_ARG;
+        int w = opts->window_cols;
+        if (w != 0 && (w < 1024 || (w & (w - 1)) != 0)) return STC_ERR_INVALID_ARG;
+    }
+    return stc_spgemm_impl(h, alg, A, B, C, opts, stream);
+}
+
+extern "C" stc_status stc_contract_spmm(stc_handle* h, stc_algebra alg, const stc_csr* A,
+                                        const void* X, int64_t ldx, int32_t ncol, void* Y,
+                                        int64_t ldy, int32_t accumulate, stc_stream stream) {
+    if (!h) return STC_ERR_INVALID_ARG;
+    if (!alg_valid(alg)) return STC_ERR_ALGEBRA;
+    stc_status st = stc_check_csr_host(A);
+    if (st != STC_OK) return st;
+    if (ncol < 0 || ldx < ncol || ldy < ncol) return STC_ERR_INVALID_ARG;
+    if (ncol > 0 && A->nrows > 0 && !Y) return STC_ERR_INVALID_ARG;
+    if (ncol > 0 && A->ncols > 0 && !X) return STC_ERR_INVALID_ARG;
+    return stc_spmm_impl(h, alg, A, X, ldx, ncol, Y, ldy, accumulate, stream);
+}
+
+extern "C" stc_status stc_contract_spmv(stc_handle* h, stc_algebra alg, const stc_csr* A,
+                                        const void* x, void* y, int32_t accumulate,
+                                        stc_stream stream) {
+    return stc_contract_spmm(h, alg, A, x, 1, 1, y, 1, accumulate, stream);
+}
+
+extern "C" stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc_csr* G,
+                                       int32_t source, void* dist_out, int32_t* rounds_out,
+                                       int64_t* relaxations_out, int32_t persistent,
+                                       stc_stream stream) {
+    if (!h || !dist_out) return STC_ERR_INVALID_ARG;
+    if (alg != STC_MIN_PLUS_I32 && alg != STC_MIN_PLUS_F32) return STC_ERR_ALGEBRA;
+    stc_status st = stc_check_csr_host(G);
+    if (st != STC_OK) return st;
+    if (G->nrows != G->ncols) return STC_ERR_SHAPE;
+    if (source < 0 || source >= G->nrows) return STC_ERR_INVALID_ARG;
+    return stc_bellman_ford_impl(h, alg, G, source, dist_out, rounds_out, relaxations_out, persistent,
+                                 stream);
+}

@@ -1,0 +1,190 @@
+"""GPU SpGEMM through the C ABI against the CPU oracle, element by element.
+
+Integer, boolean, (min,+) and multiplicity results must be bit-exact; (+,x) is
+held to rel 1e-12 (fp64) and rel 1e-5 (fp32 against the fp64 oracle).  The
+output structure (row pointers and sorted columns) must be identical.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from gpu_util import compare_values, need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ALL = [O.PT_F32, O.PT_F64, O.MP_I32, O.MP_F32, O.BOOL, O.MULTPATH]
+
+
+@pytest.fixture(scope="module")
+def H():
+    need_gpu()
+    import paper_1512_00066_b300 as stc
+    return stc.Handle()
+
+
+def vals(alg, nnz, seed, operand):
+    rng = np.random.default_rng(seed)
+    if alg == O.PT_F32:
+        return rng.standard_normal(nnz).astype(np.float32)
+    if alg == O.PT_F64:
+        return rng.standard_normal(nnz)
+    if alg == O.MP_I32:
+        return rng.integers(-1000, 100000, nnz).astype(np.int32)
+    if alg == O.MP_F32:
+        return (rng.random(nnz) * 100 - 10).astype(np.float32)
+    if alg == O.BOOL:
+        return rng.integers(0, 2, nnz).astype(np.uint8)
+    if operand == "A":
+        return rng.integers(1, 8, nnz).astype(np.int32)
+    return W.multpath_values(nnz, 20, 5, seed)
+
+
+def check(H, alg, A, B, rows=None, window_cols=0):
+    C = H.spgemm(alg, to_dev(A), to_dev(B), window_cols=window_cols)
+    torch.cuda.synchronize()
+    H.check_device_status()
+    rp, col, val = C.to_host()
+    if rows is None:
+        ptr, rcol, rval, rabs = O.spgemm(alg, A, B, want_abs=True)
+        assert np.array_equal(rp, ptr), "row pointers differ"
+        assert np.array_equal(col, rcol), "columns differ"
+        compare_values(alg, val, rval, rabs, where=f"alg {alg}")
+    else:
+        counts = O.spgemm_count(A, B)
+        assert np.array_equal(np.diff(rp), counts), "row counts differ"
+        ptr, rcol, rval, rabs = O.spgemm(alg, A, B, rows=rows, want_abs=True)
+        sel = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows]) if len(rows) else np.zeros(0, int)
+        assert np.array_equal(col[sel], rcol)
+        v = val[sel] if alg != O.MULTPATH else val[sel]
+        compare_values(alg, v, rval, rabs, where=f"alg {alg} sampled")
+    return C
+
+
+def test_er4096_min_plus_exact(H):
+    """ER n=4096, exactly 8 distinct columns per row, int32 U[1,1000]: C = A (x) A."""
+    A = W.er_fixed_degree(4096, 8, seed=0)
+    A.val = W.weights_int(A.nnz, 1, 1000, seed=0)
+    check(H, O.MP_I32, A, A)
+
+
+@pytest.mark.parametrize("alg", ALL)
+def test_random_rectangular_all_algebras(H, alg):
+    A = W.random_csr(3001, 2500, 40, seed=1, empty_frac=0.1)
+    B = W.random_csr(2500, 3999, 60, seed=2, empty_frac=0.1)
+    A.val = vals(alg, A.nnz, 3, "A")
+    B.val = vals(alg, B.nnz, 4, "B")
+    check(H, alg, A, B)
+
+
+@pytest.mark.parametrize("alg", ALL)
+def test_small_windows_multi_window_path(H, alg):
+    """Force 1024-column windows so every row spans several windows."""
+    A = W.random_csr(700, 900, 80, seed=5, empty_frac=0.05)
+    B = W.random_csr(900, 5000, 120, seed=6, empty_frac=0.05)
+    A.val = vals(alg, A.nnz, 7, "A")
+    B.val = vals(alg, B.nnz, 8, "B")
+    check(H, alg, A, B, window_cols=1024)
+
+
+@pytest.mark.parametrize("alg", ALL)
+def test_rmat14_square(H, alg):
+    """R-MAT scale 14: hub rows longer than one chunk of A, several windows."""
+    A = W.rmat(14, seed=3)
+    A.val = vals(alg, A.nnz, 9, "A")
+    B = A.with_val(vals(alg, A.nnz, 10, "B"))
+    check(H, alg, A, B)
+
+
+def test_rmat14_plus_times_unit_weights_relative(H):
+    A = W.rmat(14, seed=4)
+    A.val = W.weights_unit01(A.nnz, 1)
+    for alg in (O.PT_F64, O.PT_F32):
+        a = A.with_val(A.val.astype(np.float32 if alg == O.PT_F32 else np.float64))
+        C = H.spgemm(alg, to_dev(a), to_dev(a))
+        rp, col, val = C.to_host()
+        ptr, rcol, rval, _ = O.spgemm(alg, a, a)
+        assert np.array_equal(col, rcol)
+        tol = 1e-12 if alg == O.PT_F64 else 1e-5
+        assert np.max(np.abs(val.astype(np.float64) - rval) / rval) <= tol
+
+
+def test_edge_cases(H):
+    import paper_1512_00066_b300 as stc
+    # empty A, empty B, 1x1, rows with ub == 0, single column
+    empty = W.Csr(5, 7, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    B = W.random_csr(7, 9, 3, seed=1)
+    B.val = np.arange(B.nnz, dtype=np.int32)
+    C = H.spgemm(O.MP_I32, to_dev(empty), to_dev(B))
+    assert C.nnz == 0 and np.array_equal(C.rowptr.cpu().numpy(), np.zeros(6))
+    one = W.Csr(1, 1, np.array([0, 1], np.int64), np.array([0], np.int32), np.array([3], np.int32))
+    C = H.spgemm(O.MP_I32, to_dev(one), to_dev(one))
+    assert C.to_host()[2].tolist() == [6]
+    A = W.random_csr(50, 7, 3, seed=2, empty_frac=0.5)
+    A.val = np.ones(A.nnz, np.int32)
+    Bz = W.Csr(7, 1, np.zeros(8, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    C = H.spgemm(O.MP_I32, to_dev(A), to_dev(Bz))
+    assert C.nnz == 0
+    col1 = W.random_csr(7, 1, 1, seed=3)
+    col1.val = np.arange(col1.nnz, dtype=np.int32) + 1
+    check(H, O.MP_I32, A, col1)
+    # columns 0 and n-1 present
+    n = 300
+    E = W.csr_from_coo(np.r_[np.arange(n), np.arange(n)], np.r_[np.zeros(n, int), np.full(n, n - 1)], n, n)
+    E.val = np.arange(E.nnz, dtype=np.int32)
+    check(H, O.MP_I32, E, E)
+
+
+def test_errors_are_statuses(H):
+    import paper_1512_00066_b300 as stc
+    A = W.random_csr(10, 8, 3, seed=1)
+    A.val = np.ones(A.nnz, np.int32)
+    B = W.random_csr(9, 8, 3, seed=2)
+    B.val = np.ones(B.nnz, np.int32)
+    with pytest.raises(stc.StcError) as e:
+        H.spgemm(O.MP_I32, to_dev(A), to_dev(B))
+    assert e.value.status == 2  # shape
+    # unsorted columns
+    U = W.Csr(2, 8, np.array([0, 2, 3], np.int64), np.array([5, 1, 2], np.int32), np.ones(3, np.int32))
+    S = W.random_csr(8, 8, 3, seed=3)
+    S.val = np.ones(S.nnz, np.int32)
+    with pytest.raises(stc.StcError) as e:
+        H.spgemm(O.MP_I32, to_dev(U), to_dev(S))
+    assert e.value.status == 3
+    # column out of range
+    R = W.Csr(1, 8, np.array([0, 1], np.int64), np.array([8], np.int32), np.ones(1, np.int32))
+    with pytest.raises(stc.StcError) as e:
+        H.spgemm(O.MP_I32, to_dev(R), to_dev(S))
+    assert e.value.status == 3
+    # bad row pointers
+    P = W.Csr(2, 8, np.array([0, 3, 2], np.int64), np.array([1, 2], np.int32), np.ones(2, np.int32))
+    with pytest.raises(stc.StcError) as e:
+        H.spgemm(O.MP_I32, to_dev(P), to_dev(S))
+    assert e.value.status == 2
+    # the handle stays usable after errors
+    check(H, O.MP_I32, S, S)
+
+
+def test_repeatable(H):
+    A = W.rmat(12, seed=8)
+    A.val = W.weights_int(A.nnz, 1, 1000, 1)
+    d = to_dev(A)
+    C1 = H.spgemm(O.MP_I32, d, d).to_host()
+    C2 = H.spgemm(O.MP_I32, d, d).to_host()
+    for x, y in zip(C1, C2):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("alg", [O.PT_F64, O.PT_F32])
+def test_rmat18_full_size_sampled(H, alg):
+    """R-MAT scale 18 A.A at full size: every row count against the oracle's
+    exact counts, and every 64th row plus the 256 heaviest rows element by element."""
+    A = W.rmat(18, seed=0)
+    w = W.weights_unit01(A.nnz, seed=0)
+    A.val = w.astype(np.float32 if alg == O.PT_F32 else np.float64)
+    lens = np.diff(A.rowptr)
+    ub = np.zeros(A.nrows, np.int64)
+    np.add.at(ub, np.repeat(np.arange(A.nrows), lens), lens[A.col])
+    rows = np.unique(np.r_[np.arange(0, A.nrows, 64), np.argsort(ub)[-256:]])
+    check(H, alg, A, A, rows=rows)

@@ -1,0 +1,148 @@
+"""GPU SpMV / SpMM and Bellman-Ford through the C ABI against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from gpu_util import compare_values, dsig_from_raw, need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ALL = [O.PT_F32, O.PT_F64, O.MP_I32, O.MP_F32, O.BOOL, O.MULTPATH]
+
+
+@pytest.fixture(scope="module")
+def H():
+    need_gpu()
+    import paper_1512_00066_b300 as stc
+    return stc.Handle()
+
+
+def dense_vals(alg, shape, seed):
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(shape))
+    if alg == O.PT_F32:
+        return rng.standard_normal(n).astype(np.float32).reshape(shape)
+    if alg == O.PT_F64:
+        return rng.standard_normal(n).reshape(shape)
+    if alg == O.MP_I32:
+        return rng.integers(0, 5000, n).astype(np.int32).reshape(shape)
+    if alg == O.MP_F32:
+        return (rng.random(n) * 50).astype(np.float32).reshape(shape)
+    if alg == O.BOOL:
+        return rng.integers(0, 2, n).astype(np.uint8).reshape(shape)
+    return W.multpath_values(n, 30, 6, seed).reshape(shape)
+
+
+def a_vals(alg, nnz, seed):
+    rng = np.random.default_rng(seed)
+    if alg in (O.PT_F32,):
+        return rng.standard_normal(nnz).astype(np.float32)
+    if alg == O.PT_F64:
+        return rng.standard_normal(nnz)
+    if alg in (O.MP_I32, O.MULTPATH):
+        return rng.integers(1, 100, nnz).astype(np.int32)
+    if alg == O.MP_F32:
+        return rng.random(nnz).astype(np.float32)
+    return rng.integers(0, 2, nnz).astype(np.uint8)
+
+
+def dev_dense(alg, X):
+    if alg == O.MULTPATH:
+        raw = np.ascontiguousarray(X).view(np.uint8).reshape(X.shape + (16,))
+        return torch.from_numpy(raw.copy()).cuda()
+    return torch.from_numpy(np.ascontiguousarray(X)).cuda()
+
+
+def host_out(alg, Y):
+    y = Y.cpu().numpy()
+    if alg == O.MULTPATH:
+        return dsig_from_raw(y).reshape(y.shape[:-1])
+    return y
+
+
+@pytest.mark.parametrize("alg", ALL)
+@pytest.mark.parametrize("ncol", [1, 5, 37])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_spmm_all_algebras(H, alg, ncol, accumulate):
+    A = W.random_csr(2049, 1500, 70, seed=11, empty_frac=0.1)
+    A.val = a_vals(alg, A.nnz, 12)
+    shape = (1500,) if ncol == 1 else (1500, ncol)
+    X = dense_vals(alg, shape, 13)
+    Y0 = dense_vals(alg, (2049,) if ncol == 1 else (2049, ncol), 14) if accumulate else None
+    Yd = dev_dense(alg, Y0) if accumulate else None
+    Y = H.spmm(alg, to_dev(A), dev_dense(alg, X), Yd, accumulate=accumulate)
+    torch.cuda.synchronize()
+    H.check_device_status()
+    got = host_out(alg, Y)
+    ref = O.spmm(alg, A, X, Y0)
+    if alg in (O.PT_F32, O.PT_F64):
+        # bound relative to the sum of |terms| (signed values cancel)
+        absA = A.with_val(np.abs(A.val).astype(np.float64))
+        absX = np.abs(X).astype(np.float64)
+        scale = O.spmm(O.PT_F64, absA, absX, None if Y0 is None else np.abs(Y0).astype(np.float64))
+        tol = 1e-12 if alg == O.PT_F64 else 1e-5
+        assert np.all(np.abs(got.astype(np.float64) - ref.astype(np.float64)) <= tol * np.abs(ref) + 1e-14 * scale + 1e-30)
+    elif alg == O.MULTPATH:
+        assert np.array_equal(got["d"], ref["d"]) and np.array_equal(got["s"], ref["s"])
+    else:
+        assert got.tobytes() == ref.tobytes()
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_bellman_ford_rmat14(H, persistent):
+    G = W.rmat(14, seed=21)
+    G.val = W.weights_int(G.nnz, 1, 1000, 22)
+    d, r = H.bellman_ford(O.MP_I32, to_dev(G), 0, persistent=persistent)
+    ref, rref = O.bellman_ford(O.MP_I32, G, 0)
+    assert np.array_equal(d.cpu().numpy(), ref)
+    assert 1 <= r <= rref
+    G.val = W.weights_unit01(G.nnz, 23).astype(np.float32)
+    d, r = H.bellman_ford(O.MP_F32, to_dev(G), 0, persistent=persistent)
+    ref, rref = O.bellman_ford(O.MP_F32, G, 0)
+    assert d.cpu().numpy().tobytes() == ref.tobytes()
+    assert 1 <= r <= rref
+
+
+def test_bellman_ford_rmat18_full_size(H):
+    """R-MAT scale 18 from vertex 0, (min,+) fp32, persistent launch: bit-exact."""
+    G = W.rmat(18, seed=0)
+    G.val = W.weights_unit01(G.nnz, seed=1).astype(np.float32)
+    d, r = H.bellman_ford(O.MP_F32, to_dev(G), 0, persistent=True)
+    ref = O.dijkstra(O.MP_F32, G, 0)
+    assert d.cpu().numpy().tobytes() == ref.tobytes()
+    d2, r2 = H.bellman_ford(O.MP_F32, to_dev(G), 0, persistent=False)
+    assert d2.cpu().numpy().tobytes() == ref.tobytes()
+
+
+def test_bellman_ford_closed_forms_and_cycles(H):
+    import paper_1512_00066_b300 as stc
+    n = 1000
+    L = W.csr_from_coo(np.arange(n - 1), np.arange(1, n), n, n)
+    L.val = np.full(n - 1, 7, np.int32)
+    for persistent in (True, False):
+        d, r = H.bellman_ford(O.MP_I32, to_dev(L), 0, persistent=persistent)
+        assert np.array_equal(d.cpu().numpy(), 7 * np.arange(n)) and r == n - 1
+        d, r = H.bellman_ford(O.MP_I32, to_dev(L), 500, persistent=persistent)
+        assert np.all(d.cpu().numpy()[:500] == O.TROP_I32_ID)
+    # negative weights, no negative cycle
+    G = W.random_csr(3000, 3000, 4, seed=31)
+    rng = np.random.default_rng(3)
+    pot = rng.integers(0, 100, 3000)
+    rows = np.repeat(np.arange(3000), np.diff(G.rowptr))
+    G.val = (rng.integers(1, 50, G.nnz) + pot[G.col] - pot[rows]).astype(np.int32)
+    ref, _ = O.bellman_ford(O.MP_I32, G, 0)
+    for persistent in (True, False):
+        d, _ = H.bellman_ford(O.MP_I32, to_dev(G), 0, persistent=persistent)
+        assert np.array_equal(d.cpu().numpy(), ref)
+    # reachable negative cycle -> status
+    C = W.csr_from_coo([0, 1, 2], [1, 2, 1], 3, 3)
+    C.val = np.array([4, 2, -3], np.int32)
+    for persistent in (True, False):
+        with pytest.raises(stc.StcError) as e:
+            H.bellman_ford(O.MP_I32, to_dev(C), 0, persistent=persistent)
+        assert e.value.status == 7
+    # the handle stays usable
+    d, _ = H.bellman_ford(O.MP_I32, to_dev(L), 0)
+    assert np.array_equal(d.cpu().numpy(), 7 * np.arange(n))
