@@ -68,7 +68,9 @@ typedef enum {
     STC_ERR_OOM = 5,         /* the allocator returned NULL                       */
     STC_ERR_CUDA = 6,        /* a CUDA runtime call failed                        */
     STC_ERR_NEG_CYCLE = 7,   /* Bellman-Ford still relaxing after |V| rounds      */
-    STC_ERR_TIMEOUT = 8      /* a bounded device-side wait gave up                */
+    STC_ERR_TIMEOUT = 8,     /* a bounded device-side wait gave up                */
+    STC_ERR_CAPACITY = 9     /* problem larger than the fixed scratch of
+                                stc_bellman_ford_noalloc                         */
 } stc_status;
 
 /*
@@ -246,6 +248,34 @@ STC_API stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc_cs
 STC_API stc_status stc_set_timing(stc_handle* h, int32_t enable);
 STC_API int32_t stc_phase_times(stc_handle* h, float* ms_out, int32_t max_phases);
 STC_API int64_t stc_kernel_launches(const stc_handle* h);
+
+/*
+ * Allocation-free Bellman-Ford.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run -- for
+ * example code inside a host callback or a real-time loop where cudaMalloc would
+ * block or is forbidden, or a host process that hands out memory only from its
+ * own fixed pools.  It computes exactly what stc_bellman_ford computes with
+ * persistent = 1, takes no handle, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Its working memory (frontiers, round stamps, distance keys, counters) lives in
+ * one fixed array in device global memory that the library defines for every GPU
+ * it is loaded on (about 16 MiB, held until the process exits).  Hence:
+ *  - G->nrows may not exceed STC_NOALLOC_BF_MAX_VERTICES; larger graphs get
+ *    STC_ERR_CAPACITY before any work is enqueued.
+ *  - The first call on each device looks up that array's device address
+ *    (cudaGetSymbolAddress) with the device current; make that first call
+ *    before any stream capture on that device.
+ *  - Every call on a device shares the same array and leaves its contents
+ *    behind; each call clears what must start at zero.  Calls whose work
+ *    overlaps on the GPU (different streams or threads without ordering) race
+ *    on the array and give wrong results: serialise them.
+ * Arguments, results and the other errors are those of stc_bellman_ford;
+ * *rounds_out (host, may be NULL).  Synchronises `stream`.
+ */
+#define STC_NOALLOC_BF_MAX_VERTICES (1 << 20)
+STC_API stc_status stc_bellman_ford_noalloc(stc_algebra alg, const stc_csr* G, int32_t source,
+                                            void* dist_out, int32_t* rounds_out, stc_stream stream);
 
 #ifdef __cplusplus
 }

@@ -32,7 +32,8 @@ ALGEBRA_NAMES = {0: "plus_times_f32", 1: "plus_times_f64", 2: "min_plus_i32", 3:
 
 STATUS = {0: "STC_OK", 1: "STC_ERR_INVALID_ARG", 2: "STC_ERR_SHAPE", 3: "STC_ERR_UNSORTED",
           4: "STC_ERR_ALGEBRA", 5: "STC_ERR_OOM", 6: "STC_ERR_CUDA", 7: "STC_ERR_NEG_CYCLE",
-          8: "STC_ERR_TIMEOUT"}
+          8: "STC_ERR_TIMEOUT", 9: "STC_ERR_CAPACITY"}
+NOALLOC_BF_MAX_VERTICES = 1 << 20
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libstc.so")
@@ -107,6 +108,9 @@ def lib():
             L.stc_phase_times.restype = i32
             L.stc_kernel_launches.argtypes = [p]
             L.stc_kernel_launches.restype = i64
+            L.stc_bellman_ford_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(_Csr), i32, p,
+                                                   ctypes.POINTER(i32), p]
+            L.stc_bellman_ford_noalloc.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -295,6 +299,22 @@ class Handle:
 
     def kernel_launches(self) -> int:
         return int(lib().stc_kernel_launches(self._h))
+
+
+def bellman_ford_noalloc(alg: int, G: DeviceCsr, source: int, dist: torch.Tensor, stream=None) -> int:
+    """Allocation-free Bellman-Ford (stc_bellman_ford_noalloc) into the caller's `dist`.
+
+    For callers that must not allocate device memory during the call: the
+    library's working memory is a fixed array compiled into it.  Returns the
+    number of rounds; raises StcError (STC_ERR_CAPACITY) above
+    NOALLOC_BF_MAX_VERTICES vertices.
+    """
+    rounds = ctypes.c_int32(0)
+    g = G._c()
+    st = lib().stc_bellman_ford_noalloc(alg, ctypes.byref(g), int(source), dist.data_ptr(),
+                                        ctypes.byref(rounds), _stream_ptr(stream))
+    _check(st, "stc_bellman_ford_noalloc")
+    return int(rounds.value)
 
 
 _default = {}

@@ -16,6 +16,8 @@
 // grid barrier (bounded spin) and tests convergence on the device.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "stc_internal.cuh"
 
 namespace {
@@ -265,4 +267,111 @@ stc_status stc_bellman_ford_impl(stc_handle* h, int alg, const stc_csr* G, int32
                                  int32_t* rounds, int64_t* relax, int32_t persistent, stc_stream s) {
     if (alg == ALG_MP_I32) return run_bf<ALG_MP_I32>(h, G, source, dist, rounds, relax, persistent, s);
     return run_bf<ALG_MP_F32>(h, G, source, dist, rounds, relax, persistent, s);
+}
+
+// ----------------------------------------------------------------- allocation-free variant
+//
+// stc_bellman_ford_noalloc serves callers that cannot allocate device memory
+// while they run (host callbacks, real-time loops, processes that hand out
+// memory only from fixed pools).  It runs the same kernels as the persistent
+// driver above, with every piece of working memory carved from one file-scope
+// device array instead of the handle's allocator.
+
+namespace {
+
+constexpr size_t NOALLOC_HEADER = 256;  // counters, barrier, rounds, flags, relaxations
+// per vertex: two frontier slots, a round stamp and an fp32 distance key
+constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + size_t(STC_NOALLOC_BF_MAX_VERTICES) * 16;
+
+// Held by every GPU that loads the library, until the process exits.  Host code
+// must not pass this name to a kernel: on the host it is only a stand-in symbol.
+// Its device address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_bf_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (set-up on first use).
+stc_status noalloc_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return STC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_bf_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return STC_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return STC_OK;
+}
+
+template <int ALG>
+stc_status run_bf_noalloc(const stc_csr* G, int32_t source, void* dist_out, int32_t* rounds_out,
+                          stc_stream s) {
+    using D = typename BfT<ALG>::D;
+    const int64_t n = G->nrows;
+    int dev = 0, num_sms = 0;
+    STC_CUDA_TRY(cudaGetDevice(&dev));
+    STC_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    unsigned char* base = nullptr;
+    stc_status st = noalloc_scratch(dev, &base);
+    if (st != STC_OK) return st;
+    int* ints = reinterpret_cast<int*>(base);  // [0..2] counters, [4..5] barrier, [6] rounds, [7] flags
+    BfArgs a;
+    a.n = n;
+    a.nnz = G->nnz;
+    a.ptr = G->rowptr;
+    a.col = G->col;
+    a.w = G->val;
+    a.cnt = ints;
+    a.relax = reinterpret_cast<unsigned long long*>(base + 64);
+    a.frontier[0] = reinterpret_cast<int32_t*>(base + NOALLOC_HEADER);
+    a.frontier[1] = a.frontier[0] + n;
+    a.stamp = a.frontier[1] + n;
+    D* dist = ALG == ALG_MP_I32 ? reinterpret_cast<D*>(dist_out) : reinterpret_cast<D*>(a.stamp + n);
+    unsigned* bar = reinterpret_cast<unsigned*>(ints + 4);
+    int* d_rounds = ints + 6;
+    int* flags = ints + 7;
+
+    // the previous call's counters, barrier state and flags are left behind: clear them
+    STC_CUDA_TRY(cudaMemsetAsync(base, 0, NOALLOC_HEADER, s));
+    if ((st = stc_validate_csr_flags_async(G, flags, num_sms, s)) != STC_OK) return st;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > int64_t(num_sms) * 8) blocks = int64_t(num_sms) * 8;
+    k_bf_init<ALG><<<unsigned(blocks), 256, 0, s>>>(a, dist, source);
+    STC_LAUNCH_CHECK();
+    int per_sm = 0;
+    STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bf_persistent<ALG>, BF_NT, 0));
+    if (per_sm < 1) return STC_ERR_CUDA;
+    void* args[] = {&a, &dist, &bar, &flags, &d_rounds};
+    STC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bf_persistent<ALG>, dim3(per_sm * num_sms),
+                                             dim3(BF_NT), args, 0, s));
+    if (ALG == ALG_MP_F32) {
+        k_bf_finish<ALG><<<unsigned(blocks), 256, 0, s>>>(n, dist, dist_out);
+        STC_LAUNCH_CHECK();
+    }
+    int host[2] = {0, 0};  // rounds, flags
+    STC_CUDA_TRY(cudaMemcpyAsync(host, d_rounds, sizeof(host), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rounds_out) *rounds_out = host[0];
+    return host[1] ? stc_flags_to_status(host[1]) : STC_OK;
+}
+
+}  // namespace
+
+extern "C" stc_status stc_bellman_ford_noalloc(stc_algebra alg, const stc_csr* G, int32_t source,
+                                               void* dist_out, int32_t* rounds_out, stc_stream stream) {
+    if (!dist_out) return STC_ERR_INVALID_ARG;
+    if (alg != STC_MIN_PLUS_I32 && alg != STC_MIN_PLUS_F32) return STC_ERR_ALGEBRA;
+    stc_status st = stc_check_csr_host(G);
+    if (st != STC_OK) return st;
+    if (G->nrows != G->ncols) return STC_ERR_SHAPE;
+    if (G->nrows > STC_NOALLOC_BF_MAX_VERTICES) return STC_ERR_CAPACITY;
+    if (source < 0 || source >= G->nrows) return STC_ERR_INVALID_ARG;
+    if (alg == STC_MIN_PLUS_I32) return run_bf_noalloc<ALG_MP_I32>(G, source, dist_out, rounds_out, stream);
+    return run_bf_noalloc<ALG_MP_F32>(G, source, dist_out, rounds_out, stream);
 }

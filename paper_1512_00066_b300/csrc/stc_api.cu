@@ -17,6 +17,7 @@ static const char* k_status_text[] = {
     "CUDA runtime error",
     "negative cycle reachable from the source",
     "bounded device-side wait timed out",
+    "graph larger than the fixed scratch of the allocation-free entry point",
 };
 
 extern "C" const char* stc_status_str(stc_status s) {
@@ -204,6 +205,17 @@ stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s)
                                                     h->d_flags);
     STC_LAUNCH_CHECK();
     stc_count(h);
+    return STC_OK;
+}
+
+// Same validation with the flag word supplied by the caller (no handle).
+stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, int num_sms, stc_stream s) {
+    int64_t warps_needed = m->nrows > 0 ? m->nrows : 1;
+    int64_t blocks = (warps_needed * 32 + 255) / 256;
+    int64_t cap = int64_t(num_sms) * 8;
+    if (blocks > cap) blocks = cap;
+    k_validate_csr<<<(unsigned)blocks, 256, 0, s>>>(m->nrows, m->ncols, m->nnz, m->rowptr, m->col, flags);
+    STC_LAUNCH_CHECK();
     return STC_OK;
 }
 

@@ -80,6 +80,8 @@ stc_status stc_check_csr_host(const stc_csr* m);
 // Enqueue the device-side validation of a CSR matrix; raises STC_FLAG_SHAPE /
 // STC_FLAG_UNSORTED in h->d_flags.
 stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s);
+// The same check raising its flags in `flags` (a device int); needs no handle.
+stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, int num_sms, stc_stream s);
 
 // ----------------------------------------------------------------- algebra ids
 
