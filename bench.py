@@ -44,11 +44,12 @@ def peaks():
 
 
 def build_workload(name: str):
-    if name == "rmat18":
-        A = W.rmat(18, seed=0)
+    if name.startswith("rmat"):
+        scale = int(name[4:])
+        A = W.rmat(scale, seed=0)
         w = W.weights_unit01(A.nnz, seed=0)
         g = W.weights_unit01(A.nnz, seed=1).astype(np.float32)
-        return {"A": A, "w64": w, "w32": w.astype(np.float32), "g32": g, "scale": 18}
+        return {"A": A, "w64": w, "w32": w.astype(np.float32), "g32": g, "scale": scale}
     if name == "er4096":
         A = W.er_fixed_degree(4096, 8, seed=0)
         return {"A": A, "wi32": W.weights_int(A.nnz, 1, 1000, seed=0), "scale": None}
@@ -257,13 +258,13 @@ def run_stc(args):
         t_total = float(tt.item())
     value = world * ops_total / t_total
 
-    # roofline of the dominant kernel (numeric pass of the first SpGEMM)
+    # roofline of the dominant kernel (numeric pass of the first SpGEMM): compulsory
+    # DRAM bytes = read A and B once, the cell-offset table, C.rowptr; write C
     n, nnzA = A.nrows, A.nnz
     nnzC = infos[0]["nnzC"]
     s = dom_val_bytes
-    W_cols = 8192 if s == 8 else 16384
-    nwin = max(1, -(-A.ncols // W_cols))
-    compulsory = (csr_bytes(n, nnzA, s) * 2 + (4 * A.nrows * (nwin + 1) if nwin > 1 else 0)
+    ncell = -(-A.ncols // 1024)
+    compulsory = (csr_bytes(n, nnzA, s) * 2 + 4 * A.nrows * (ncell + 1)
                   + 8 * (n + 1) + (4 + s) * nnzC)
     num_ms = statistics.mean(i["numeric_ms"] for i in infos)
     hbm, peak_kind = peaks()
@@ -282,8 +283,9 @@ def run_stc(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32" if wl["scale"] else "int32",
             "data": "synthetic",
-            "config": {"workload": ("rmat18: (+,x) SpGEMM A.A fp64 and fp32 + Bellman-Ford (min,+) fp32 "
-                                    "from vertex 0" if wl["scale"] else "er4096: (min,+) int32 SpGEMM A(x)A"),
+            "config": {"workload": (f"rmat{wl['scale']}: (+,x) SpGEMM A.A fp64 and fp32 + Bellman-Ford "
+                                    "(min,+) fp32 from vertex 0" if wl["scale"] else
+                                    "er4096: (min,+) int32 SpGEMM A(x)A"),
                        "n": A.nrows, "nnz": A.nnz, "nnzC": nnzC, "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "flushed between timed steps (write of 2x L2)",
                        "ops_per_step": ops_total // args.steps},
@@ -376,7 +378,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="stc", choices=["stc", "reference"])
-    ap.add_argument("--workload", default="rmat18", choices=["rmat18", "er4096"])
+    ap.add_argument("--workload", default="rmat18",
+                    help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -77,8 +77,8 @@ typedef enum {
  * Algebras (Section 3.1, Table 1; Section 3.3.2 for the mixed-type function).
  * Operand element types are given as A / B / C.
  *
- *  STC_PLUS_TIMES_F32   (+,x) field. float / float / float.  Products and sums
- *                       are formed in fp64 and rounded to fp32 once per output.
+ *  STC_PLUS_TIMES_F32   (+,x) field. float / float / float.  Products rounded to
+ *                       fp32, summed in fp32 in an unspecified order.
  *  STC_PLUS_TIMES_F64   (+,x) field. double / double / double.
  *  STC_MIN_PLUS_I32     tropical semiring, (+) = min, f = integer +, additive
  *                       identity INT_MAX/2 = 1073741823 (Section 3.1: half of the

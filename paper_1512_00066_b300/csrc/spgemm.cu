@@ -46,12 +46,14 @@ struct SpgArgs {
 template <int ALG> struct Tr;
 
 template <> struct Tr<ALG_PT_F32> {
-    using A = float; using B = float; using C = float; using Acc = double;
-    static __device__ __forceinline__ Acc empty() { return 0.0; }
+    // fp32 products summed with fp32 shared-memory atomics (B300's fp64 rate is a
+    // small fraction of its fp32 rate)
+    using A = float; using B = float; using C = float; using Acc = float;
+    static __device__ __forceinline__ Acc empty() { return 0.0f; }
     static __device__ __forceinline__ void combine(Acc* acc, int c, A a, B b) {
-        atomicAdd(&acc[c], double(a) * double(b));
+        atomicAdd(&acc[c], __fmul_rn(a, b));
     }
-    static __device__ __forceinline__ C out(Acc v) { return float(v); }
+    static __device__ __forceinline__ C out(Acc v) { return v; }
 };
 template <> struct Tr<ALG_PT_F64> {
     using A = double; using B = double; using C = double; using Acc = double;
@@ -441,6 +443,415 @@ k_numeric(SpgArgs g, const int32_t* __restrict__ rowlist, const int* __restrict_
     }
 }
 
+// ----------------------------------------------------------------- rank-indexed accumulator
+//
+// For outputs of at most RK_MAX_COLS columns: one CTA owns an output row and
+// keeps its whole column bitmap in shared memory (1 bit per column, plus one
+// summary bit per 32-bit word).  The products of the row are walked as warp
+// tasks: each task is up to RK_SUB consecutive entries of one B row, read by the
+// 32 lanes of a warp with coalesced loads (the few stored entries of A_i index
+// long B rows, so segment-per-warp beats product-per-thread here).
+//
+//  symbolic  bitmap of the union of the column sets, popcount of touched words
+//  numeric   1) bitmap again; 2) per 1024-column cell the popcount prefix of its
+//            words and the cells' exclusive prefix give every present column its
+//            rank, i.e. its position in the output row; the columns are written
+//            to C in order; 3) the values are accumulated in shared memory
+//            indexed by rank, with the algebra's additive operator as a
+//            shared-memory atomic, then written to C coalesced.  Rows with more
+//            entries than the value buffer are cut into rank windows made of
+//            whole cells; a table of per-cell offsets inside every B row restricts
+//            each window's walk to that window's columns.
+
+constexpr int RK_SUB = 256;                 // B entries per warp task
+constexpr int RK_CELL_SHIFT = 10;           // 1024-column cells (32 bitmap words)
+constexpr int RK_CELL = 1 << RK_CELL_SHIFT;
+constexpr int RK_MAX_COLS = 1 << 18;        // 32 KB bitmap
+constexpr int RK_NT = 1024;     // numeric kernel: one CTA per SM, large value buffer
+constexpr int RK_SYM_NT = 256;  // symbolic kernel: more rows in flight per SM
+constexpr size_t RK_SMEM_TARGET = 224 * 1024;  // one CTA per SM
+
+template <int NT>
+struct TaskSmem {
+    int pre[NT];      // exclusive prefix of the warp-task counts of the chunk's segments
+    int len[NT];      // segment length
+    int64_t lo[NT];   // first B position of the segment
+    int warp[NT / 32 + 1];
+};
+
+// Segments of the chunk [p0, p0+NT) of A_i: whole B rows, or (ctab != null) the
+// part of each B row inside cells [cl, ch).  Returns the number of warp tasks.
+template <int NT, class AT, bool WITH_VAL>
+__device__ __forceinline__ int load_tasks(const SpgArgs& g, const int32_t* __restrict__ ctab, int ncell,
+                                          int64_t p0, int64_t ahi, int cl, int ch, TaskSmem<NT>& ts,
+                                          AT* s_aval) {
+    int64_t p = p0 + threadIdx.x;
+    int len = 0;
+    int64_t lo = 0;
+    AT av = AT();
+    if (p < ahi) {
+        int32_t k = g.a_col[p];
+        if ((uint64_t)k < (uint64_t)g.K) {
+            int64_t bl, bh;
+            row_range(g.b_ptr, k, g.nnzB, bl, bh);
+            if (ctab) {
+                const int32_t* t = ctab + int64_t(k) * (ncell + 1);
+                int64_t s = bl + t[cl], e = bl + t[ch];
+                if (e > bh) e = bh;
+                if (s > e) s = e;
+                bl = s;
+                bh = e;
+            }
+            lo = bl;
+            len = int(bh - bl);
+            if (WITH_VAL) av = static_cast<const AT*>(g.a_val)[p];
+        }
+    }
+    int total;
+    int ex = block_exclusive_scan<NT, int>((len + RK_SUB - 1) / RK_SUB, ts.warp, total);
+    ts.pre[threadIdx.x] = ex;
+    ts.len[threadIdx.x] = len;
+    ts.lo[threadIdx.x] = lo;
+    if (WITH_VAL) s_aval[threadIdx.x] = av;
+    __syncthreads();
+    return total;
+}
+
+// Run op(p, col, j) for every product of the loaded chunk (p: B position,
+// j: index of the A entry in the chunk).  Columns are loaded RK_SUB/32 at a time.
+template <int NT, class Op>
+__device__ __forceinline__ void walk_tasks(const SpgArgs& g, const TaskSmem<NT>& ts, int ntasks, Op op) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int U = RK_SUB / 32;
+    for (int t = wid; t < ntasks; t += NT / 32) {
+        const int j = find_seg<NT>(ts.pre, t);
+        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
+        const int64_t end = ts.lo[j] + ts.len[j];
+        // warp-uniform number of 32-entry steps of this task (short B rows stop early)
+        const int64_t span = end - start;
+        const int nu = span >= RK_SUB ? U : int((span + 31) >> 5);
+        int col[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u < nu) {
+                const int64_t p = start + lane + 32 * u;
+                col[u] = p < end ? g.b_col[p] : -1;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u < nu) {
+                const int64_t p = start + lane + 32 * u;
+                if (p < end) op(p, col[u], j);
+            }
+        }
+    }
+}
+
+// As walk_tasks, also loading the B values of the task up front:
+// op(p, col, val, j).
+template <int NT, class BT, class Op>
+__device__ __forceinline__ void walk_tasks_val(const SpgArgs& g, const TaskSmem<NT>& ts, int ntasks,
+                                               const BT* __restrict__ bval, Op op) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int U = RK_SUB / 32;
+    for (int t = wid; t < ntasks; t += NT / 32) {
+        const int j = find_seg<NT>(ts.pre, t);
+        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
+        const int64_t end = ts.lo[j] + ts.len[j];
+        const int64_t span = end - start;
+        const int nu = span >= RK_SUB ? U : int((span + 31) >> 5);
+        int col[U];
+        BT val[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u < nu) {
+                const int64_t p = start + lane + 32 * u;
+                if (p < end) {
+                    col[u] = g.b_col[p];
+                    val[u] = bval[p];
+                } else {
+                    col[u] = -1;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u < nu) {
+                const int64_t p = start + lane + 32 * u;
+                if (p < end) op(p, col[u], val[u], j);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t* summ, int col) {
+    const int w = col >> 5;
+    const uint32_t m = 1u << (col & 31);
+    if (!(bits[w] & m)) {
+        uint32_t old = atomicOr(&bits[w], m);
+        if (old == 0u) atomicOr(&summ[w >> 5], 1u << (w & 31));
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 4)
+k_symbolic_rank(SpgArgs g, const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
+                int* __restrict__ counter, int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz) {
+    extern __shared__ uint4 smem_raw[];
+    const int ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
+    const int NW = ncell * 32;
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw);
+    uint32_t* summ = bits + NW;  // one summary word per cell
+    __shared__ TaskSmem<NT> ts;
+    __shared__ int s_row;
+    __shared__ int s_red[NT / 32 + 1];
+    for (int w = threadIdx.x; w < NW + ncell; w += NT) bits[w] = 0u;
+    const int nlist = *nlist_ptr;
+    int local_max = 0;
+    for (;;) {
+        const int i = next_row(counter, nlist, rowlist, &s_row);
+        if (i < 0) break;
+        int64_t alo, ahi;
+        row_range(g.a_ptr, i, g.nnzA, alo, ahi);
+        for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
+            const int ntasks = load_tasks<NT, int, false>(g, nullptr, 0, p0, ahi, 0, 0, ts, nullptr);
+            walk_tasks<NT>(g, ts, ntasks, [&](int64_t, int col, int) {
+                if ((uint64_t)col < (uint64_t)g.ncols) set_bit(bits, summ, col);
+            });
+            __syncthreads();
+        }
+        int cnt = 0;
+        for (int w = threadIdx.x; w < NW; w += NT) {
+            const uint32_t b = bits[w];
+            if (b) {
+                cnt += __popc(b);
+                bits[w] = 0u;
+            }
+        }
+        for (int c = threadIdx.x; c < ncell; c += NT) summ[c] = 0u;
+        int tot;
+        (void)block_exclusive_scan<NT, int>(cnt, s_red, tot);
+        if (threadIdx.x == 0) {
+            row_nnz[i] = tot;
+            local_max = max(local_max, tot);
+        }
+    }
+    if (threadIdx.x == 0 && local_max) atomicMax(max_nnz, local_max);
+}
+
+// ctab[k*(ncell+1) + c] = number of entries of B_k with column < c * RK_CELL.
+__global__ void k_cell_offsets(SpgArgs g, int ncell, int32_t* __restrict__ ctab) {
+    const int64_t stride = int64_t(ncell) + 1;
+    const int64_t total = g.K * stride;
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t k = idx / stride;
+        const int64_t c = idx - k * stride;
+        int64_t lo, hi;
+        row_range(g.b_ptr, k, g.nnzB, lo, hi);
+        const int64_t target = c << RK_CELL_SHIFT;
+        int64_t a = lo, b = hi;
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if (int64_t(g.b_col[m]) < target) a = m + 1; else b = m;
+        }
+        ctab[idx] = int32_t(a - lo);
+    }
+}
+
+struct RankLayout {
+    size_t bits, summ, wpre, cellbase, winfirst, vals, scol, sig, total;
+};
+
+__host__ __device__ inline size_t rk_align(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline RankLayout rank_layout(int ncell, int vcap, int maxwin, size_t acc_bytes,
+                                                  bool multpath) {
+    RankLayout L;
+    const size_t NW = size_t(ncell) * 32;
+    L.bits = 0;
+    L.summ = rk_align(L.bits + NW * 4);
+    L.wpre = rk_align(L.summ + size_t(ncell) * 4);
+    L.cellbase = rk_align(L.wpre + NW * 2);
+    L.winfirst = rk_align(L.cellbase + (size_t(ncell) + 1) * 4);
+    L.vals = rk_align(L.winfirst + (size_t(maxwin) + 1) * 4);
+    L.scol = rk_align(L.vals + size_t(vcap) * acc_bytes);
+    L.sig = rk_align(L.scol + size_t(vcap) * 4);
+    L.total = multpath ? rk_align(L.sig + size_t(vcap) * 8) : L.sig;
+    return L;
+}
+
+template <int ALG, int NT>
+__global__ void __launch_bounds__(NT, 1)
+k_numeric_rank(SpgArgs g, const int32_t* __restrict__ ctab, int vcap, int maxwin,
+               const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
+               int* __restrict__ counter, const int64_t* __restrict__ c_ptr, int32_t* __restrict__ c_col,
+               void* __restrict__ c_val, int* __restrict__ flags) {
+    using T = Tr<ALG>;
+    using AT = typename T::A;
+    using BT = typename T::B;
+    using Acc = typename T::Acc;
+    extern __shared__ uint4 smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
+    const int ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
+    const int NW = ncell * 32;
+    const RankLayout L = rank_layout(ncell, vcap, maxwin, sizeof(Acc), ALG == ALG_MULTPATH);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(sm + L.bits);
+    uint32_t* summ = reinterpret_cast<uint32_t*>(sm + L.summ);
+    uint16_t* wpre = reinterpret_cast<uint16_t*>(sm + L.wpre);
+    int* cellbase = reinterpret_cast<int*>(sm + L.cellbase);
+    int* winfirst = reinterpret_cast<int*>(sm + L.winfirst);
+    Acc* vals = reinterpret_cast<Acc*>(sm + L.vals);
+    int32_t* scol = reinterpret_cast<int32_t*>(sm + L.scol);  // column of each rank of the window
+    double* sig = reinterpret_cast<double*>(sm + L.sig);
+    __shared__ TaskSmem<NT> ts;
+    __shared__ AT s_aval[NT];
+    __shared__ int s_row;
+    __shared__ int s_warp[NT / 32 + 1];
+    __shared__ int s_nwin;
+
+    for (int w = threadIdx.x; w < NW; w += NT) bits[w] = 0u;
+    for (int c = threadIdx.x; c < ncell; c += NT) summ[c] = 0u;
+    for (int r = threadIdx.x; r < vcap; r += NT) {
+        vals[r] = T::empty();
+        if constexpr (ALG == ALG_MULTPATH) sig[r] = 0.0;
+    }
+    const int nlist = *nlist_ptr;
+    const int vstep = vcap - RK_CELL;  // rank span that starts a new window
+    const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
+    auto* cval = static_cast<typename T::C*>(c_val);
+
+    for (;;) {
+        const int i = next_row(counter, nlist, rowlist, &s_row);
+        if (i < 0) break;
+        int64_t alo, ahi;
+        row_range(g.a_ptr, i, g.nnzA, alo, ahi);
+        const int64_t o0 = c_ptr[i];
+        const int64_t o1 = c_ptr[i + 1];
+
+        // 1) bitmap of the row's columns
+        for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
+            const int ntasks = load_tasks<NT, AT, false>(g, nullptr, 0, p0, ahi, 0, 0, ts, nullptr);
+            walk_tasks<NT>(g, ts, ntasks, [&](int64_t, int col, int) {
+                if ((uint64_t)col < (uint64_t)g.ncols) set_bit(bits, summ, col);
+            });
+            __syncthreads();
+        }
+
+        // 2) ranks: word prefix inside each cell, cell prefix, windows; columns of C
+        constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;  // cells per thread
+        int cnt[CPT];
+        int ctot = 0;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = threadIdx.x * CPT + q;
+            int n = 0;
+            if (c < ncell) {
+                uint32_t s = summ[c];
+                while (s) {
+                    const int w = c * 32 + __ffs(s) - 1;
+                    s &= s - 1;
+                    wpre[w] = uint16_t(n);
+                    n += __popc(bits[w]);
+                }
+            }
+            cnt[q] = n;
+            ctot += n;
+        }
+        int total;
+        int ex = block_exclusive_scan<NT, int>(ctot, s_warp, total);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = threadIdx.x * CPT + q;
+            if (c < ncell) cellbase[c] = ex;
+            ex += cnt[q];
+        }
+        if (threadIdx.x == 0) {
+            cellbase[ncell] = total;
+            if (total != int(o1 - o0)) atomicOr(flags, STC_FLAG_INTERNAL);
+        }
+        __syncthreads();
+        const bool fits = total <= int(o1 - o0);
+        for (int c = threadIdx.x; c < ncell; c += NT) {
+            const int wc = cellbase[c] / vstep;
+            if (c == 0 || (cellbase[c - 1] / vstep) != wc) winfirst[wc] = c;
+        }
+        if (threadIdx.x == 0) {
+            const int nw = total > 0 ? cellbase[ncell - 1] / vstep + 1 : 0;
+            winfirst[nw] = ncell;
+            s_nwin = nw;
+        }
+        __syncthreads();
+        const int nwin = s_nwin;
+
+        // 3) values, one rank window at a time
+        for (int wdw = 0; wdw < nwin; ++wdw) {
+            const int cl = winfirst[wdw], ch = winfirst[wdw + 1];
+            const int rb = cellbase[cl];
+            const int rcount = cellbase[ch] - rb;
+            const int32_t* tab = nwin > 1 ? ctab : nullptr;
+            auto rank_of = [&](int col) -> int {
+                const int w = col >> 5;
+                return cellbase[col >> RK_CELL_SHIFT] + wpre[w] +
+                       __popc(bits[w] & ((1u << (col & 31)) - 1u)) - rb;
+            };
+            for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
+                const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
+                walk_tasks_val<NT, BT>(g, ts, ntasks, bval, [&](int64_t, int col, const BT& b, int j) {
+                    if ((uint64_t)col >= (uint64_t)g.ncols) return;
+                    const int r = rank_of(col);
+                    if ((unsigned)r >= (unsigned)rcount) return;
+                    scol[r] = col;
+                    if constexpr (ALG == ALG_MULTPATH) atomicMin(&vals[r], s_aval[j] + b.d);
+                    else T::combine(vals, r, s_aval[j], b);
+                });
+                __syncthreads();
+            }
+            if constexpr (ALG == ALG_MULTPATH) {
+                for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
+                    const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
+                    walk_tasks_val<NT, BT>(g, ts, ntasks, bval, [&](int64_t, int col, const BT& b, int j) {
+                        if ((uint64_t)col >= (uint64_t)g.ncols) return;
+                        const int r = rank_of(col);
+                        if ((unsigned)r >= (unsigned)rcount) return;
+                        if (s_aval[j] + b.d == vals[r]) atomicAdd(&sig[r], b.s);
+                    });
+                    __syncthreads();
+                }
+            }
+            for (int r = threadIdx.x; r < rcount; r += NT) {
+                if (fits) {
+                    c_col[o0 + rb + r] = scol[r];
+                    if constexpr (ALG == ALG_MULTPATH) {
+                        DSig o;
+                        o.d = vals[r];
+                        o.pad = 0;
+                        o.s = sig[r];
+                        cval[o0 + rb + r] = o;
+                        sig[r] = 0.0;
+                    } else {
+                        cval[o0 + rb + r] = T::out(vals[r]);
+                    }
+                }
+                vals[r] = T::empty();
+            }
+            __syncthreads();
+        }
+
+        // 4) clear the touched words
+        for (int c = threadIdx.x; c < ncell; c += NT) {
+            uint32_t s = summ[c];
+            summ[c] = 0u;
+            while (s) {
+                const int w = c * 32 + __ffs(s) - 1;
+                s &= s - 1;
+                bits[w] = 0u;
+            }
+        }
+    }
+}
+
 // ----------------------------------------------------------------- host side
 
 int64_t pow2_ceil(int64_t x) {
@@ -485,6 +896,26 @@ stc_status run_numeric(stc_handle* h, const SpgArgs& g, const int32_t* rowlist, 
     if (st != STC_OK) return st;
     if (int64_t(grid) > nA) grid = int(nA > 0 ? nA : 1);
     kern<<<grid, SP_NT, smem, s>>>(g, rowlist, nlist, counter, c_ptr, c_col, c_val, h->d_flags);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return STC_OK;
+}
+
+template <int ALG>
+stc_status run_numeric_rank(stc_handle* h, const SpgArgs& g, const int32_t* ctab, int vcap, int maxwin,
+                            const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
+                            int32_t* c_col, void* c_val, int64_t nA, stc_stream s) {
+    const int ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
+    const size_t smem = rank_layout(ncell, vcap, maxwin, sizeof(typename Tr<ALG>::Acc), ALG == ALG_MULTPATH).total;
+    auto kern = k_numeric_rank<ALG, RK_NT>;
+    STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int per_sm = 0;
+    STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_NT, smem));
+    if (per_sm < 1) return STC_ERR_CUDA;
+    int grid = per_sm * h->num_sms;
+    if (int64_t(grid) > nA) grid = int(nA > 0 ? nA : 1);
+    kern<<<grid, RK_NT, smem, s>>>(g, ctab, vcap, maxwin, rowlist, nlist, counter, c_ptr, c_col, c_val,
+                                   h->d_flags);
     STC_LAUNCH_CHECK();
     stc_count(h);
     return STC_OK;
@@ -537,6 +968,12 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
     g.b_col = B->col;
     g.b_val = B->val;
     g.woff = nullptr;
+    const bool trivial = nA == 0 || A->nnz == 0 || B->nnz == 0 || B->ncols == 0;
+    // rank-indexed kernels whenever the row bitmap fits shared memory, unless a
+    // column window width is forced (the window kernels then serve any width)
+    const bool rank_path = B->ncols <= RK_MAX_COLS && !(opts && opts->window_cols);
+    const int ncell = int((B->ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
+
     const int64_t ncp = pow2_ceil(B->ncols > 0 ? B->ncols : 1);
     int64_t W = numeric_window_max(alg);
     if (opts && opts->window_cols) W = opts->window_cols;
@@ -544,8 +981,25 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
     g.W = int(W);
     g.nwin = int((B->ncols + W - 1) / W);
     if (g.nwin < 1) g.nwin = 1;
-    const bool trivial = nA == 0 || A->nnz == 0 || B->nnz == 0 || B->ncols == 0;
-    if (numeric_smem_bytes(alg, g.W) > size_t(h->smem_optin) - 24 * 1024) return fail(STC_ERR_INVALID_ARG);
+    if (!rank_path && numeric_smem_bytes(alg, g.W) > size_t(h->smem_optin) - 24 * 1024)
+        return fail(STC_ERR_INVALID_ARG);
+
+    // value-buffer capacity of the rank kernel: two CTAs per SM
+    const size_t acc_bytes = alg == ALG_PT_F64 ? 8 : 4;
+    const size_t static_bytes = sizeof(TaskSmem<RK_NT>) + RK_NT * 8 + 256;
+    int vcap = 0, maxwin = 0;
+    if (rank_path) {
+        for (int v = 64 * 1024; v >= 2048; v -= 1024) {
+            int mw = int(B->ncols / (v - RK_CELL)) + 2;
+            RankLayout L = rank_layout(ncell, v, mw, acc_bytes, alg == ALG_MULTPATH);
+            if (L.total + static_bytes <= RK_SMEM_TARGET) {
+                vcap = v;
+                maxwin = mw;
+                break;
+            }
+        }
+        if (!vcap) return fail(STC_ERR_INVALID_ARG);
+    }
 
     {
         StcScratch sc(h, s);
@@ -565,7 +1019,8 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
             int* cursor = ints + NBINS;
             int* nlist = ints + 2 * NBINS;
             int* counters = ints + 2 * NBINS + 1;  // [0] symbolic, [1] numeric
-            if (g.nwin > 1) {
+            int* max_nnz = ints + 2 * NBINS + 4;
+            if (!rank_path && g.nwin > 1) {
                 int32_t* woff = sc.get<int32_t>(size_t(g.K) * size_t(g.nwin + 1));
                 if (!woff) return fail(STC_ERR_OOM);
                 g.woff = woff;
@@ -586,7 +1041,20 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
                 stc_count(h, 3);
             }
             stc_mark(h, s, 2);
-            {
+            if (rank_path) {
+                size_t smem = size_t(ncell) * 33 * 4;
+                int grid = 0;
+                auto kern = k_symbolic_rank<RK_SYM_NT>;
+                STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+                int per_sm = 0;
+                STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
+                if (per_sm < 1) return fail(STC_ERR_CUDA);
+                grid = per_sm * h->num_sms;
+                if (int64_t(grid) > nA) grid = int(nA);
+                kern<<<grid, RK_SYM_NT, smem, s>>>(g, rowlist, nlist, counters, c_ptr + 1, max_nnz);
+                if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+                stc_count(h);
+            } else {
                 size_t smem = size_t(Ws / 32) * 4;
                 int grid = 0;
                 auto kern = k_symbolic<SP_NT>;
@@ -602,17 +1070,22 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
             stc_mark(h, s, 2);
             stc_mark(h, s, 3);
         }
-        // the single synchronisation: nnz(C) and the validation flags
+        // the single synchronisation: nnz(C), the largest row and the validation flags
+        int* stage_i = reinterpret_cast<int*>(&h->h_stage[1]);
+        stage_i[0] = 0;
+        stage_i[1] = 0;
         if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + nA, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
-            cudaMemcpyAsync(&h->h_stage[1], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
+            cudaMemcpyAsync(&stage_i[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            (ints && cudaMemcpyAsync(&stage_i[1], ints + 2 * NBINS + 4, sizeof(int), cudaMemcpyDeviceToHost,
+                                     s) != cudaSuccess) ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             (void)cudaGetLastError();
             return fail(STC_ERR_CUDA);
         }
         const int64_t nnz = h->h_stage[0];
-        const int flags = int(reinterpret_cast<int*>(&h->h_stage[1])[0]);
+        const int flags = stage_i[0];
+        const int max_row = stage_i[1];
         if (flags) {
             (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
             return fail(stc_flags_to_status(flags));
@@ -621,18 +1094,41 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
         c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
         c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
         if (!c_col || !c_val) return fail(STC_ERR_OOM);
+        int32_t* ctab = nullptr;
+        if (!trivial && nnz > 0 && rank_path && max_row >= vcap - RK_CELL) {
+            ctab = sc.get<int32_t>(size_t(g.K) * size_t(ncell + 1));
+            if (!ctab) return fail(STC_ERR_OOM);
+            int64_t tot = g.K * (ncell + 1);
+            int64_t blocks = (tot + 255) / 256;
+            if (blocks > int64_t(h->num_sms) * 64) blocks = int64_t(h->num_sms) * 64;
+            k_cell_offsets<<<unsigned(blocks > 0 ? blocks : 1), 256, 0, s>>>(g, ncell, ctab);
+            if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+            stc_count(h);
+        }
         stc_mark(h, s, 4);
         if (!trivial && nnz > 0) {
             int* nlist = ints + 2 * NBINS;
             int* counters = ints + 2 * NBINS + 1;
-            switch (alg) {
-            case ALG_PT_F32: st = run_numeric<ALG_PT_F32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-            case ALG_PT_F64: st = run_numeric<ALG_PT_F64>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-            case ALG_MP_I32: st = run_numeric<ALG_MP_I32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-            case ALG_MP_F32: st = run_numeric<ALG_MP_F32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-            case ALG_BOOL: st = run_numeric<ALG_BOOL>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-            case ALG_MULTPATH: st = run_numeric<ALG_MULTPATH>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-            default: st = STC_ERR_ALGEBRA;
+            if (rank_path) {
+                switch (alg) {
+                case ALG_PT_F32: st = run_numeric_rank<ALG_PT_F32>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_PT_F64: st = run_numeric_rank<ALG_PT_F64>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_MP_I32: st = run_numeric_rank<ALG_MP_I32>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_MP_F32: st = run_numeric_rank<ALG_MP_F32>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_BOOL: st = run_numeric_rank<ALG_BOOL>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_MULTPATH: st = run_numeric_rank<ALG_MULTPATH>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                default: st = STC_ERR_ALGEBRA;
+                }
+            } else {
+                switch (alg) {
+                case ALG_PT_F32: st = run_numeric<ALG_PT_F32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_PT_F64: st = run_numeric<ALG_PT_F64>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_MP_I32: st = run_numeric<ALG_MP_I32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_MP_F32: st = run_numeric<ALG_MP_F32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_BOOL: st = run_numeric<ALG_BOOL>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                case ALG_MULTPATH: st = run_numeric<ALG_MULTPATH>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
+                default: st = STC_ERR_ALGEBRA;
+                }
             }
             if (st != STC_OK) return fail(st);
         }

@@ -27,16 +27,19 @@ def dsig_from_raw(raw: np.ndarray) -> np.ndarray:
 
 
 def compare_values(alg, got, ref, ref_abs=None, where=""):
-    """Elementwise comparison of one contraction's values against the oracle's."""
+    """Elementwise comparison of one contraction's values against the oracle's.
+
+    (+,x): |got - ref| <= tol * max(|ref|, sum of |products|).  On positive data the
+    two are equal (plain relative error); on signed data a cancelled sum is judged
+    against the magnitude of its terms, which is what bounds rounding error.
+    """
     if alg == O.PT_F64 or alg == O.PT_F32:
         tol = TOL_F64 if alg == O.PT_F64 else TOL_F32
         got = got.astype(np.float64)
         err = np.abs(got - ref)
-        bound = tol * np.abs(ref)
-        if ref_abs is not None:
-            bound = bound + 1e-2 * tol * ref_abs
-        bad = err > bound
-        assert not bad.any(), f"{where}: {bad.sum()} values off, worst rel {np.max(err / np.maximum(np.abs(ref), 1e-300))}"
+        scale = np.abs(ref) if ref_abs is None else np.maximum(np.abs(ref), ref_abs)
+        bad = err > tol * scale
+        assert not bad.any(), f"{where}: {bad.sum()} values off, worst {np.max(err / np.maximum(scale, 1e-300))}"
     elif alg == O.MULTPATH:
         g = dsig_from_raw(got)
         assert np.array_equal(g["d"], ref["d"]), where

@@ -89,6 +89,16 @@ def test_small_windows_multi_window_path(H, alg):
 
 
 @pytest.mark.parametrize("alg", ALL)
+def test_wide_rows_many_rank_windows(H, alg):
+    """Output rows with tens of thousands of entries: several rank windows per row."""
+    A = W.random_csr(150, 300, 300, seed=15, empty_frac=0.05)
+    B = W.random_csr(300, 60000, 400, seed=16)
+    A.val = vals(alg, A.nnz, 17, "A")
+    B.val = vals(alg, B.nnz, 18, "B")
+    check(H, alg, A, B)
+
+
+@pytest.mark.parametrize("alg", ALL)
 def test_rmat14_square(H, alg):
     """R-MAT scale 14: hub rows longer than one chunk of A, several windows."""
     A = W.rmat(14, seed=3)
