@@ -233,6 +233,36 @@ STC_API stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc_cs
                             int32_t persistent, stc_stream stream);
 
 /*
+ * Shortest distances and path counts from up to 256 sources at once: Bellman-Ford
+ * over the (distance, multiplicity) monoid of STC_MULTPATH_I32_F64 (the geodetic
+ * semiring that Section 4.2 names for betweenness centrality), with each vertex
+ * propagating only the multiplicity it gained since it last sent.
+ *
+ * G: out-edge CSR (row u lists u -> v); val = int32 lengths >= 1, or NULL for
+ * unit lengths.  sources: HOST array of nsources (1..256) vertex ids.
+ * d_out (device, int32 [G->nrows][nsources]) receives d_s(v) (INT_MAX/2 when v is
+ * unreachable from s); sigma_out (device, fp64 [G->nrows][nsources]) the number of
+ * shortest s-v paths (exact while below 2^53).  *rounds_out (host, may be NULL):
+ * rounds run.  Synchronises `stream` once per round.  Errors: argument/CSR
+ * errors, STC_ERR_INVALID_ARG for a length < 1.
+ */
+STC_API stc_status stc_mfbc_sssp(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources,
+                                 int32_t* d_out, double* sigma_out, int32_t* rounds_out, stc_stream stream);
+
+/*
+ * Betweenness centrality summed over the given sources (Brandes' dependency
+ * accumulation on the multiplicity-monoid shortest paths above):
+ *   bc_out[v] = sum over s in sources, s != v, of
+ *               sum over t of sigma_st(v) / sigma_st
+ * Directed; no normalisation or halving.  Sources are processed in batches of
+ * `batch` (1..256) columns at a time; device memory ~ 32 * G->nrows * batch bytes.
+ * G, sources and lengths as for stc_mfbc_sssp; bc_out: device fp64 [G->nrows],
+ * overwritten.  Synchronises `stream` once per round of each phase.
+ */
+STC_API stc_status stc_mfbc(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources,
+                            int32_t batch, double* bc_out, stc_stream stream);
+
+/*
  * Instrumentation (no counterpart in the paper, which reports only the share of
  * time spent in local kernels).
  *

@@ -108,6 +108,10 @@ def lib():
             L.stc_phase_times.restype = i32
             L.stc_kernel_launches.argtypes = [p]
             L.stc_kernel_launches.restype = i64
+            L.stc_mfbc_sssp.argtypes = [p, ctypes.POINTER(_Csr), p, i32, p, p, ctypes.POINTER(i32), p]
+            L.stc_mfbc_sssp.restype = ctypes.c_int
+            L.stc_mfbc.argtypes = [p, ctypes.POINTER(_Csr), p, i32, i32, p, p]
+            L.stc_mfbc.restype = ctypes.c_int
             L.stc_bellman_ford_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(_Csr), i32, p,
                                                    ctypes.POINTER(i32), p]
             L.stc_bellman_ford_noalloc.restype = ctypes.c_int
@@ -285,6 +289,31 @@ class Handle:
         _check(st, "stc_bellman_ford")
         self.last_relaxations = int(relax.value)
         return dist, int(rounds.value)
+
+    def mfbc_sssp(self, G: DeviceCsr, sources, stream=None):
+        """(d [n, S] int32, sigma [n, S] fp64, rounds) from up to 256 sources."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        S = int(src.size)
+        d = torch.empty((G.nrows, S), dtype=torch.int32, device=G.col.device)
+        sig = torch.empty((G.nrows, S), dtype=torch.float64, device=G.col.device)
+        rounds = ctypes.c_int32(0)
+        g = G._c()
+        st = lib().stc_mfbc_sssp(self._h, ctypes.byref(g), src.ctypes.data_as(ctypes.c_void_p), S,
+                                 d.data_ptr(), sig.data_ptr(), ctypes.byref(rounds), _stream_ptr(stream))
+        _check(st, "stc_mfbc_sssp")
+        return d, sig, int(rounds.value)
+
+    def mfbc(self, G: DeviceCsr, sources, batch: int = 256, bc: Optional[torch.Tensor] = None,
+             stream=None) -> torch.Tensor:
+        """Betweenness centrality summed over `sources` (host ids), batches of `batch`."""
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        if bc is None:
+            bc = torch.empty(G.nrows, dtype=torch.float64, device=G.col.device)
+        g = G._c()
+        st = lib().stc_mfbc(self._h, ctypes.byref(g), src.ctypes.data_as(ctypes.c_void_p), int(src.size),
+                            int(batch), bc.data_ptr(), _stream_ptr(stream))
+        _check(st, "stc_mfbc")
+        return bc
 
     # -------------------------------------------------------------- instrumentation
 

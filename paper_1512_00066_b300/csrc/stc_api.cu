@@ -35,6 +35,7 @@ stc_status stc_flags_to_status(int f) {
     if (f & STC_FLAG_TIMEOUT) return STC_ERR_TIMEOUT;
     if (f & STC_FLAG_NEG_CYCLE) return STC_ERR_NEG_CYCLE;
     if (f & STC_FLAG_INTERNAL) return STC_ERR_CUDA;
+    if (f & STC_FLAG_INVALID) return STC_ERR_INVALID_ARG;
     return STC_OK;
 }
 
@@ -350,4 +351,33 @@ extern "C" stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc
     if (source < 0 || source >= G->nrows) return STC_ERR_INVALID_ARG;
     return stc_bellman_ford_impl(h, alg, G, source, dist_out, rounds_out, relaxations_out, persistent,
                                  stream);
+}
+
+static stc_status mfbc_args(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources) {
+    if (!h || !sources || nsources <= 0 || !G) return STC_ERR_INVALID_ARG;
+    // val may be NULL here: unit lengths
+    stc_csr structure = *G;
+    if (!structure.val) structure.val = structure.col;
+    stc_status st = stc_check_csr_host(&structure);
+    if (st != STC_OK) return st;
+    if (G->nrows != G->ncols) return STC_ERR_SHAPE;
+    for (int32_t i = 0; i < nsources; ++i)
+        if (sources[i] < 0 || sources[i] >= G->nrows) return STC_ERR_INVALID_ARG;
+    return STC_OK;
+}
+
+extern "C" stc_status stc_mfbc_sssp(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources,
+                                    int32_t* d_out, double* sigma_out, int32_t* rounds_out, stc_stream stream) {
+    stc_status st = mfbc_args(h, G, sources, nsources);
+    if (st != STC_OK) return st;
+    if (nsources > 256 || !d_out || !sigma_out) return STC_ERR_INVALID_ARG;
+    return stc_mfbc_sssp_impl(h, G, sources, nsources, d_out, sigma_out, rounds_out, stream);
+}
+
+extern "C" stc_status stc_mfbc(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources,
+                               int32_t batch, double* bc_out, stc_stream stream) {
+    stc_status st = mfbc_args(h, G, sources, nsources);
+    if (st != STC_OK) return st;
+    if (batch < 1 || batch > 256 || !bc_out) return STC_ERR_INVALID_ARG;
+    return stc_mfbc_impl(h, G, sources, nsources, batch, bc_out, stream);
 }

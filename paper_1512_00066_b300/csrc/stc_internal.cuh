@@ -38,6 +38,7 @@ enum : int {
     STC_FLAG_TIMEOUT = 4,
     STC_FLAG_NEG_CYCLE = 8,
     STC_FLAG_INTERNAL = 16,
+    STC_FLAG_INVALID = 32,
 };
 
 stc_status stc_flags_to_status(int flags);
@@ -167,6 +168,11 @@ stc_status stc_spmm_impl(stc_handle* h, int alg, const stc_csr* A, const void* X
 stc_status stc_bellman_ford_impl(stc_handle* h, int alg, const stc_csr* G, int32_t source,
                                  void* dist, int32_t* rounds, int64_t* relaxations,
                                  int32_t persistent, stc_stream s);
+
+stc_status stc_mfbc_sssp_impl(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsrc,
+                              int32_t* d_out, double* sigma_out, int32_t* rounds_out, stc_stream s);
+stc_status stc_mfbc_impl(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsrc, int32_t batch,
+                         double* bc, stc_stream s);
 
 // Inclusive scan in place of n int64 values (device), using scratch from sc.
 stc_status stc_inclusive_scan_i64(stc_handle* h, StcScratch& sc, int64_t* data, int64_t n,

@@ -1,0 +1,120 @@
+"""GPU betweenness centrality (multiplicity-monoid shortest paths + Brandes
+accumulation) through the C ABI against the CPU oracle.
+
+Forward distances and path counts are exact integers (fp64 counts below 2^53) and
+must match bit for bit; centrality is held to relative 1e-12 (absolute 1e-9 on
+entries the oracle gives as exactly zero).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from gpu_util import need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+INF = O.TROP_I32_ID
+
+
+@pytest.fixture(scope="module")
+def H():
+    need_gpu()
+    import paper_1512_00066_b300 as stc
+    return stc.Handle()
+
+
+def graph(scale, seed, weighted):
+    G = W.rmat(scale, seed=seed)
+    G.val = W.weights_int(G.nnz, 1, 255, seed + 1) if weighted else None
+    return G
+
+
+def check_forward(H, G, sources, weighted):
+    d, sig, rounds = H.mfbc_sssp(to_dev(G), sources)
+    d = d.cpu().numpy()
+    sig = sig.cpu().numpy()
+    assert rounds >= 1
+    for j, s in enumerate(sources):
+        rd, rs = O.sssp_counts(G, int(s), weighted)
+        exp_d = np.where(rd < 0, INF, rd)
+        assert np.array_equal(d[:, j], exp_d), f"distances differ for source {s}"
+        assert np.array_equal(sig[:, j], rs), f"path counts differ for source {s}"
+
+
+def bc_close(got, ref):
+    assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-9 * (ref == 0))
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_forward_exact_rmat12(H, weighted):
+    G = graph(12, 3, weighted)
+    src = W.sample_sources(G, 37, seed=4)  # ragged: not a multiple of 32
+    check_forward(H, G, src, weighted)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("batch", [256, 96])
+def test_bc_matches_brandes_rmat12(H, weighted, batch):
+    G = graph(12, 5, weighted)
+    src = W.sample_sources(G, 300, seed=6)  # several batches, the last one partial
+    bc = H.mfbc(to_dev(G), src, batch=batch).cpu().numpy()
+    bc_close(bc, O.brandes(G, src, weighted))
+
+
+def test_bc_all_sources_small_and_closed_forms(H):
+    G = graph(9, 7, True)
+    allsrc = np.arange(G.nrows, dtype=np.int32)
+    bc = H.mfbc(to_dev(G), allsrc, batch=200).cpu().numpy()
+    bc_close(bc, O.brandes(G, allsrc, True))
+    m = 9  # star, both directions
+    rows = np.r_[np.zeros(m, int), np.arange(1, m + 1)]
+    cols = np.r_[np.arange(1, m + 1), np.zeros(m, int)]
+    S = W.csr_from_coo(rows, cols, m + 1, m + 1)
+    bc = H.mfbc(to_dev(S), np.arange(m + 1, dtype=np.int32)).cpu().numpy()
+    assert bc[0] == m * (m - 1) and np.all(bc[1:] == 0)
+    n = 12  # directed path
+    P = W.csr_from_coo(np.arange(n - 1), np.arange(1, n), n, n)
+    bc = H.mfbc(to_dev(P), np.arange(n, dtype=np.int32)).cpu().numpy()
+    assert np.array_equal(bc, np.array([v * (n - 1 - v) for v in range(n)], float))
+
+
+def test_equal_length_paths_multiply(H):
+    """A ladder of k diamonds has 2^k shortest paths end to end."""
+    k = 40
+    rows, cols = [], []
+    for i in range(k):
+        a, b, c, d = 3 * i, 3 * i + 1, 3 * i + 2, 3 * i + 3
+        rows += [a, a, b, c]
+        cols += [b, c, d, d]
+    n = 3 * k + 1
+    G = W.csr_from_coo(rows, cols, n, n)
+    G.val = np.full(G.nnz, 2, np.int32)
+    d, sig, _ = H.mfbc_sssp(to_dev(G), [0])
+    assert int(d[n - 1, 0]) == 4 * k and float(sig[n - 1, 0]) == 2.0 ** k
+
+
+def test_invalid_lengths_are_rejected(H):
+    import paper_1512_00066_b300 as stc
+    G = graph(8, 9, True)
+    G.val[5] = 0
+    with pytest.raises(stc.StcError) as e:
+        H.mfbc(to_dev(G), [0, 1])
+    assert e.value.status == 1
+    with pytest.raises(stc.StcError):
+        H.mfbc(to_dev(G), [G.nrows])  # source out of range (host check)
+
+
+def test_rmat22_full_size_forward_sampled(H):
+    """R-MAT scale 22, int32 lengths U[1,255], a 256-source batch: distances and
+    path counts of 4 of the sources against the oracle, element by element."""
+    G = graph(22, 0, True)
+    src = W.sample_sources(G, 256, seed=0)
+    d, sig, rounds = H.mfbc_sssp(to_dev(G), src)
+    for j in (0, 77, 150, 255):
+        rd, rs = O.sssp_counts(G, int(src[j]), True)
+        dj = d[:, j].cpu().numpy()
+        sj = sig[:, j].cpu().numpy()
+        assert np.array_equal(dj, np.where(rd < 0, INF, rd))
+        assert np.array_equal(sj, rs)

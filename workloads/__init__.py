@@ -59,6 +59,17 @@ def _rng(seed) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
+def sorted_unique(keys: np.ndarray) -> np.ndarray:
+    """Ascending distinct values (sort, then drop repeats)."""
+    k = np.sort(keys, kind="stable" if keys.size < 1024 else "quicksort")
+    if k.size == 0:
+        return k
+    keep = np.empty(k.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(k[1:], k[:-1], out=keep[1:])
+    return k[keep]
+
+
 def csr_from_sorted_keys(keys: np.ndarray, nrows: int, ncols: int) -> Csr:
     """Build a CSR structure from unique int64 keys row*ncols+col, sorted ascending."""
     rows = keys // ncols
@@ -77,7 +88,7 @@ def csr_from_coo(rows: np.ndarray, cols: np.ndarray, nrows: int, ncols: int,
     if drop_self_loops:
         keep = rows != cols
         rows, cols = rows[keep], cols[keep]
-    keys = np.unique(rows * ncols + cols)
+    keys = sorted_unique(rows * ncols + cols)
     return csr_from_sorted_keys(keys, nrows, ncols)
 
 
@@ -140,34 +151,46 @@ def random_csr(nrows: int, ncols: int, max_per_row: int, seed: int,
 
 
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
-         c: float = 0.19, seed: int = 0, chunk: int = 1 << 24) -> Csr:
+         c: float = 0.19, seed: int = 0, chunk: int = 1 << 23) -> Csr:
     """R-MAT digraph on 2^scale vertices with edge_factor * 2^scale draws.
 
     Each edge picks one quadrant per level (a: top-left, b: top-right,
-    c: bottom-left, d: bottom-right); the high bit is decided first.  No noise,
-    no label permutation (vertex 0 is the largest hub).  Self-loops and
-    duplicates are removed; the result is sorted by (row, col).
+    c: bottom-left, d: bottom-right); the high bit is decided first.  A level's
+    choice compares a 16-bit uniform integer with the cumulative probabilities
+    scaled to 2^16 (four levels per 64-bit random word).  No noise, no label
+    permutation (vertex 0 is the largest hub).  Self-loops and duplicates are
+    removed; the result is sorted by (row, col).
     """
     n = 1 << scale
     m = edge_factor * n
     rng = _rng(seed)
+    t_ab = np.uint64(round((a + b) * 65536))
+    t_a = np.uint64(round(a * 65536))
+    t_abc = np.uint64(round((a + b + c) * 65536))
+    mask = np.uint64(0xFFFF)
     keys_parts = []
-    ab = a + b
-    abc = a + b + c
+    nwords = (scale + 3) // 4
     for s in range(0, m, chunk):
         cnt = min(chunk, m - s)
-        u = np.zeros(cnt, dtype=np.int64)
-        v = np.zeros(cnt, dtype=np.int64)
-        for level in range(scale):
-            r = rng.random(cnt)
-            bit = np.int64(1) << np.int64(scale - 1 - level)
-            down = r >= ab                      # quadrants c or d: row bit set
-            right = ((r >= a) & (r < ab)) | (r >= abc)  # quadrants b or d: col bit set
-            u |= np.where(down, bit, 0)
-            v |= np.where(right, bit, 0)
+        u = np.zeros(cnt, dtype=np.uint64)
+        v = np.zeros(cnt, dtype=np.uint64)
+        level = 0
+        for _ in range(nwords):
+            word = rng.integers(0, 2 ** 64 - 1, size=cnt, dtype=np.uint64, endpoint=True)
+            for q in range(4):
+                if level == scale:
+                    break
+                r = (word >> np.uint64(16 * q)) & mask
+                down = r >= t_ab                        # quadrants c or d: row bit set
+                right = ((r >= t_a) & (r < t_ab)) | (r >= t_abc)  # quadrants b or d: col bit
+                sh = np.uint64(scale - 1 - level)
+                u |= down.astype(np.uint64) << sh
+                v |= right.astype(np.uint64) << sh
+                level += 1
         keep = u != v
-        keys_parts.append(np.unique(u[keep] * n + v[keep]))
-    keys = np.unique(np.concatenate(keys_parts))
+        uu = u[keep].astype(np.int64)
+        keys_parts.append(sorted_unique(uu * n + v[keep].astype(np.int64)))
+    keys = sorted_unique(np.concatenate(keys_parts))
     return csr_from_sorted_keys(keys, n, n)
 
 
