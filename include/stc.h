@@ -182,6 +182,24 @@ STC_API stc_status stc_contract_spgemm(stc_handle* h, stc_algebra alg, const stc
                                stc_csr* C, const stc_opts* opts, stc_stream stream);
 
 /*
+ * Batched SpGEMM: C_b = A_b (x) B_b for b < nbatch independent pairs (Section
+ * 3.3.1: an index shared by all three operands names independent problems), all
+ * rows of all pairs handled by the same persistent launches (one row work queue
+ * across the batch) and one synchronisation for the whole batch.
+ *
+ * A, B: HOST arrays of nbatch CSR descriptors (device pointers inside); every
+ * B_b has at most 2^18 columns.  C: HOST array of nbatch descriptors filled on
+ * success.  Their arrays are views into three allocations shared by the batch:
+ * C[0].rowptr, C[0].col and C[0].val are the allocation bases (release those
+ * three with stc_free); C[b].rowptr is row-pointer array b (starting at 0), and
+ * C[b].col / C[b].val point at matrix b's entries.  Errors as for
+ * stc_contract_spgemm; nbatch in 1..65535.
+ */
+STC_API stc_status stc_contract_spgemm_batched(stc_handle* h, stc_algebra alg, int32_t nbatch, const stc_csr* A,
+                                               const stc_csr* B, stc_csr* C, const stc_opts* opts,
+                                               stc_stream stream);
+
+/*
  * SpMM: Y = A (x) X, or Y = Y (+) (A (x) X) when accumulate != 0
  * (Section 3.3.1 contraction with a dense operand).
  *

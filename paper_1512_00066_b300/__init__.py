@@ -93,6 +93,10 @@ def lib():
             L.stc_contract_spgemm.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr),
                                               ctypes.POINTER(_Csr), ctypes.POINTER(_Opts), p]
             L.stc_contract_spgemm.restype = ctypes.c_int
+            L.stc_contract_spgemm_batched.argtypes = [p, ctypes.c_int, i32, ctypes.POINTER(_Csr),
+                                                      ctypes.POINTER(_Csr), ctypes.POINTER(_Csr),
+                                                      ctypes.POINTER(_Opts), p]
+            L.stc_contract_spgemm_batched.restype = ctypes.c_int
             L.stc_contract_spmm.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), p, i64, i32, p, i64, i32, p]
             L.stc_contract_spmm.restype = ctypes.c_int
             L.stc_contract_spmv.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), p, p, i32, p]
@@ -240,6 +244,37 @@ class Handle:
         else:
             val = raw.view(ct)[:nnz]
         return DeviceCsr(int(C.nrows), int(C.ncols), rowptr, col, val)
+
+    def spgemm_batched(self, alg: int, As, Bs, skip_validation: bool = False, stream=None):
+        """C_b = A_b (x) B_b for every pair, in one batched call (one synchronisation).
+
+        Returns a list of DeviceCsr whose tensors are views into three shared
+        allocations (row pointers, columns, values) owned by the first result.
+        """
+        nb = len(As)
+        assert nb == len(Bs) and nb > 0
+        A = (_Csr * nb)(*[a._c() for a in As])
+        B = (_Csr * nb)(*[b._c() for b in Bs])
+        C = (_Csr * nb)()
+        opts = _Opts(1 if skip_validation else 0, 0)
+        st = lib().stc_contract_spgemm_batched(self._h, alg, nb, A, B, C, ctypes.byref(opts), _stream_ptr(stream))
+        _check(st, "stc_contract_spgemm_batched")
+        rp = self._take(C[0].rowptr).view(torch.int64)
+        col = self._take(C[0].col).view(torch.int32)
+        raw = self._take(C[0].val)
+        ct = _DT[alg][2]
+        vb = DSIG_BYTES if ct == "dsig" else torch.empty(0, dtype=ct).element_size()
+        out = []
+        for b in range(nb):
+            r0 = (C[b].rowptr - C[0].rowptr) // 8
+            c0 = (C[b].col - C[0].col) // 4
+            nnz = int(C[b].nnz)
+            rowptr = rp[r0: r0 + int(C[b].nrows) + 1]
+            cols = col[c0: c0 + nnz]
+            v = raw[c0 * vb: (c0 + nnz) * vb]
+            val = v.view(nnz, DSIG_BYTES) if ct == "dsig" else v.view(ct)
+            out.append(DeviceCsr(int(C[b].nrows), int(C[b].ncols), rowptr, cols, val))
+        return out
 
     def spmm(self, alg: int, A: DeviceCsr, X: torch.Tensor, Y: Optional[torch.Tensor] = None,
              accumulate: bool = False, stream=None) -> torch.Tensor:

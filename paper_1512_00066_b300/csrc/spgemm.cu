@@ -39,7 +39,28 @@ struct SpgArgs {
     const int32_t* __restrict__ woff;  // [K][nwin+1] or null when nwin == 1
     int W;                             // numeric window width, power of two
     int nwin;                          // number of numeric windows
+    const int32_t* __restrict__ ctab;  // rank path: [K][ncell+1] per-cell offsets in B rows, or null
+    int ncell;                         // rank path: 1024-column cells of the output
 };
+
+// Rows of one matrix (table == null: `one`) or of a batch of independent
+// matrices whose rows are numbered consecutively (row_off[b] = first global row
+// of matrix b, row_off[nb] = total).
+struct SpgRows {
+    SpgArgs one;
+    const SpgArgs* __restrict__ table;
+    const int64_t* __restrict__ row_off;
+    int nb;
+};
+
+__device__ __forceinline__ int batch_of(const SpgRows& R, int64_t gi) {
+    int lo = 0, hi = R.nb - 1;  // last b with row_off[b] <= gi
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (R.row_off[mid] <= gi) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // ----------------------------------------------------------------- algebra traits
 
@@ -594,24 +615,52 @@ __device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t* summ, int col)
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, 4)
-k_symbolic_rank(SpgArgs g, const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
+// Persistent-CTA row loop over a row list of global rows: thread 0 resolves the
+// row's matrix into shared memory.  Returns the global row or -1.
+__device__ __forceinline__ int64_t next_row_b(int* counter, int nlist, const int32_t* rowlist, const SpgRows& R,
+                                              SpgArgs* s_args, int64_t* s_row) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int r = atomicAdd(counter, 1);
+        const int64_t gi = r < nlist ? rowlist[r] : -1;
+        int64_t li = gi;
+        if (gi >= 0) {
+            if (R.table) {
+                const int b = batch_of(R, gi);
+                *s_args = R.table[b];
+                li = gi - R.row_off[b];
+            } else {
+                *s_args = R.one;
+            }
+        }
+        s_row[0] = gi;
+        s_row[1] = li;
+    }
+    __syncthreads();
+    return s_row[0];
+}
+
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                 int* __restrict__ counter, int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz) {
     extern __shared__ uint4 smem_raw[];
-    const int ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
-    const int NW = ncell * 32;
+    const int NWmax = ncell_max * 32;
     uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw);
-    uint32_t* summ = bits + NW;  // one summary word per cell
+    uint32_t* summ = bits + NWmax;  // one summary word per cell
     __shared__ TaskSmem<NT> ts;
-    __shared__ int s_row;
+    __shared__ SpgArgs s_args;
+    __shared__ int64_t s_row[2];
     __shared__ int s_red[NT / 32 + 1];
-    for (int w = threadIdx.x; w < NW + ncell; w += NT) bits[w] = 0u;
+    for (int w = threadIdx.x; w < NWmax + ncell_max; w += NT) bits[w] = 0u;
     const int nlist = *nlist_ptr;
     int local_max = 0;
     for (;;) {
-        const int i = next_row(counter, nlist, rowlist, &s_row);
-        if (i < 0) break;
+        const int64_t gi = next_row_b(counter, nlist, rowlist, R, &s_args, s_row);
+        if (gi < 0) break;
+        const SpgArgs& g = s_args;
+        const int64_t i = s_row[1];
+        const int NW = g.ncell * 32;
         int64_t alo, ahi;
         row_range(g.a_ptr, i, g.nnzA, alo, ahi);
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
@@ -629,20 +678,24 @@ k_symbolic_rank(SpgArgs g, const int32_t* __restrict__ rowlist, const int* __res
                 bits[w] = 0u;
             }
         }
-        for (int c = threadIdx.x; c < ncell; c += NT) summ[c] = 0u;
+        for (int c = threadIdx.x; c < g.ncell; c += NT) summ[c] = 0u;
         int tot;
         (void)block_exclusive_scan<NT, int>(cnt, s_red, tot);
         if (threadIdx.x == 0) {
-            row_nnz[i] = tot;
+            row_nnz[gi] = tot;
             local_max = max(local_max, tot);
         }
     }
     if (threadIdx.x == 0 && local_max) atomicMax(max_nnz, local_max);
 }
 
-// ctab[k*(ncell+1) + c] = number of entries of B_k with column < c * RK_CELL.
-__global__ void k_cell_offsets(SpgArgs g, int ncell, int32_t* __restrict__ ctab) {
-    const int64_t stride = int64_t(ncell) + 1;
+// ctab[k*(ncell+1) + c] = number of entries of B_k with column < c * RK_CELL, for
+// matrix blockIdx.y of the batch (or the single matrix).
+__global__ void k_cell_offsets(SpgRows R) {
+    const SpgArgs g = R.table ? R.table[blockIdx.y] : R.one;
+    int32_t* ctab = const_cast<int32_t*>(g.ctab);
+    if (!ctab) return;
+    const int64_t stride = int64_t(g.ncell) + 1;
     const int64_t total = g.K * stride;
     for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
          idx += int64_t(gridDim.x) * blockDim.x) {
@@ -658,6 +711,68 @@ __global__ void k_cell_offsets(SpgArgs g, int ncell, int32_t* __restrict__ ctab)
         }
         ctab[idx] = int32_t(a - lo);
     }
+}
+
+// Row analysis over global rows (batch-aware): ub and log2 bins.
+__global__ void k_row_ub_b(SpgRows R, int64_t NR, int64_t* __restrict__ ub, int* __restrict__ bin_count) {
+    __shared__ int s_bins[NBINS];
+    for (int t = threadIdx.x; t < NBINS; t += blockDim.x) s_bins[t] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t gi = warp; gi < NR; gi += nwarps) {
+        SpgArgs g;
+        int64_t i = gi;
+        if (R.table) {
+            const int b = batch_of(R, gi);
+            g = R.table[b];
+            i = gi - R.row_off[b];
+        } else {
+            g = R.one;
+        }
+        int64_t lo, hi;
+        row_range(g.a_ptr, i, g.nnzA, lo, hi);
+        int64_t sum = 0;
+        for (int64_t p = lo + lane; p < hi; p += 32) {
+            const int32_t k = g.a_col[p];
+            if ((uint64_t)k < (uint64_t)g.K) {
+                int64_t bl, bh;
+                row_range(g.b_ptr, k, g.nnzB, bl, bh);
+                sum += bh - bl;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+        if (lane == 0) {
+            ub[gi] = sum;
+            atomicAdd(&s_bins[bin_of(sum)], 1);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NBINS; t += blockDim.x)
+        if (s_bins[t]) atomicAdd(&bin_count[t], s_bins[t]);
+}
+
+// Per-batch row pointers: rp[row_off[b] + b + i] = c_ptr[row_off[b] + i] - c_ptr[row_off[b]].
+__global__ void k_rebase_rowptr(SpgRows R, const int64_t* __restrict__ c_ptr, int64_t* __restrict__ rp) {
+    const int64_t total = R.row_off[R.nb] + R.nb;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = R.nb - 1;  // last b with row_off[b] + b <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (R.row_off[mid] + mid <= e) lo = mid; else hi = mid - 1;
+        }
+        const int64_t i = e - (R.row_off[lo] + lo);
+        rp[e] = c_ptr[R.row_off[lo] + i] - c_ptr[R.row_off[lo]];
+    }
+}
+
+// c_ptr at the first row of every matrix of the batch (and the total).
+__global__ void k_batch_bounds(SpgRows R, const int64_t* __restrict__ c_ptr, int64_t* __restrict__ out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= R.nb; b += gridDim.x * blockDim.x)
+        out[b] = c_ptr[R.row_off[b]];
 }
 
 struct RankLayout {
@@ -682,9 +797,9 @@ __host__ __device__ inline RankLayout rank_layout(int ncell, int vcap, int maxwi
     return L;
 }
 
-template <int ALG, int NT>
-__global__ void __launch_bounds__(NT, 1)
-k_numeric_rank(SpgArgs g, const int32_t* __restrict__ ctab, int vcap, int maxwin,
+template <int ALG, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                int* __restrict__ counter, const int64_t* __restrict__ c_ptr, int32_t* __restrict__ c_col,
                void* __restrict__ c_val, int* __restrict__ flags) {
@@ -694,9 +809,7 @@ k_numeric_rank(SpgArgs g, const int32_t* __restrict__ ctab, int vcap, int maxwin
     using Acc = typename T::Acc;
     extern __shared__ uint4 smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
-    const int ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
-    const int NW = ncell * 32;
-    const RankLayout L = rank_layout(ncell, vcap, maxwin, sizeof(Acc), ALG == ALG_MULTPATH);
+    const RankLayout L = rank_layout(ncell_max, vcap, maxwin, sizeof(Acc), ALG == ALG_MULTPATH);
     uint32_t* bits = reinterpret_cast<uint32_t*>(sm + L.bits);
     uint32_t* summ = reinterpret_cast<uint32_t*>(sm + L.summ);
     uint16_t* wpre = reinterpret_cast<uint16_t*>(sm + L.wpre);
@@ -707,28 +820,32 @@ k_numeric_rank(SpgArgs g, const int32_t* __restrict__ ctab, int vcap, int maxwin
     double* sig = reinterpret_cast<double*>(sm + L.sig);
     __shared__ TaskSmem<NT> ts;
     __shared__ AT s_aval[NT];
-    __shared__ int s_row;
+    __shared__ SpgArgs s_args;
+    __shared__ int64_t s_row[2];
     __shared__ int s_warp[NT / 32 + 1];
     __shared__ int s_nwin;
 
-    for (int w = threadIdx.x; w < NW; w += NT) bits[w] = 0u;
-    for (int c = threadIdx.x; c < ncell; c += NT) summ[c] = 0u;
+    for (int w = threadIdx.x; w < ncell_max * 32; w += NT) bits[w] = 0u;
+    for (int c = threadIdx.x; c < ncell_max; c += NT) summ[c] = 0u;
     for (int r = threadIdx.x; r < vcap; r += NT) {
         vals[r] = T::empty();
         if constexpr (ALG == ALG_MULTPATH) sig[r] = 0.0;
     }
     const int nlist = *nlist_ptr;
     const int vstep = vcap - RK_CELL;  // rank span that starts a new window
-    const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
     auto* cval = static_cast<typename T::C*>(c_val);
 
     for (;;) {
-        const int i = next_row(counter, nlist, rowlist, &s_row);
-        if (i < 0) break;
+        const int64_t gi = next_row_b(counter, nlist, rowlist, R, &s_args, s_row);
+        if (gi < 0) break;
+        const SpgArgs& g = s_args;
+        const int64_t i = s_row[1];
+        const int ncell = g.ncell;
+        const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
         int64_t alo, ahi;
         row_range(g.a_ptr, i, g.nnzA, alo, ahi);
-        const int64_t o0 = c_ptr[i];
-        const int64_t o1 = c_ptr[i + 1];
+        const int64_t o0 = c_ptr[gi];
+        const int64_t o1 = c_ptr[gi + 1];
 
         // 1) bitmap of the row's columns
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
@@ -740,7 +857,7 @@ k_numeric_rank(SpgArgs g, const int32_t* __restrict__ ctab, int vcap, int maxwin
         }
 
         // 2) ranks: word prefix inside each cell, cell prefix, windows; columns of C
-        constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;  // cells per thread
+        constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;  // cells per thread (upper bound)
         int cnt[CPT];
         int ctot = 0;
 #pragma unroll
@@ -790,7 +907,7 @@ k_numeric_rank(SpgArgs g, const int32_t* __restrict__ ctab, int vcap, int maxwin
             const int cl = winfirst[wdw], ch = winfirst[wdw + 1];
             const int rb = cellbase[cl];
             const int rcount = cellbase[ch] - rb;
-            const int32_t* tab = nwin > 1 ? ctab : nullptr;
+            const int32_t* tab = nwin > 1 ? g.ctab : nullptr;
             auto rank_of = [&](int col) -> int {
                 const int w = col >> 5;
                 return cellbase[col >> RK_CELL_SHIFT] + wpre[w] +
@@ -870,7 +987,7 @@ int numeric_window_max(int alg) {
 }
 
 size_t numeric_smem_bytes(int alg, int W) {
-    size_t acc = (alg == ALG_PT_F32 || alg == ALG_PT_F64) ? 8 : 4;
+    size_t acc = alg == ALG_PT_F64 ? 8 : 4;
     size_t per = acc + (alg == ALG_MULTPATH ? 8 : 0);
     return per * size_t(W) + size_t(W / 32) * 4;
 }
@@ -901,39 +1018,318 @@ stc_status run_numeric(stc_handle* h, const SpgArgs& g, const int32_t* rowlist, 
     return STC_OK;
 }
 
-template <int ALG>
-stc_status run_numeric_rank(stc_handle* h, const SpgArgs& g, const int32_t* ctab, int vcap, int maxwin,
-                            const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
-                            int32_t* c_col, void* c_val, int64_t nA, stc_stream s) {
-    const int ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
-    const size_t smem = rank_layout(ncell, vcap, maxwin, sizeof(typename Tr<ALG>::Acc), ALG == ALG_MULTPATH).total;
-    auto kern = k_numeric_rank<ALG, RK_NT>;
-    STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+// Launch configuration of the rank kernels: narrow outputs (at most 16384
+// columns, e.g. many small matrices) use small CTAs so that many rows are in
+// flight per SM; wide outputs use one 1024-thread CTA per SM and a large value
+// buffer (fewer rank windows per row).
+struct RankCfg {
+    bool small;
+    int vcap, maxwin;
+    size_t smem;
+};
+
+template <int ALG, int NT, int MINB>
+stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
+                               const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
+                               int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+    auto kern = k_numeric_rank<ALG, NT, MINB>;
+    STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)));
     int per_sm = 0;
-    STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_NT, smem));
+    STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, cfg.smem));
     if (per_sm < 1) return STC_ERR_CUDA;
-    int grid = per_sm * h->num_sms;
-    if (int64_t(grid) > nA) grid = int(nA > 0 ? nA : 1);
-    kern<<<grid, RK_NT, smem, s>>>(g, ctab, vcap, maxwin, rowlist, nlist, counter, c_ptr, c_col, c_val,
-                                   h->d_flags);
+    int64_t grid = int64_t(per_sm) * h->num_sms;
+    if (grid > NR) grid = NR > 0 ? NR : 1;
+    kern<<<unsigned(grid), NT, cfg.smem, s>>>(R, ncell_max, cfg.vcap, cfg.maxwin, rowlist, nlist, counter, c_ptr,
+                                              c_col, c_val, h->d_flags);
     STC_LAUNCH_CHECK();
     stc_count(h);
     return STC_OK;
 }
 
+template <int ALG>
+stc_status run_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
+                            const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
+                            int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+    if (cfg.small)
+        return launch_numeric_rank<ALG, 256, 4>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val,
+                                                NR, s);
+    return launch_numeric_rank<ALG, RK_NT, 1>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val,
+                                              NR, s);
+}
+
+RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max) {
+    RankCfg c{};
+    const size_t acc_bytes = alg == ALG_PT_F64 ? 8 : 4;
+    const bool mp = alg == ALG_MULTPATH;
+    c.small = ncols_max <= 16384;
+    const int nt = c.small ? 256 : RK_NT;
+    const size_t target = c.small ? 54 * 1024 : RK_SMEM_TARGET;  // four / one CTA per SM
+    const size_t static_bytes = size_t(nt) * 16 + size_t(nt) * 8 + 512 + sizeof(SpgArgs);
+    for (int v = 64 * 1024; v >= 2048; v -= 1024) {
+        const int mw = int(ncols_max / (v - RK_CELL)) + 2;
+        RankLayout L = rank_layout(ncell_max, v, mw, acc_bytes, mp);
+        if (L.total + static_bytes <= target) {
+            c.vcap = v;
+            c.maxwin = mw;
+            c.smem = L.total;
+            return c;
+        }
+    }
+    return c;
+}
+
+// The rank path over nb matrices (nb == 1: a single SpGEMM).  Produces the
+// global row pointers (NR + 1), columns and values; *bounds_h (host, nb + 1)
+// receives the output offset of every matrix's first row.
+stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_h, const int64_t* row_off_h,
+                            bool validate, const stc_csr* Av, const stc_csr* Bv, int64_t** c_ptr_out,
+                            int32_t** c_col_out, void** c_val_out, int64_t* nnz_out, int64_t* bounds_h,
+                            stc_stream s) {
+    *c_ptr_out = nullptr;
+    *c_col_out = nullptr;
+    *c_val_out = nullptr;
+    *nnz_out = 0;
+    const int64_t NR = row_off_h[nb];
+    const size_t vbytes = stc_val_bytes(alg, 'C');
+    int64_t ncols_max = 0;
+    for (int b = 0; b < nb; ++b) ncols_max = args_h[b].ncols > ncols_max ? args_h[b].ncols : ncols_max;
+    const int ncell_max = int((ncols_max + RK_CELL - 1) >> RK_CELL_SHIFT) > 0
+                              ? int((ncols_max + RK_CELL - 1) >> RK_CELL_SHIFT) : 1;
+    const RankCfg cfg = rank_config(alg, ncols_max, ncell_max);
+    if (!cfg.vcap) return STC_ERR_INVALID_ARG;
+
+    int64_t* c_ptr = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(NR + 1) * 8, s));
+    if (!c_ptr) return STC_ERR_OOM;
+    int32_t* c_col = nullptr;
+    void* c_val = nullptr;
+    auto fail = [&](stc_status st) {
+        stc_free_bytes(h, c_ptr, s);
+        if (c_col) stc_free_bytes(h, c_col, s);
+        if (c_val) stc_free_bytes(h, c_val, s);
+        return st;
+    };
+    StcScratch sc(h, s);
+    stc_mark(h, s, 0);
+    if (cudaMemsetAsync(c_ptr, 0, size_t(NR + 1) * 8, s) != cudaSuccess) return fail(STC_ERR_CUDA);
+    stc_status st;
+    if (validate) {
+        if ((st = stc_validate_many_async(h, sc, Av, nb, s)) != STC_OK) return fail(st);
+        if ((st = stc_validate_many_async(h, sc, Bv, nb, s)) != STC_OK) return fail(st);
+    }
+    stc_mark(h, s, 1);
+
+    SpgRows R{};
+    R.nb = nb;
+    SpgArgs* table_d = nullptr;
+    if (nb == 1) {
+        R.one = args_h[0];
+    } else {
+        table_d = sc.get<SpgArgs>(size_t(nb));
+        int64_t* roff_d = sc.get<int64_t>(size_t(nb) + 1);
+        if (sc.failed) return fail(STC_ERR_OOM);
+        if (cudaMemcpyAsync(table_d, args_h, sizeof(SpgArgs) * nb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(roff_d, row_off_h, sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(STC_ERR_CUDA);
+        R.table = table_d;
+        R.row_off = roff_d;
+    }
+    int64_t* ub = sc.get<int64_t>(size_t(NR));
+    int32_t* rowlist = sc.get<int32_t>(size_t(NR));
+    int* ints = sc.get<int>(2 * NBINS + 8);
+    int64_t* bounds_d = sc.get<int64_t>(size_t(nb) + 1);
+    if (sc.failed) return fail(STC_ERR_OOM);
+    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS + 8), s) != cudaSuccess) return fail(STC_ERR_CUDA);
+    int* bin_count = ints;
+    int* cursor = ints + NBINS;
+    int* nlist = ints + 2 * NBINS;
+    int* counters = ints + 2 * NBINS + 1;  // [0] symbolic, [1] numeric
+    int* max_nnz = ints + 2 * NBINS + 4;
+    if (NR > 0) {
+        int64_t blocks = (NR * 32 + 255) / 256;
+        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count);
+        k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, cursor, rowlist);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h, 3);
+    }
+    stc_mark(h, s, 2);
+    if (NR > 0) {
+        const size_t smem = size_t(ncell_max) * 33 * 4;
+        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        int per_sm = 0;
+        STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
+        if (per_sm < 1) return fail(STC_ERR_CUDA);
+        int64_t grid = int64_t(per_sm) * h->num_sms;
+        if (grid > NR) grid = NR;
+        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell_max, rowlist, nlist, counters, c_ptr + 1, max_nnz);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+    }
+    stc_mark(h, s, 3);
+    if ((st = stc_inclusive_scan_i64(h, sc, c_ptr + 1, NR, s)) != STC_OK) return fail(st);
+    if (nb > 1) {
+        k_batch_bounds<<<unsigned((nb + 256) / 256), 256, 0, s>>>(R, c_ptr, bounds_d);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+    }
+    // the single synchronisation: nnz, the largest row, the validation flags (and batch bounds)
+    int* stage_i = reinterpret_cast<int*>(&h->h_stage[1]);
+    stage_i[0] = 0;
+    stage_i[1] = 0;
+    if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&stage_i[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&stage_i[1], max_nnz, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        (nb > 1 && cudaMemcpyAsync(bounds_h, bounds_d, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToHost, s) !=
+                       cudaSuccess) ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(STC_ERR_CUDA);
+    }
+    const int64_t nnz = h->h_stage[0];
+    const int flags = stage_i[0];
+    const int max_row = stage_i[1];
+    if (nb == 1) {
+        bounds_h[0] = 0;
+        bounds_h[1] = nnz;
+    }
+    if (flags) {
+        (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
+        return fail(stc_flags_to_status(flags));
+    }
+    if (nnz < 0) return fail(STC_ERR_CUDA);
+    c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
+    c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
+    if (!c_col || !c_val) return fail(STC_ERR_OOM);
+
+    // per-cell offset tables, only when some row needs several rank windows
+    if (nnz > 0 && max_row >= cfg.vcap - RK_CELL) {
+        std::vector<SpgArgs> args(args_h, args_h + nb);
+        size_t tot = 0;
+        std::vector<size_t> off(nb);
+        int64_t kmax = 0;
+        for (int b = 0; b < nb; ++b) {
+            off[b] = tot;
+            tot += size_t(args[b].K) * size_t(args[b].ncell + 1);
+            kmax = args[b].K * (args[b].ncell + 1) > kmax ? args[b].K * (args[b].ncell + 1) : kmax;
+        }
+        int32_t* ctab = sc.get<int32_t>(tot);
+        if (!ctab) return fail(STC_ERR_OOM);
+        for (int b = 0; b < nb; ++b) args[b].ctab = ctab + off[b];
+        if (nb == 1) {
+            R.one = args[0];
+        } else if (cudaMemcpyAsync(table_d, args.data(), sizeof(SpgArgs) * nb, cudaMemcpyHostToDevice, s) !=
+                   cudaSuccess) {
+            return fail(STC_ERR_CUDA);
+        }
+        int64_t bx = (kmax + 255) / 256;
+        const int64_t cap = nb == 1 ? int64_t(h->num_sms) * 64 : 64;
+        if (bx > cap) bx = cap;
+        if (bx < 1) bx = 1;
+        k_cell_offsets<<<dim3(unsigned(bx), unsigned(nb)), 256, 0, s>>>(R);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+        if (nb > 1 && cudaStreamSynchronize(s) != cudaSuccess) return fail(STC_ERR_CUDA);  // args vector lifetime
+    }
+    stc_mark(h, s, 4);
+    if (nnz > 0) {
+        int* counter = counters + 1;
+        switch (alg) {
+        case ALG_PT_F32: st = run_numeric_rank<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
+        case ALG_PT_F64: st = run_numeric_rank<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
+        case ALG_MP_I32: st = run_numeric_rank<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
+        case ALG_MP_F32: st = run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
+        case ALG_BOOL: st = run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
+        case ALG_MULTPATH: st = run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
+        default: st = STC_ERR_ALGEBRA;
+        }
+        if (st != STC_OK) return fail(st);
+    }
+    stc_mark(h, s, 5);
+    if (nb > 1) {
+        // per-matrix row pointers that start at zero
+        int64_t* rp = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(NR + nb) * 8, s));
+        if (!rp) return fail(STC_ERR_OOM);
+        int64_t blocks = (NR + nb + 255) / 256;
+        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+        k_rebase_rowptr<<<unsigned(blocks), 256, 0, s>>>(R, c_ptr, rp);
+        if (cudaGetLastError() != cudaSuccess) {
+            stc_free_bytes(h, rp, s);
+            return fail(STC_ERR_CUDA);
+        }
+        stc_count(h);
+        stc_free_bytes(h, c_ptr, s);
+        c_ptr = rp;
+    }
+    *c_ptr_out = c_ptr;
+    *c_col_out = c_col;
+    *c_val_out = c_val;
+    *nnz_out = nnz;
+    return STC_OK;
+}
+
+SpgArgs make_args(const stc_csr* A, const stc_csr* B) {
+    SpgArgs g{};
+    g.nA = A->nrows;
+    g.K = A->ncols;
+    g.ncols = B->ncols;
+    g.nnzA = A->nnz;
+    g.nnzB = B->nnz;
+    g.a_ptr = A->rowptr;
+    g.a_col = A->col;
+    g.a_val = A->val;
+    g.b_ptr = B->rowptr;
+    g.b_col = B->col;
+    g.b_val = B->val;
+    g.woff = nullptr;
+    g.W = 0;
+    g.nwin = 1;
+    g.ctab = nullptr;
+    g.ncell = int((B->ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
+    return g;
+}
+
 }  // namespace
 
-stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
-                           const stc_opts* opts, stc_stream s) {
-    C->nrows = A->nrows;
-    C->ncols = B->ncols;
-    C->nnz = 0;
-    C->rowptr = nullptr;
-    C->col = nullptr;
-    C->val = nullptr;
+stc_status stc_spgemm_batched_impl(stc_handle* h, int alg, int nb, const stc_csr* A, const stc_csr* B,
+                                   stc_csr* C, const stc_opts* opts, stc_stream s) {
+    std::vector<SpgArgs> args(nb);
+    std::vector<int64_t> row_off(size_t(nb) + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        args[b] = make_args(&A[b], &B[b]);
+        row_off[b + 1] = row_off[b] + A[b].nrows;
+        C[b].nrows = A[b].nrows;
+        C[b].ncols = B[b].ncols;
+        C[b].nnz = 0;
+        C[b].rowptr = nullptr;
+        C[b].col = nullptr;
+        C[b].val = nullptr;
+    }
+    std::vector<int64_t> bounds(size_t(nb) + 1, 0);
+    int64_t* c_ptr = nullptr;
+    int32_t* c_col = nullptr;
+    void* c_val = nullptr;
+    int64_t nnz = 0;
+    stc_status st = spgemm_rank_impl(h, alg, nb, args.data(), row_off.data(), !(opts && opts->skip_validation),
+                                     A, B, &c_ptr, &c_col, &c_val, &nnz, bounds.data(), s);
+    if (st != STC_OK) return st;
+    const size_t vbytes = stc_val_bytes(alg, 'C');
+    for (int b = 0; b < nb; ++b) {
+        C[b].rowptr = c_ptr + row_off[b] + b;
+        C[b].col = c_col + bounds[b];
+        C[b].val = static_cast<char*>(c_val) + size_t(bounds[b]) * vbytes;
+        C[b].nnz = bounds[b + 1] - bounds[b];
+    }
+    return STC_OK;
+}
+
+// Column-window path: any output width (the dense window accumulator of W
+// columns is walked once per window, with the per-window offset table of B rows).
+static stc_status spgemm_window_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
+                                     const stc_opts* opts, stc_stream s) {
     const int64_t nA = A->nrows;
     const size_t vbytes = stc_val_bytes(alg, 'C');
-
     int64_t* c_ptr = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(nA + 1) * 8, s));
     if (!c_ptr) return STC_ERR_OOM;
     int32_t* c_col = nullptr;
@@ -946,34 +1342,14 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
     };
     stc_mark(h, s, 0);
     if (cudaMemsetAsync(c_ptr, 0, size_t(nA + 1) * 8, s) != cudaSuccess) return fail(STC_ERR_CUDA);
-
-    const bool validate = !(opts && opts->skip_validation);
     stc_status st;
-    if (validate) {
+    if (!(opts && opts->skip_validation)) {
         if ((st = stc_validate_csr_async(h, A, s)) != STC_OK) return fail(st);
         if ((st = stc_validate_csr_async(h, B, s)) != STC_OK) return fail(st);
     }
     stc_mark(h, s, 1);
-
-    SpgArgs g;
-    g.nA = nA;
-    g.K = A->ncols;
-    g.ncols = B->ncols;
-    g.nnzA = A->nnz;
-    g.nnzB = B->nnz;
-    g.a_ptr = A->rowptr;
-    g.a_col = A->col;
-    g.a_val = A->val;
-    g.b_ptr = B->rowptr;
-    g.b_col = B->col;
-    g.b_val = B->val;
-    g.woff = nullptr;
+    SpgArgs g = make_args(A, B);
     const bool trivial = nA == 0 || A->nnz == 0 || B->nnz == 0 || B->ncols == 0;
-    // rank-indexed kernels whenever the row bitmap fits shared memory, unless a
-    // column window width is forced (the window kernels then serve any width)
-    const bool rank_path = B->ncols <= RK_MAX_COLS && !(opts && opts->window_cols);
-    const int ncell = int((B->ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
-
     const int64_t ncp = pow2_ceil(B->ncols > 0 ? B->ncols : 1);
     int64_t W = numeric_window_max(alg);
     if (opts && opts->window_cols) W = opts->window_cols;
@@ -981,162 +1357,123 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
     g.W = int(W);
     g.nwin = int((B->ncols + W - 1) / W);
     if (g.nwin < 1) g.nwin = 1;
-    if (!rank_path && numeric_smem_bytes(alg, g.W) > size_t(h->smem_optin) - 24 * 1024)
-        return fail(STC_ERR_INVALID_ARG);
-
-    // value-buffer capacity of the rank kernel: two CTAs per SM
-    const size_t acc_bytes = alg == ALG_PT_F64 ? 8 : 4;
-    const size_t static_bytes = sizeof(TaskSmem<RK_NT>) + RK_NT * 8 + 256;
-    int vcap = 0, maxwin = 0;
-    if (rank_path) {
-        for (int v = 64 * 1024; v >= 2048; v -= 1024) {
-            int mw = int(B->ncols / (v - RK_CELL)) + 2;
-            RankLayout L = rank_layout(ncell, v, mw, acc_bytes, alg == ALG_MULTPATH);
-            if (L.total + static_bytes <= RK_SMEM_TARGET) {
-                vcap = v;
-                maxwin = mw;
-                break;
-            }
-        }
-        if (!vcap) return fail(STC_ERR_INVALID_ARG);
-    }
-
-    {
-        StcScratch sc(h, s);
-        int32_t* rowlist = nullptr;
-        int* ints = nullptr;
-        if (!trivial) {
-            int64_t Ws = ncp < SYM_MAX_COLS ? ncp : SYM_MAX_COLS;
-            if (Ws < W) Ws = W;
-            const int R = int(Ws / W);
-            int64_t* ub = sc.get<int64_t>(size_t(nA));
-            rowlist = sc.get<int32_t>(size_t(nA));
-            ints = sc.get<int>(2 * NBINS + 8);
-            if (sc.failed) return fail(STC_ERR_OOM);
-            if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS + 8), s) != cudaSuccess)
-                return fail(STC_ERR_CUDA);
-            int* bin_count = ints;
-            int* cursor = ints + NBINS;
-            int* nlist = ints + 2 * NBINS;
-            int* counters = ints + 2 * NBINS + 1;  // [0] symbolic, [1] numeric
-            int* max_nnz = ints + 2 * NBINS + 4;
-            if (!rank_path && g.nwin > 1) {
-                int32_t* woff = sc.get<int32_t>(size_t(g.K) * size_t(g.nwin + 1));
-                if (!woff) return fail(STC_ERR_OOM);
-                g.woff = woff;
-                int64_t tot = g.K * (g.nwin + 1);
-                int64_t blocks = (tot + 255) / 256;
-                if (blocks > int64_t(h->num_sms) * 32) blocks = int64_t(h->num_sms) * 32;
-                k_window_offsets<<<unsigned(blocks > 0 ? blocks : 1), 256, 0, s>>>(g, woff);
-                if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
-                stc_count(h);
-            }
-            {
-                int64_t blocks = (nA * 32 + 255) / 256;
-                if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-                k_row_ub<<<unsigned(blocks), 256, 0, s>>>(g, ub, bin_count);
-                k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
-                k_bin_scatter<<<unsigned((nA + 511) / 512), 512, 0, s>>>(nA, ub, cursor, rowlist);
-                if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
-                stc_count(h, 3);
-            }
-            stc_mark(h, s, 2);
-            if (rank_path) {
-                size_t smem = size_t(ncell) * 33 * 4;
-                int grid = 0;
-                auto kern = k_symbolic_rank<RK_SYM_NT>;
-                STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-                int per_sm = 0;
-                STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
-                if (per_sm < 1) return fail(STC_ERR_CUDA);
-                grid = per_sm * h->num_sms;
-                if (int64_t(grid) > nA) grid = int(nA);
-                kern<<<grid, RK_SYM_NT, smem, s>>>(g, rowlist, nlist, counters, c_ptr + 1, max_nnz);
-                if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
-                stc_count(h);
-            } else {
-                size_t smem = size_t(Ws / 32) * 4;
-                int grid = 0;
-                auto kern = k_symbolic<SP_NT>;
-                if ((st = launch_persistent(h, kern, smem, grid)) != STC_OK) return fail(st);
-                if (int64_t(grid) > nA) grid = int(nA);
-                kern<<<grid, SP_NT, smem, s>>>(g, R, rowlist, nlist, counters, c_ptr + 1);
-                if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
-                stc_count(h);
-            }
-            stc_mark(h, s, 3);
-            if ((st = stc_inclusive_scan_i64(h, sc, c_ptr + 1, nA, s)) != STC_OK) return fail(st);
-        } else {
-            stc_mark(h, s, 2);
-            stc_mark(h, s, 3);
-        }
-        // the single synchronisation: nnz(C), the largest row and the validation flags
-        int* stage_i = reinterpret_cast<int*>(&h->h_stage[1]);
-        stage_i[0] = 0;
-        stage_i[1] = 0;
-        if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + nA, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(&stage_i[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            (ints && cudaMemcpyAsync(&stage_i[1], ints + 2 * NBINS + 4, sizeof(int), cudaMemcpyDeviceToHost,
-                                     s) != cudaSuccess) ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return fail(STC_ERR_CUDA);
-        }
-        const int64_t nnz = h->h_stage[0];
-        const int flags = stage_i[0];
-        const int max_row = stage_i[1];
-        if (flags) {
-            (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
-            return fail(stc_flags_to_status(flags));
-        }
-        if (nnz < 0) return fail(STC_ERR_CUDA);
-        c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
-        c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
-        if (!c_col || !c_val) return fail(STC_ERR_OOM);
-        int32_t* ctab = nullptr;
-        if (!trivial && nnz > 0 && rank_path && max_row >= vcap - RK_CELL) {
-            ctab = sc.get<int32_t>(size_t(g.K) * size_t(ncell + 1));
-            if (!ctab) return fail(STC_ERR_OOM);
-            int64_t tot = g.K * (ncell + 1);
+    if (numeric_smem_bytes(alg, g.W) > size_t(h->smem_optin) - 24 * 1024) return fail(STC_ERR_INVALID_ARG);
+    StcScratch sc(h, s);
+    int32_t* rowlist = nullptr;
+    int* ints = nullptr;
+    if (!trivial) {
+        int64_t Ws = ncp < SYM_MAX_COLS ? ncp : SYM_MAX_COLS;
+        if (Ws < W) Ws = W;
+        const int R = int(Ws / W);
+        int64_t* ub = sc.get<int64_t>(size_t(nA));
+        rowlist = sc.get<int32_t>(size_t(nA));
+        ints = sc.get<int>(2 * NBINS + 8);
+        if (sc.failed) return fail(STC_ERR_OOM);
+        if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS + 8), s) != cudaSuccess) return fail(STC_ERR_CUDA);
+        int* bin_count = ints;
+        int* cursor = ints + NBINS;
+        int* nlist = ints + 2 * NBINS;
+        int* counters = ints + 2 * NBINS + 1;
+        if (g.nwin > 1) {
+            int32_t* woff = sc.get<int32_t>(size_t(g.K) * size_t(g.nwin + 1));
+            if (!woff) return fail(STC_ERR_OOM);
+            g.woff = woff;
+            int64_t tot = g.K * (g.nwin + 1);
             int64_t blocks = (tot + 255) / 256;
-            if (blocks > int64_t(h->num_sms) * 64) blocks = int64_t(h->num_sms) * 64;
-            k_cell_offsets<<<unsigned(blocks > 0 ? blocks : 1), 256, 0, s>>>(g, ncell, ctab);
+            if (blocks > int64_t(h->num_sms) * 32) blocks = int64_t(h->num_sms) * 32;
+            k_window_offsets<<<unsigned(blocks > 0 ? blocks : 1), 256, 0, s>>>(g, woff);
             if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
             stc_count(h);
         }
-        stc_mark(h, s, 4);
-        if (!trivial && nnz > 0) {
-            int* nlist = ints + 2 * NBINS;
-            int* counters = ints + 2 * NBINS + 1;
-            if (rank_path) {
-                switch (alg) {
-                case ALG_PT_F32: st = run_numeric_rank<ALG_PT_F32>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_PT_F64: st = run_numeric_rank<ALG_PT_F64>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_MP_I32: st = run_numeric_rank<ALG_MP_I32>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_MP_F32: st = run_numeric_rank<ALG_MP_F32>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_BOOL: st = run_numeric_rank<ALG_BOOL>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_MULTPATH: st = run_numeric_rank<ALG_MULTPATH>(h, g, ctab, vcap, maxwin, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                default: st = STC_ERR_ALGEBRA;
-                }
-            } else {
-                switch (alg) {
-                case ALG_PT_F32: st = run_numeric<ALG_PT_F32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_PT_F64: st = run_numeric<ALG_PT_F64>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_MP_I32: st = run_numeric<ALG_MP_I32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_MP_F32: st = run_numeric<ALG_MP_F32>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_BOOL: st = run_numeric<ALG_BOOL>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                case ALG_MULTPATH: st = run_numeric<ALG_MULTPATH>(h, g, rowlist, nlist, counters + 1, c_ptr, c_col, c_val, nA, s); break;
-                default: st = STC_ERR_ALGEBRA;
-                }
-            }
-            if (st != STC_OK) return fail(st);
-        }
-        stc_mark(h, s, 5);
-        C->nnz = nnz;
+        int64_t blocks = (nA * 32 + 255) / 256;
+        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+        k_row_ub<<<unsigned(blocks), 256, 0, s>>>(g, ub, bin_count);
+        k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
+        k_bin_scatter<<<unsigned((nA + 511) / 512), 512, 0, s>>>(nA, ub, cursor, rowlist);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h, 3);
+        stc_mark(h, s, 2);
+        size_t smem = size_t(Ws / 32) * 4;
+        int grid = 0;
+        auto kern = k_symbolic<SP_NT>;
+        if ((st = launch_persistent(h, kern, smem, grid)) != STC_OK) return fail(st);
+        if (int64_t(grid) > nA) grid = int(nA);
+        kern<<<grid, SP_NT, smem, s>>>(g, R, rowlist, nlist, counters, c_ptr + 1);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+        stc_mark(h, s, 3);
+        if ((st = stc_inclusive_scan_i64(h, sc, c_ptr + 1, nA, s)) != STC_OK) return fail(st);
+    } else {
+        stc_mark(h, s, 2);
+        stc_mark(h, s, 3);
     }
+    int* stage_i = reinterpret_cast<int*>(&h->h_stage[1]);
+    stage_i[0] = 0;
+    if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + nA, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&stage_i[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(STC_ERR_CUDA);
+    }
+    const int64_t nnz = h->h_stage[0];
+    const int flags = stage_i[0];
+    if (flags) {
+        (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
+        return fail(stc_flags_to_status(flags));
+    }
+    if (nnz < 0) return fail(STC_ERR_CUDA);
+    c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
+    c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
+    if (!c_col || !c_val) return fail(STC_ERR_OOM);
+    stc_mark(h, s, 4);
+    if (!trivial && nnz > 0) {
+        int* nlist = ints + 2 * NBINS;
+        int* counter = ints + 2 * NBINS + 2;
+        switch (alg) {
+        case ALG_PT_F32: st = run_numeric<ALG_PT_F32>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
+        case ALG_PT_F64: st = run_numeric<ALG_PT_F64>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
+        case ALG_MP_I32: st = run_numeric<ALG_MP_I32>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
+        case ALG_MP_F32: st = run_numeric<ALG_MP_F32>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
+        case ALG_BOOL: st = run_numeric<ALG_BOOL>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
+        case ALG_MULTPATH: st = run_numeric<ALG_MULTPATH>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
+        default: st = STC_ERR_ALGEBRA;
+        }
+        if (st != STC_OK) return fail(st);
+    }
+    stc_mark(h, s, 5);
     C->rowptr = c_ptr;
     C->col = c_col;
     C->val = c_val;
+    C->nnz = nnz;
     return STC_OK;
+}
+
+stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
+                           const stc_opts* opts, stc_stream s) {
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->nnz = 0;
+    C->rowptr = nullptr;
+    C->col = nullptr;
+    C->val = nullptr;
+    // rank-indexed kernels whenever the row bitmap fits shared memory, unless a
+    // column window width is forced (the window kernels then serve any width)
+    if (B->ncols <= RK_MAX_COLS && !(opts && opts->window_cols)) {
+        SpgArgs g = make_args(A, B);
+        const int64_t row_off[2] = {0, A->nrows};
+        int64_t bounds[2];
+        int64_t* c_ptr = nullptr;
+        int32_t* c_col = nullptr;
+        void* c_val = nullptr;
+        int64_t nnz = 0;
+        stc_status st = spgemm_rank_impl(h, alg, 1, &g, row_off, !(opts && opts->skip_validation), A, B, &c_ptr,
+                                         &c_col, &c_val, &nnz, bounds, s);
+        if (st != STC_OK) return st;
+        C->rowptr = c_ptr;
+        C->col = c_col;
+        C->val = c_val;
+        C->nnz = nnz;
+        return STC_OK;
+    }
+    return spgemm_window_impl(h, alg, A, B, C, opts, s);
 }

@@ -2,6 +2,7 @@
 // device-wide scan used to turn per-row counts into row pointers.
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "stc_internal.cuh"
 
@@ -209,6 +210,57 @@ stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s)
     return STC_OK;
 }
 
+// Validation of many matrices in one launch: blockIdx.y selects the matrix.
+struct CsrView {
+    int64_t nrows, ncols, nnz;
+    const int64_t* ptr;
+    const int32_t* col;
+};
+
+__global__ void k_validate_many(const CsrView* __restrict__ views, int* flags) {
+    const CsrView m = views[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    if (warp == 0 && lane == 0 && (m.ptr[0] != 0 || m.ptr[m.nrows] != m.nnz)) atomicOr(flags, STC_FLAG_SHAPE);
+    int bad = 0;
+    for (int64_t i = warp; i < m.nrows; i += nwarps) {
+        const int64_t lo = m.ptr[i], hi = m.ptr[i + 1];
+        if (lo < 0 || hi < lo || hi > m.nnz) {
+            bad |= STC_FLAG_SHAPE;
+            continue;
+        }
+        for (int64_t p = lo + lane; p < hi; p += 32) {
+            const int32_t c = m.col[p];
+            if (c < 0 || c >= m.ncols) bad |= STC_FLAG_UNSORTED;
+            if (p > lo && m.col[p - 1] >= c) bad |= STC_FLAG_UNSORTED;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane == 0 && bad) atomicOr(flags, bad);
+}
+
+stc_status stc_validate_many_async(stc_handle* h, StcScratch& sc, const stc_csr* mats, int count, stc_stream s) {
+    if (count == 1) return stc_validate_csr_async(h, mats, s);
+    std::vector<CsrView> v(count);
+    int64_t maxrows = 1;
+    for (int i = 0; i < count; ++i) {
+        v[i] = CsrView{mats[i].nrows, mats[i].ncols, mats[i].nnz, mats[i].rowptr, mats[i].col};
+        if (mats[i].nrows > maxrows) maxrows = mats[i].nrows;
+    }
+    CsrView* d = sc.get<CsrView>(size_t(count));
+    if (!d) return STC_ERR_OOM;
+    STC_CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(CsrView) * count, cudaMemcpyHostToDevice, s));
+    int64_t bx = (maxrows * 32 + 255) / 256;
+    if (bx > 32) bx = 32;
+    k_validate_many<<<dim3(unsigned(bx), unsigned(count)), 256, 0, s>>>(d, h->d_flags);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    // the host vector must outlive the copy
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    return STC_OK;
+}
+
 // Same validation with the flag word supplied by the caller (no handle).
 stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, int num_sms, stc_stream s) {
     int64_t warps_needed = m->nrows > 0 ? m->nrows : 1;
@@ -318,6 +370,27 @@ extern "C" stc_status stc_contract_spgemm(stc_handle* h, stc_algebra alg, const 
         if (w != 0 && (w < 1024 || (w & (w - 1)) != 0)) return STC_ERR_INVALID_ARG;
     }
     return stc_spgemm_impl(h, alg, A, B, C, opts, stream);
+}
+
+extern "C" stc_status stc_contract_spgemm_batched(stc_handle* h, stc_algebra alg, int32_t nbatch,
+                                                  const stc_csr* A, const stc_csr* B, stc_csr* C,
+                                                  const stc_opts* opts, stc_stream stream) {
+    if (!h || !A || !B || !C || nbatch < 1 || nbatch > 65535) return STC_ERR_INVALID_ARG;
+    if (!alg_valid(alg)) return STC_ERR_ALGEBRA;
+    int64_t rows = 0;
+    for (int32_t b = 0; b < nbatch; ++b) {
+        stc_status st = stc_check_csr_host(&A[b]);
+        if (st != STC_OK) return st;
+        if ((st = stc_check_csr_host(&B[b])) != STC_OK) return st;
+        if (A[b].ncols != B[b].nrows) return STC_ERR_SHAPE;
+        if (B[b].ncols > (1 << 18)) return STC_ERR_INVALID_ARG;
+        rows += A[b].nrows;
+    }
+    if (rows >= INT32_MAX) return STC_ERR_INVALID_ARG;
+    if (opts)
+        for (int r : opts->reserved)
+            if (r != 0) return STC_ERR_INVALID_ARG;
+    return stc_spgemm_batched_impl(h, alg, nbatch, A, B, C, opts, stream);
 }
 
 extern "C" stc_status stc_contract_spmm(stc_handle* h, stc_algebra alg, const stc_csr* A,

@@ -81,6 +81,8 @@ stc_status stc_check_csr_host(const stc_csr* m);
 // Enqueue the device-side validation of a CSR matrix; raises STC_FLAG_SHAPE /
 // STC_FLAG_UNSORTED in h->d_flags.
 stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s);
+// Validation of `count` matrices (host descriptors) in one launch.
+stc_status stc_validate_many_async(stc_handle* h, StcScratch& sc, const stc_csr* mats, int count, stc_stream s);
 // The same check raising its flags in `flags` (a device int); needs no handle.
 stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, int num_sms, stc_stream s);
 
@@ -163,6 +165,8 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T& total) {
 
 stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
                            const stc_opts* opts, stc_stream s);
+stc_status stc_spgemm_batched_impl(stc_handle* h, int alg, int nb, const stc_csr* A, const stc_csr* B,
+                                   stc_csr* C, const stc_opts* opts, stc_stream s);
 stc_status stc_spmm_impl(stc_handle* h, int alg, const stc_csr* A, const void* X, int64_t ldx,
                          int32_t ncol, void* Y, int64_t ldy, int32_t accumulate, stc_stream s);
 stc_status stc_bellman_ford_impl(stc_handle* h, int alg, const stc_csr* G, int32_t source,
