@@ -65,6 +65,12 @@ def lib():
             L.orc_floyd_warshall_i32.argtypes = [_i64, _p]
             L.orc_brandes.argtypes = [_i64, _p, _p, _p, ctypes.c_int, _p, _i64, _p]
             L.orc_sssp_counts.argtypes = [_i64, _p, _p, _p, ctypes.c_int, _i32, _p, _p]
+            L.orc_splitmix64.argtypes = [ctypes.c_uint64]
+            L.orc_splitmix64.restype = ctypes.c_uint64
+            L.orc_row_features.argtypes = [_p, _p, _p, _p, _p, _i64, _p]
+            L.orc_mlp_num_weights.restype = ctypes.c_int
+            L.orc_mlp_forward.argtypes = [_p, _p, _i64, _p]
+            L.orc_mlp_grad.argtypes = [_p, _p, _p, _i64, _p, _p]
             _lib = L
     return _lib
 
@@ -197,3 +203,44 @@ def sssp_counts(G: Csr, source: int, weighted: bool):
     lib().orc_sssp_counts(G.nrows, _ptr(_c(G.rowptr, np.int64)), _ptr(_c(G.col, np.int32)), _ptr(w),
                           1 if weighted else 0, int(source), _ptr(d), _ptr(s))
     return d, s
+
+
+# ----------------------------------------------------------------- learned row sizing
+
+NFEAT = 67
+NHID = 64
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().orc_splitmix64(ctypes.c_uint64(x)))
+
+
+def row_features(A: Csr, B: Csr, rows=None) -> np.ndarray:
+    """fp64 features [len(rows), 67] of the output rows of A B (see stc_oracle.c)."""
+    rows = np.arange(A.nrows, dtype=np.int64) if rows is None else _c(rows, np.int64)
+    f = np.zeros((rows.size, NFEAT), dtype=np.float64)
+    lib().orc_row_features(_ptr(_c(A.rowptr, np.int64)), _ptr(_c(A.col, np.int32)),
+                           _ptr(_c(B.rowptr, np.int64)), _ptr(_c(B.col, np.int32)), _ptr(rows),
+                           rows.size, _ptr(f))
+    return f
+
+
+def mlp_num_weights() -> int:
+    return int(lib().orc_mlp_num_weights())
+
+
+def mlp_forward(w: np.ndarray, x: np.ndarray) -> np.ndarray:
+    x = _c(x, np.float64)
+    y = np.zeros(x.shape[0], dtype=np.float64)
+    lib().orc_mlp_forward(_ptr(_c(w, np.float64)), _ptr(x), x.shape[0], _ptr(y))
+    return y
+
+
+def mlp_grad(w: np.ndarray, x: np.ndarray, t: np.ndarray):
+    """(gradient of the mean squared error w.r.t. the weights, loss), fp64."""
+    x = _c(x, np.float64)
+    g = np.zeros(mlp_num_weights(), dtype=np.float64)
+    loss = np.zeros(1, dtype=np.float64)
+    lib().orc_mlp_grad(_ptr(_c(w, np.float64)), _ptr(x), _ptr(_c(t, np.float64)), x.shape[0], _ptr(g),
+                       _ptr(loss))
+    return g, float(loss[0])

@@ -566,3 +566,138 @@ void orc_sssp_counts(int64_t n, const int64_t* ptr, const int32_t* col, const in
     for (int64_t v = 0; v < n; ++v) dist_out[v] = (int32_t)dist[v];
     free(dist); free(order); free(done); free(h);
 }
+
+/* ------------------------------------------------------- learned row sizing */
+
+/* SplitMix64 output function (Steele, Lea & Flood; Vigna's public-domain
+ * reference): the 64-bit mix of x + 0x9E3779B97F4A7C15.  The one-permutation
+ * min-hash below hashes column ids with it. */
+uint64_t orc_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+#define ORC_NB 32        /* min-hash buckets */
+#define ORC_NF 67        /* features per row: 3 scalars + 2 per bucket */
+
+/* Features of the selected rows of C = A B, in fp64:
+ *   f[0] = log2(1 + ub),  ub = sum over stored k of row i of nnz(B_k)
+ *   f[1] = log2(1 + nnz(A_i))
+ *   f[2] = log2(1 + max over stored k of nnz(B_k))
+ *   f[3 + 2b], f[4 + 2b] for bucket b < 32 of the one-permutation min-hash of the
+ *   union U_i of the column sets of those B rows: h = splitmix64(j), bucket =
+ *   h >> 59, key = low 32 bits of h; f[3+2b] = (min key) / 2^32 and f[4+2b] = 0,
+ *   or 1 and 1 when no column of U_i falls in the bucket.
+ * The sketch is computed directly over U_i (every product visited). */
+void orc_row_features(const int64_t* a_ptr, const int32_t* a_col, const int64_t* b_ptr,
+                      const int32_t* b_col, const int64_t* rows, int64_t nsel, double* feat) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < nsel; ++t) {
+        int64_t i = rows[t];
+        double* f = feat + t * ORC_NF;
+        int64_t ub = 0, mx = 0;
+        uint32_t mins[ORC_NB];
+        for (int b = 0; b < ORC_NB; ++b) mins[b] = 0xFFFFFFFFu;
+        int seen[ORC_NB];
+        for (int b = 0; b < ORC_NB; ++b) seen[b] = 0;
+        for (int64_t p = a_ptr[i]; p < a_ptr[i + 1]; ++p) {
+            int32_t k = a_col[p];
+            int64_t len = b_ptr[k + 1] - b_ptr[k];
+            ub += len;
+            if (len > mx) mx = len;
+            for (int64_t q = b_ptr[k]; q < b_ptr[k + 1]; ++q) {
+                uint64_t h = orc_splitmix64((uint64_t)b_col[q]);
+                int b = (int)(h >> 59);
+                uint32_t key = (uint32_t)(h & 0xFFFFFFFFull);
+                seen[b] = 1;
+                if (key < mins[b]) mins[b] = key;
+            }
+        }
+        f[0] = log2(1.0 + (double)ub);
+        f[1] = log2(1.0 + (double)(a_ptr[i + 1] - a_ptr[i]));
+        f[2] = log2(1.0 + (double)mx);
+        for (int b = 0; b < ORC_NB; ++b) {
+            f[3 + 2 * b] = seen[b] ? (double)mins[b] / 4294967296.0 : 1.0;
+            f[4 + 2 * b] = seen[b] ? 0.0 : 1.0;
+        }
+    }
+}
+
+/* Two-hidden-layer perceptron 67 -> 64 -> 64 -> 1 with ReLU, fp64.
+ * Weight vector layout (8577 values): W1[64][67], b1[64], W2[64][64], b2[64],
+ * w3[64], b3.  y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3. */
+#define ORC_H 64
+#define ORC_NW (ORC_H * ORC_NF + ORC_H + ORC_H * ORC_H + ORC_H + ORC_H + 1)
+
+static void mlp_one(const double* w, const double* x, double* h1, double* h2, double* y) {
+    const double* W1 = w;
+    const double* b1 = W1 + ORC_H * ORC_NF;
+    const double* W2 = b1 + ORC_H;
+    const double* b2 = W2 + ORC_H * ORC_H;
+    const double* w3 = b2 + ORC_H;
+    const double* b3 = w3 + ORC_H;
+    for (int o = 0; o < ORC_H; ++o) {
+        double a = b1[o];
+        for (int i = 0; i < ORC_NF; ++i) a += W1[o * ORC_NF + i] * x[i];
+        h1[o] = a > 0.0 ? a : 0.0;
+    }
+    double out = b3[0];
+    for (int o = 0; o < ORC_H; ++o) {
+        double a = b2[o];
+        for (int j = 0; j < ORC_H; ++j) a += W2[o * ORC_H + j] * h1[j];
+        h2[o] = a > 0.0 ? a : 0.0;
+        out += w3[o] * h2[o];
+    }
+    *y = out;
+}
+
+int orc_mlp_num_weights(void) { return ORC_NW; }
+
+void orc_mlp_forward(const double* w, const double* x, int64_t n, double* y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n; ++r) {
+        double h1[ORC_H], h2[ORC_H];
+        mlp_one(w, x + r * ORC_NF, h1, h2, &y[r]);
+    }
+}
+
+/* Gradient of the mean squared error L = (1/n) sum_r (y_r - t_r)^2 with respect
+ * to every weight (backpropagation through the two ReLU layers); *loss = L. */
+void orc_mlp_grad(const double* w, const double* x, const double* t, int64_t n, double* grad,
+                  double* loss) {
+    for (int k = 0; k < ORC_NW; ++k) grad[k] = 0.0;
+    const double* W2 = w + ORC_H * ORC_NF + ORC_H;
+    const double* w3 = W2 + ORC_H * ORC_H + ORC_H;
+    double* gW1 = grad;
+    double* gb1 = gW1 + ORC_H * ORC_NF;
+    double* gW2 = gb1 + ORC_H;
+    double* gb2 = gW2 + ORC_H * ORC_H;
+    double* gw3 = gb2 + ORC_H;
+    double* gb3 = gw3 + ORC_H;
+    double L = 0.0;
+    for (int64_t r = 0; r < n; ++r) {
+        const double* xr = x + r * ORC_NF;
+        double h1[ORC_H], h2[ORC_H], y, d2[ORC_H], d1[ORC_H];
+        mlp_one(w, xr, h1, h2, &y);
+        double e = y - t[r];
+        L += e * e;
+        double dy = 2.0 * e / (double)n;
+        gb3[0] += dy;
+        for (int o = 0; o < ORC_H; ++o) {
+            gw3[o] += dy * h2[o];
+            d2[o] = h2[o] > 0.0 ? dy * w3[o] : 0.0;
+            gb2[o] += d2[o];
+            for (int j = 0; j < ORC_H; ++j) gW2[o * ORC_H + j] += d2[o] * h1[j];
+        }
+        for (int j = 0; j < ORC_H; ++j) {
+            double a = 0.0;
+            for (int o = 0; o < ORC_H; ++o) a += W2[o * ORC_H + j] * d2[o];
+            d1[j] = h1[j] > 0.0 ? a : 0.0;
+            gb1[j] += d1[j];
+            for (int i = 0; i < ORC_NF; ++i) gW1[j * ORC_NF + i] += d1[j] * xr[i];
+        }
+    }
+    *loss = L / (double)n;
+}
