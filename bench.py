@@ -275,6 +275,12 @@ def run_stc(args):
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(args, stc, H, wl, dev)
+    forms = {}
+    if not args.no_forms and wl["scale"] is not None and rank == 0:
+        H.set_timing(False)
+        forms["learned_vs_plain"] = measure_learned(stc, H, wl, dev)
+        forms["batched_vs_per_call"] = measure_batched(stc, H)
+        forms["mfbc"] = measure_mfbc(stc, H)
 
     if rank == 0:
         out = {
@@ -299,6 +305,8 @@ def run_stc(args):
         }
         if e2e is not None:
             out["e2e"] = e2e
+        if forms:
+            out["forms"] = forms
         if not args.no_cpu_baseline and world == 1:
             import oracle as O
             cores = len(os.sched_getaffinity(0))
@@ -309,6 +317,101 @@ def run_stc(args):
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _timed(fn, reps):
+    """Median wall time (s) of fn() over reps runs, each bracketed by device syncs."""
+    import torch
+    ts = []
+    out = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t)
+        if out is not None and not isinstance(out, tuple):
+            del out
+            out = None
+    return statistics.median(ts)
+
+
+def measure_learned(stc, H, wl, dev):
+    """Plain two-pass vs learned single pass (trained model) vs upper-bound single
+    pass on the workload's (+,x) fp32 SpGEMM.  The model is trained on R-MAT
+    scales 14-16 (seeds 1..3), ER and banded matrices, never on the measured graph."""
+    import torch
+    A = wl["A"]
+    pairs = []
+    for sc in (14, 15, 16):
+        m = W.rmat(sc, seed=sc - 13)
+        d = stc.DeviceCsr.from_host(m.nrows, m.ncols, m.rowptr, m.col, None)
+        pairs.append((d, d))
+    for m in (W.er_fixed_degree(1 << 16, 8, seed=1), W.banded(1 << 16, 16, 0.5, seed=2)):
+        d = stc.DeviceCsr.from_host(m.nrows, m.ncols, m.rowptr, m.col, None)
+        pairs.append((d, d))
+    t0 = time.perf_counter()
+    feat, target = stc.training_rows(H, pairs)
+    w = stc.mlp_init(seed=1)
+    losses = H.mlp_train(w, feat, target, batch=4096, epochs=30, lr=2e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    del feat, target, pairs
+    d32 = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["w32"])
+    nprod = products(A)
+    t_plain = _timed(lambda: H.spgemm(stc.PLUS_TIMES_F32, d32, d32), 3)
+    stats = {}
+
+    def learned(weights, margin, key):
+        C, st = H.spgemm_learned(stc.PLUS_TIMES_F32, d32, d32, weights, margin)
+        stats[key] = st
+        return C
+
+    t_ml = _timed(lambda: learned(w, 0.5, "model"), 3)
+    t_ub = _timed(lambda: learned(None, 0.0, "upper_bound"), 3)
+    torch.cuda.empty_cache()
+    return {"unit": UNIT, "workload": "rmat18 (+,x) fp32 A.A",
+            "plain_two_pass": nprod / t_plain, "learned_single_pass": nprod / t_ml,
+            "upper_bound_single_pass": nprod / t_ub,
+            "ms": {"plain": 1e3 * t_plain, "learned": 1e3 * t_ml, "upper_bound": 1e3 * t_ub},
+            "model_stats": stats.get("model"), "upper_bound_stats": stats.get("upper_bound"),
+            "training": {"seconds": t_train, "final_loss": losses[-1] if losses else None,
+                         "epochs": len(losses)}}
+
+
+def measure_batched(stc, H):
+    """4096 independent (+,x) fp32 pairs: one batched call vs one call per pair."""
+    import torch
+    sizes, As, Bs = W.powerlaw_batch(4096, 64, 16384, 2.1, 4, 64, seed=0)
+    dA = [stc.DeviceCsr.from_host(a.nrows, a.ncols, a.rowptr, a.col, a.val) for a in As]
+    dB = [stc.DeviceCsr.from_host(b.nrows, b.ncols, b.rowptr, b.col, b.val) for b in Bs]
+    nprod = sum(int(np.diff(b.rowptr)[a.col].sum()) for a, b in zip(As, Bs))
+    t_b = _timed(lambda: H.spgemm_batched(stc.PLUS_TIMES_F32, dA, dB), 3)
+
+    def per_call():
+        for a, b in zip(dA, dB):
+            H.spgemm(stc.PLUS_TIMES_F32, a, b)
+    t_p = _timed(per_call, 1)
+    torch.cuda.empty_cache()
+    return {"unit": UNIT, "workload": "4096 pairs, rows power-law [64,16384] exp 2.1, U{4..64}/row, N(0,1) fp32",
+            "products": nprod, "batched": nprod / t_b, "per_call": nprod / t_p,
+            "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p}}
+
+
+def measure_mfbc(stc, H, scale=22, nsrc=256):
+    """Betweenness centrality, one batch of 256 sources on R-MAT scale 22: GTEPS =
+    sources * edges / time (forward + backward + reduction)."""
+    import torch
+    G = W.rmat(scale, seed=0)
+    src = W.sample_sources(G, nsrc, seed=0)
+    out = {"unit": "GTEPS", "workload": f"rmat{scale}, {nsrc} sources (one batch)", "edges": G.nnz}
+    for name, val in (("unit_lengths", None), ("int_lengths_1_255", W.weights_int(G.nnz, 1, 255, seed=1))):
+        d = stc.DeviceCsr.from_host(G.nrows, G.ncols, G.rowptr, G.col, val)
+        t = _timed(lambda: H.mfbc(d, src, batch=nsrc), 1)
+        out[name] = nsrc * G.nnz / t / 1e9
+        out[name + "_ms"] = 1e3 * t
+        del d
+        torch.cuda.empty_cache()
+    return out
 
 
 def measure_e2e(args, stc, H, wl, dev):
@@ -382,6 +485,8 @@ def main():
                     help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the learned / batched / centrality measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

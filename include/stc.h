@@ -281,6 +281,81 @@ STC_API stc_status stc_mfbc(stc_handle* h, const stc_csr* G, const int32_t* sour
                             int32_t batch, double* bc_out, stc_stream stream);
 
 /*
+ * Learned output sizing (no counterpart in the paper, which leaves SpGEMM and
+ * output sparsity as future work, Section 7; it names automatically-adjusted
+ * performance models as a direction there).
+ *
+ * Features of output row i of C = A B, STC_MLP_FEAT_STRIDE floats per row (the
+ * last is zero padding):
+ *   f0 = log2(1 + ub_i), ub_i = sum over stored k of row i of A of nnz(B_k)
+ *   f1 = log2(1 + nnz(A_i)),  f2 = log2(1 + max over those k of nnz(B_k))
+ *   f3+2b, f4+2b (b < 32): one-permutation min-hash of the union of those B rows'
+ *   columns: h = SplitMix64 output of the column id, bucket = top 5 bits of h,
+ *   key = low 32 bits; (min key) / 2^32 and 0, or 1 and 1 if the bucket is empty.
+ * Model: y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 predicting log2(1 + nnz(C_i)),
+ * 67 -> 64 -> 64 -> 1.  Weights: STC_MLP_NUM_WEIGHTS fp32 values in device memory,
+ * laid out W1[64][67], b1[64], W2[64][64], b2[64], w3[64], b3; they are rounded to
+ * bf16 wherever the model is evaluated, sums are fp32.
+ */
+#define STC_MLP_INPUTS 67
+#define STC_MLP_FEAT_STRIDE 68
+#define STC_MLP_HIDDEN 64
+#define STC_MLP_NUM_WEIGHTS 8577
+
+/* feat (device, float [A->nrows][STC_MLP_FEAT_STRIDE]) <- features of every row of A B. */
+STC_API stc_status stc_row_features(stc_handle* h, const stc_csr* A, const stc_csr* B, float* feat,
+                                    stc_stream stream);
+
+/* y[r] (device float [n]) <- model(feat[r]). */
+STC_API stc_status stc_mlp_forward(stc_handle* h, const float* weights, const float* feat, int64_t n, float* y,
+                                   stc_stream stream);
+
+/* grad (device float [STC_MLP_NUM_WEIGHTS]) += gradient of
+ * (1/scale) * sum over the n rows r = idx[0..n) (idx NULL: rows 0..n) of
+ * (y_r - target_r)^2; *loss (device float) += that sum of squares. */
+STC_API stc_status stc_mlp_grad(stc_handle* h, const float* weights, const float* feat, const float* target,
+                                const int32_t* idx, int64_t n, float scale, float* grad, float* loss,
+                                stc_stream stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step counted from 1) on the
+ * fp32 weights with moment buffers m, v; grad is consumed and cleared. */
+STC_API stc_status stc_mlp_adam(stc_handle* h, float* weights, float* m, float* v, float* grad, int64_t step,
+                                float lr, stc_stream stream);
+
+/* Initialise weights (device) with He-normal layers and zero biases from `seed`. */
+STC_API stc_status stc_mlp_init(float* weights, uint64_t seed, stc_stream stream);
+
+/* Mini-batch training: `epochs` passes over the n examples (feat, target on the
+ * device) in a seeded random order, mean squared error, Adam with rate lr.
+ * loss_out (host, may be NULL) receives the mean loss of every epoch.
+ * Synchronises `stream` once per epoch. */
+STC_API stc_status stc_mlp_train(stc_handle* h, float* weights, const float* feat, const float* target, int64_t n,
+                                 int32_t batch, int32_t epochs, float lr, uint64_t seed, float* loss_out,
+                                 stc_stream stream);
+
+typedef struct {
+    int64_t rows;              /* output rows with at least one product (-1: exact path used) */
+    int64_t overflow_rows;     /* rows whose predicted capacity was too small */
+    int64_t scratch_entries;   /* total predicted capacity */
+    int64_t nnz;               /* nnz(C) */
+    double mean_abs_log2_error; /* mean |prediction - log2(1 + nnz(C_i))| (-1 without a model) */
+} stc_learned_stats;
+
+/*
+ * Learned single-pass SpGEMM: C = A (x) B with the same result as
+ * stc_contract_spgemm (bit-identical structure), without the separate symbolic
+ * pass.  Every row gets a capacity -- (1 + margin) * (2^prediction - 1) + 8 from
+ * the model `weights`, clipped to [1, min(ub_i, ncols)], or min(ub_i, ncols) when
+ * weights is NULL -- and one numeric pass writes it into scratch of that size
+ * while counting it exactly; rows that fit are compacted into C, rows that did
+ * not are recomputed exactly.  B->ncols above 2^18 uses the exact two-pass path.
+ * Synchronises `stream` twice.  stats (host, may be NULL) as above.
+ */
+STC_API stc_status stc_contract_spgemm_learned(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
+                                               stc_csr* C, const float* weights, float margin,
+                                               stc_learned_stats* stats, const stc_opts* opts, stc_stream stream);
+
+/*
  * Instrumentation (no counterpart in the paper, which reports only the share of
  * time spent in local kernels).
  *

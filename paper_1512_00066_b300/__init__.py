@@ -34,6 +34,7 @@ STATUS = {0: "STC_OK", 1: "STC_ERR_INVALID_ARG", 2: "STC_ERR_SHAPE", 3: "STC_ERR
           4: "STC_ERR_ALGEBRA", 5: "STC_ERR_OOM", 6: "STC_ERR_CUDA", 7: "STC_ERR_NEG_CYCLE",
           8: "STC_ERR_TIMEOUT", 9: "STC_ERR_CAPACITY"}
 NOALLOC_BF_MAX_VERTICES = 1 << 20
+MLP_INPUTS, MLP_FEAT_STRIDE, MLP_HIDDEN, MLP_NUM_WEIGHTS = 67, 68, 64, 8577
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libstc.so")
@@ -64,6 +65,11 @@ class _Csr(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("skip_validation", ctypes.c_int32), ("window_cols", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 6)]
+
+
+class _LearnedStats(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("overflow_rows", ctypes.c_int64), ("scratch_entries", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("mean_abs_log2_error", ctypes.c_double)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -116,6 +122,23 @@ def lib():
             L.stc_mfbc_sssp.restype = ctypes.c_int
             L.stc_mfbc.argtypes = [p, ctypes.POINTER(_Csr), p, i32, i32, p, p]
             L.stc_mfbc.restype = ctypes.c_int
+            L.stc_row_features.argtypes = [p, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, p]
+            L.stc_row_features.restype = ctypes.c_int
+            L.stc_mlp_forward.argtypes = [p, p, p, i64, p, p]
+            L.stc_mlp_forward.restype = ctypes.c_int
+            L.stc_mlp_grad.argtypes = [p, p, p, p, p, i64, ctypes.c_float, p, p, p]
+            L.stc_mlp_grad.restype = ctypes.c_int
+            L.stc_mlp_adam.argtypes = [p, p, p, p, p, i64, ctypes.c_float, p]
+            L.stc_mlp_adam.restype = ctypes.c_int
+            L.stc_mlp_init.argtypes = [p, ctypes.c_uint64, p]
+            L.stc_mlp_init.restype = ctypes.c_int
+            L.stc_mlp_train.argtypes = [p, p, p, p, i64, i32, i32, ctypes.c_float, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_float), p]
+            L.stc_mlp_train.restype = ctypes.c_int
+            L.stc_contract_spgemm_learned.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr),
+                                                      ctypes.POINTER(_Csr), p, ctypes.c_float,
+                                                      ctypes.POINTER(_LearnedStats), ctypes.POINTER(_Opts), p]
+            L.stc_contract_spgemm_learned.restype = ctypes.c_int
             L.stc_bellman_ford_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(_Csr), i32, p,
                                                    ctypes.POINTER(i32), p]
             L.stc_bellman_ford_noalloc.restype = ctypes.c_int
@@ -325,6 +348,60 @@ class Handle:
         self.last_relaxations = int(relax.value)
         return dist, int(rounds.value)
 
+    # -------------------------------------------------------------- learned sizing
+
+    def row_features(self, A: DeviceCsr, B: DeviceCsr, stream=None) -> torch.Tensor:
+        """Features of every output row of A B: float [A.nrows, 68]."""
+        f = torch.empty((A.nrows, MLP_FEAT_STRIDE), dtype=torch.float32, device=A.col.device)
+        a, b = A._c(), B._c()
+        _check(lib().stc_row_features(self._h, ctypes.byref(a), ctypes.byref(b), f.data_ptr(), _stream_ptr(stream)),
+               "stc_row_features")
+        return f
+
+    def mlp_forward(self, weights: torch.Tensor, feat: torch.Tensor, stream=None) -> torch.Tensor:
+        y = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        _check(lib().stc_mlp_forward(self._h, weights.data_ptr(), feat.data_ptr(), feat.shape[0], y.data_ptr(),
+                                     _stream_ptr(stream)), "stc_mlp_forward")
+        return y
+
+    def mlp_grad(self, weights, feat, target, idx=None, scale=None, stream=None):
+        """(gradient, sum of squared errors) of mean-squared error over the rows."""
+        n = feat.shape[0] if idx is None else idx.numel()
+        g = torch.zeros(MLP_NUM_WEIGHTS, dtype=torch.float32, device=feat.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=feat.device)
+        _check(lib().stc_mlp_grad(self._h, weights.data_ptr(), feat.data_ptr(), target.data_ptr(),
+                                  None if idx is None else idx.data_ptr(), n, float(scale or n), g.data_ptr(),
+                                  loss.data_ptr(), _stream_ptr(stream)), "stc_mlp_grad")
+        return g, loss
+
+    def mlp_train(self, weights, feat, target, batch=4096, epochs=10, lr=1e-3, seed=0, stream=None):
+        """Train `weights` in place; returns the mean loss of every epoch."""
+        losses = (ctypes.c_float * max(epochs, 1))()
+        _check(lib().stc_mlp_train(self._h, weights.data_ptr(), feat.data_ptr(), target.data_ptr(), feat.shape[0],
+                                   int(batch), int(epochs), float(lr), int(seed), losses, _stream_ptr(stream)),
+               "stc_mlp_train")
+        return [float(losses[i]) for i in range(epochs)]
+
+    def spgemm_learned(self, alg: int, A: DeviceCsr, B: DeviceCsr, weights: Optional[torch.Tensor] = None,
+                       margin: float = 0.25, skip_validation: bool = False, stream=None):
+        """Single-pass SpGEMM sized by the model (or by the upper bound): (C, stats)."""
+        C = _Csr()
+        st_ = _LearnedStats()
+        opts = _Opts(1 if skip_validation else 0, 0)
+        a, b = A._c(), B._c()
+        st = lib().stc_contract_spgemm_learned(self._h, alg, ctypes.byref(a), ctypes.byref(b), ctypes.byref(C),
+                                               None if weights is None else weights.data_ptr(), float(margin),
+                                               ctypes.byref(st_), ctypes.byref(opts), _stream_ptr(stream))
+        _check(st, "stc_contract_spgemm_learned")
+        nnz = int(C.nnz)
+        rowptr = self._take(C.rowptr).view(torch.int64)[: C.nrows + 1]
+        col = self._take(C.col).view(torch.int32)[:nnz]
+        raw = self._take(C.val)
+        ct = _DT[alg][2]
+        val = raw[: nnz * DSIG_BYTES].view(nnz, DSIG_BYTES) if ct == "dsig" else raw.view(ct)[:nnz]
+        stats = {f: getattr(st_, f) for f, _ in _LearnedStats._fields_}
+        return DeviceCsr(int(C.nrows), int(C.ncols), rowptr, col, val), stats
+
     def mfbc_sssp(self, G: DeviceCsr, sources, stream=None):
         """(d [n, S] int32, sigma [n, S] fp64, rounds) from up to 256 sources."""
         src = np.ascontiguousarray(sources, dtype=np.int32)
@@ -379,6 +456,27 @@ def bellman_ford_noalloc(alg: int, G: DeviceCsr, source: int, dist: torch.Tensor
                                         ctypes.byref(rounds), _stream_ptr(stream))
     _check(st, "stc_bellman_ford_noalloc")
     return int(rounds.value)
+
+
+def mlp_init(seed: int = 0, device="cuda", stream=None) -> torch.Tensor:
+    """New fp32 weight vector (He-normal layers, zero biases) on the device."""
+    w = torch.empty(MLP_NUM_WEIGHTS, dtype=torch.float32, device=device)
+    _check(lib().stc_mlp_init(w.data_ptr(), int(seed), _stream_ptr(stream)), "stc_mlp_init")
+    return w
+
+
+def training_rows(H: "Handle", pairs):
+    """Features and exact targets log2(1 + nnz(C_i)) for every row of every (A, B)
+    pair (DeviceCsr), computed on the device: (feat [N, 68], target [N])."""
+    feats, targets = [], []
+    for A, B in pairs:
+        feats.append(H.row_features(A, B))
+        C = H.spgemm(OR_AND_BOOL, A.__class__(A.nrows, A.ncols, A.rowptr, A.col,
+                                              torch.ones(A.nnz, dtype=torch.uint8, device=A.col.device)),
+                     B.__class__(B.nrows, B.ncols, B.rowptr, B.col,
+                                 torch.ones(B.nnz, dtype=torch.uint8, device=B.col.device)))
+        targets.append(torch.log2(1.0 + (C.rowptr[1:] - C.rowptr[:-1]).to(torch.float32)))
+    return torch.cat(feats), torch.cat(targets)
 
 
 _default = {}

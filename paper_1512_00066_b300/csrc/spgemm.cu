@@ -53,6 +53,20 @@ struct SpgRows {
     int nb;
 };
 
+// Where the numeric rank kernel writes a row.  Plain form: ptr = C's row
+// pointers (cap == null), and a row must fill exactly its slot.  Learned form:
+// ptr = scratch offsets, cap = predicted capacity; the exact count goes to nnz[],
+// a row larger than its capacity is listed in ovf[] and not written.
+struct RankOut {
+    const int64_t* __restrict__ ptr;
+    const int64_t* __restrict__ cap;
+    int64_t* __restrict__ nnz;
+    int32_t* __restrict__ ovf;
+    int* __restrict__ novf;
+    const float* __restrict__ pred;  // predicted log2(1 + nnz), or null
+    double* __restrict__ err;        // sum of |pred - log2(1 + nnz)|
+};
+
 __device__ __forceinline__ int batch_of(const SpgRows& R, int64_t gi) {
     int lo = 0, hi = R.nb - 1;  // last b with row_off[b] <= gi
     while (lo < hi) {
@@ -801,7 +815,7 @@ template <int ALG, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
-               int* __restrict__ counter, const int64_t* __restrict__ c_ptr, int32_t* __restrict__ c_col,
+               int* __restrict__ counter, RankOut out, int32_t* __restrict__ c_col,
                void* __restrict__ c_val, int* __restrict__ flags) {
     using T = Tr<ALG>;
     using AT = typename T::A;
@@ -844,8 +858,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
         int64_t alo, ahi;
         row_range(g.a_ptr, i, g.nnzA, alo, ahi);
-        const int64_t o0 = c_ptr[gi];
-        const int64_t o1 = c_ptr[gi + 1];
+        const int64_t o0 = out.ptr[gi];
+        const int64_t o1 = out.cap ? o0 + out.cap[gi] : out.ptr[gi + 1];
 
         // 1) bitmap of the row's columns
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
@@ -886,7 +900,13 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         }
         if (threadIdx.x == 0) {
             cellbase[ncell] = total;
-            if (total != int(o1 - o0)) atomicOr(flags, STC_FLAG_INTERNAL);
+            if (out.cap) {
+                out.nnz[gi] = total;
+                if (total > o1 - o0) out.ovf[atomicAdd(out.novf, 1)] = int32_t(gi);
+                if (out.pred) atomicAdd(out.err, fabs(double(out.pred[gi]) - log2(1.0 + double(total))));
+            } else if (total != int(o1 - o0)) {
+                atomicOr(flags, STC_FLAG_INTERNAL);
+            }
         }
         __syncthreads();
         const bool fits = total <= int(o1 - o0);
@@ -895,7 +915,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             if (c == 0 || (cellbase[c - 1] / vstep) != wc) winfirst[wc] = c;
         }
         if (threadIdx.x == 0) {
-            const int nw = total > 0 ? cellbase[ncell - 1] / vstep + 1 : 0;
+            const int nw = (total > 0 && fits) ? cellbase[ncell - 1] / vstep + 1 : 0;
             winfirst[nw] = ncell;
             s_nwin = nw;
         }
@@ -1030,7 +1050,7 @@ struct RankCfg {
 
 template <int ALG, int NT, int MINB>
 stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
-                               const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
+                               const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
                                int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
     auto kern = k_numeric_rank<ALG, NT, MINB>;
     STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)));
@@ -1039,7 +1059,7 @@ stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, c
     if (per_sm < 1) return STC_ERR_CUDA;
     int64_t grid = int64_t(per_sm) * h->num_sms;
     if (grid > NR) grid = NR > 0 ? NR : 1;
-    kern<<<unsigned(grid), NT, cfg.smem, s>>>(R, ncell_max, cfg.vcap, cfg.maxwin, rowlist, nlist, counter, c_ptr,
+    kern<<<unsigned(grid), NT, cfg.smem, s>>>(R, ncell_max, cfg.vcap, cfg.maxwin, rowlist, nlist, counter, out,
                                               c_col, c_val, h->d_flags);
     STC_LAUNCH_CHECK();
     stc_count(h);
@@ -1048,13 +1068,27 @@ stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, c
 
 template <int ALG>
 stc_status run_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
-                            const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
+                            const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
                             int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
     if (cfg.small)
-        return launch_numeric_rank<ALG, 256, 4>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val,
+        return launch_numeric_rank<ALG, 256, 4>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
                                                 NR, s);
-    return launch_numeric_rank<ALG, RK_NT, 1>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val,
+    return launch_numeric_rank<ALG, RK_NT, 1>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
                                               NR, s);
+}
+
+stc_status run_numeric_any(stc_handle* h, int alg, const SpgRows& R, int ncell_max, const RankCfg& cfg,
+                           const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
+                           int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+    switch (alg) {
+    case ALG_PT_F32: return run_numeric_rank<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
+    case ALG_PT_F64: return run_numeric_rank<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
+    case ALG_MP_I32: return run_numeric_rank<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
+    case ALG_MP_F32: return run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
+    case ALG_BOOL: return run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
+    case ALG_MULTPATH: return run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
+    default: return STC_ERR_ALGEBRA;
+    }
 }
 
 RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max) {
@@ -1234,17 +1268,11 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     }
     stc_mark(h, s, 4);
     if (nnz > 0) {
-        int* counter = counters + 1;
-        switch (alg) {
-        case ALG_PT_F32: st = run_numeric_rank<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
-        case ALG_PT_F64: st = run_numeric_rank<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
-        case ALG_MP_I32: st = run_numeric_rank<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
-        case ALG_MP_F32: st = run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
-        case ALG_BOOL: st = run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
-        case ALG_MULTPATH: st = run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s); break;
-        default: st = STC_ERR_ALGEBRA;
-        }
-        if (st != STC_OK) return fail(st);
+        RankOut out{};
+        out.ptr = c_ptr;
+        if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, nlist, counters + 1, out, c_col, c_val, NR,
+                                  s)) != STC_OK)
+            return fail(st);
     }
     stc_mark(h, s, 5);
     if (nb > 1) {
@@ -1269,6 +1297,58 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     return STC_OK;
 }
 
+// Predicted capacity of every output row: min(ub, ncols) without a model (the
+// upper-bound single pass), else (1 + margin) * (2^pred - 1) + 8, clipped to
+// [1, min(ub, ncols)].  Also the scan input of the scratch offsets and the largest
+// capacity.
+__global__ void k_capacity(int64_t NR, const int64_t* __restrict__ ub, const float* __restrict__ pred, float margin,
+                           int64_t ncols, int64_t* __restrict__ cap, int64_t* __restrict__ cap_scan,
+                           int* __restrict__ maxcap) {
+    int m = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NR; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t u = ub[i];
+        int64_t c = 0;
+        if (u > 0) {
+            const int64_t lim = u < ncols ? u : ncols;
+            if (pred) {
+                const float p = fmaxf(exp2f(pred[i]) - 1.0f, 0.0f);
+                c = int64_t(ceilf((1.0f + margin) * p)) + 8;
+                c = c < lim ? c : lim;
+                c = c > 1 ? c : 1;
+            } else {
+                c = lim;
+            }
+        }
+        cap[i] = c;
+        cap_scan[i] = c;
+        m = max(m, int(c < INT_MAX ? c : INT_MAX));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(maxcap, m);
+}
+
+// Copy every listed row that fit its capacity from the scratch to C (warp per row).
+template <class V>
+__global__ void k_compact(const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
+                          const int64_t* __restrict__ soff, const int64_t* __restrict__ cap,
+                          const int64_t* __restrict__ c_ptr, const int32_t* __restrict__ scol,
+                          const V* __restrict__ sval, int32_t* __restrict__ c_col, V* __restrict__ c_val) {
+    const int lane = threadIdx.x & 31;
+    const int nlist = *nlist_ptr;
+    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t r = warp; r < nlist; r += nwarps) {
+        const int32_t i = rowlist[r];
+        const int64_t d0 = c_ptr[i], n = c_ptr[i + 1] - d0;
+        if (n > cap[i]) continue;  // overflow: recomputed exactly
+        const int64_t s0 = soff[i];
+        for (int64_t e = lane; e < n; e += 32) {
+            c_col[d0 + e] = scol[s0 + e];
+            c_val[d0 + e] = sval[s0 + e];
+        }
+    }
+}
+
 SpgArgs make_args(const stc_csr* A, const stc_csr* B) {
     SpgArgs g{};
     g.nA = A->nrows;
@@ -1290,6 +1370,184 @@ SpgArgs make_args(const stc_csr* A, const stc_csr* B) {
     return g;
 }
 
+
+// Learned single-pass SpGEMM (one matrix, at most RK_MAX_COLS output columns):
+// row analysis, features and perceptron (or the upper bound) give every row a
+// capacity; one numeric pass writes each row into scratch of that capacity and
+// records its exact size; a scan gives C's row pointers; the rows that fit are
+// compacted into C and the rows that overflowed are recomputed exactly into C.
+stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
+                               const float* weights, float margin, stc_learned_stats* stats, bool validate,
+                               stc_stream s) {
+    SpgArgs g = make_args(A, B);
+    const int64_t NR = A->nrows;
+    const int ncell_max = g.ncell > 0 ? g.ncell : 1;
+    const RankCfg cfg = rank_config(alg, B->ncols, ncell_max);
+    if (!cfg.vcap) return STC_ERR_INVALID_ARG;
+    const size_t vbytes = stc_val_bytes(alg, 'C');
+    int64_t* c_ptr = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(NR + 1) * 8, s));
+    if (!c_ptr) return STC_ERR_OOM;
+    int32_t* c_col = nullptr;
+    void* c_val = nullptr;
+    auto fail = [&](stc_status st) {
+        stc_free_bytes(h, c_ptr, s);
+        if (c_col) stc_free_bytes(h, c_col, s);
+        if (c_val) stc_free_bytes(h, c_val, s);
+        return st;
+    };
+    StcScratch sc(h, s);
+    stc_mark(h, s, 0);
+    if (cudaMemsetAsync(c_ptr, 0, size_t(NR + 1) * 8, s) != cudaSuccess) return fail(STC_ERR_CUDA);
+    stc_status st;
+    if (validate) {
+        if ((st = stc_validate_csr_async(h, A, s)) != STC_OK) return fail(st);
+        if ((st = stc_validate_csr_async(h, B, s)) != STC_OK) return fail(st);
+    }
+    stc_mark(h, s, 1);
+    SpgRows R{};
+    R.one = g;
+    R.nb = 1;
+    int64_t* ub = sc.get<int64_t>(size_t(NR));
+    int32_t* rowlist = sc.get<int32_t>(size_t(NR));
+    int32_t* ovf = sc.get<int32_t>(size_t(NR));
+    int64_t* cap = sc.get<int64_t>(size_t(NR));
+    int64_t* soff = sc.get<int64_t>(size_t(NR) + 1);
+    int* ints = sc.get<int>(2 * NBINS + 16);
+    double* err = sc.get<double>(1);
+    float* pred = weights ? sc.get<float>(size_t(NR)) : nullptr;
+    float* feat = weights ? sc.get<float>(size_t(NR) * STC_MLP_FEAT_STRIDE) : nullptr;
+    if (sc.failed) return fail(STC_ERR_OOM);
+    int* bin_count = ints;
+    int* cursor = ints + NBINS;
+    int* nlist = ints + 2 * NBINS;
+    int* counters = ints + 2 * NBINS + 1;  // [0] learned pass, [1] overflow pass
+    int* maxcap = ints + 2 * NBINS + 4;
+    int* novf = ints + 2 * NBINS + 5;
+    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS + 16), s) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(double), s) != cudaSuccess ||
+        cudaMemsetAsync(soff, 0, sizeof(int64_t), s) != cudaSuccess)
+        return fail(STC_ERR_CUDA);
+    if (NR > 0) {
+        int64_t blocks = (NR * 32 + 255) / 256;
+        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count);
+        k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, cursor, rowlist);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h, 3);
+        if (weights) {
+            if ((st = stc_features_impl(h, sc, A, B, feat, s)) != STC_OK) return fail(st);
+            if ((st = stc_mlp_forward_impl(h, weights, feat, NR, pred, s)) != STC_OK) return fail(st);
+        }
+        int64_t cb = (NR + 255) / 256;
+        if (cb > int64_t(h->num_sms) * 8) cb = int64_t(h->num_sms) * 8;
+        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred, margin, B->ncols, cap, soff + 1, maxcap);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+        if ((st = stc_inclusive_scan_i64(h, sc, soff + 1, NR, s)) != STC_OK) return fail(st);
+    }
+    stc_mark(h, s, 2);
+    // synchronisation 1: scratch size, largest capacity, validation flags
+    int* stage_i = reinterpret_cast<int*>(&h->h_stage[1]);
+    stage_i[0] = stage_i[1] = 0;
+    if (cudaMemcpyAsync(&h->h_stage[0], soff + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&stage_i[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&stage_i[1], maxcap, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(STC_ERR_CUDA);
+    }
+    const int64_t S_total = h->h_stage[0];
+    if (stage_i[0]) {
+        const int f = stage_i[0];
+        (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
+        return fail(stc_flags_to_status(f));
+    }
+    const int max_cap = stage_i[1];
+    int32_t* scol = sc.get<int32_t>(size_t(S_total));
+    unsigned char* sval = sc.get<unsigned char>(size_t(S_total) * vbytes);
+    if (sc.failed) return fail(STC_ERR_OOM);
+    if (NR > 0 && max_cap >= cfg.vcap - RK_CELL) {
+        int32_t* ctab = sc.get<int32_t>(size_t(g.K) * size_t(g.ncell + 1));
+        if (!ctab) return fail(STC_ERR_OOM);
+        R.one.ctab = ctab;
+        int64_t bx = (g.K * (g.ncell + 1) + 255) / 256;
+        if (bx > int64_t(h->num_sms) * 64) bx = int64_t(h->num_sms) * 64;
+        k_cell_offsets<<<dim3(unsigned(bx > 0 ? bx : 1), 1), 256, 0, s>>>(R);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+    }
+    stc_mark(h, s, 3);
+    if (NR > 0) {
+        RankOut out{};
+        out.ptr = soff;
+        out.cap = cap;
+        out.nnz = c_ptr + 1;
+        out.ovf = ovf;
+        out.novf = novf;
+        out.pred = pred;
+        out.err = err;
+        if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, nlist, counters, out, scol, sval, NR, s)) !=
+            STC_OK)
+            return fail(st);
+        if ((st = stc_inclusive_scan_i64(h, sc, c_ptr + 1, NR, s)) != STC_OK) return fail(st);
+    }
+    // synchronisation 2: nnz, overflowing rows, listed rows, prediction error
+    int* st2 = reinterpret_cast<int*>(&h->h_stage[8]);
+    st2[0] = st2[1] = 0;
+    double* err_h = reinterpret_cast<double*>(&h->h_stage[9]);
+    *err_h = 0.0;
+    if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&st2[0], novf, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&st2[1], nlist, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(err_h, err, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(STC_ERR_CUDA);
+    }
+    const int64_t nnz = h->h_stage[0];
+    const int n_ovf = st2[0], n_rows = st2[1];
+    const double err_sum = *err_h;
+    c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
+    c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
+    if (!c_col || !c_val) return fail(STC_ERR_OOM);
+    stc_mark(h, s, 4);
+    if (NR > 0 && nnz > 0) {
+        int64_t blocks = (int64_t(n_rows) * 32 + 255) / 256;
+        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+        if (blocks < 1) blocks = 1;
+        switch (vbytes) {
+        case 1: k_compact<uint8_t><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, sval, c_col, static_cast<uint8_t*>(c_val)); break;
+        case 4: k_compact<uint32_t><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, reinterpret_cast<const uint32_t*>(sval), c_col, static_cast<uint32_t*>(c_val)); break;
+        case 8: k_compact<uint64_t><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, reinterpret_cast<const uint64_t*>(sval), c_col, static_cast<uint64_t*>(c_val)); break;
+        default: k_compact<uint4><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, reinterpret_cast<const uint4*>(sval), c_col, static_cast<uint4*>(c_val)); break;
+        }
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+        if (n_ovf > 0) {
+            RankOut out{};
+            out.ptr = c_ptr;
+            if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, ovf, novf, counters + 1, out, c_col, c_val, NR, s)) !=
+                STC_OK)
+                return fail(st);
+        }
+    }
+    stc_mark(h, s, 5);
+    if (stats) {
+        stats->rows = n_rows;
+        stats->overflow_rows = n_ovf;
+        stats->scratch_entries = S_total;
+        stats->nnz = nnz;
+        stats->mean_abs_log2_error = (weights && n_rows > 0) ? err_sum / n_rows : -1.0;
+    }
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->rowptr = c_ptr;
+    C->col = c_col;
+    C->val = c_val;
+    C->nnz = nnz;
+    return STC_OK;
+}
 }  // namespace
 
 stc_status stc_spgemm_batched_impl(stc_handle* h, int alg, int nb, const stc_csr* A, const stc_csr* B,
@@ -1476,4 +1734,28 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
         return STC_OK;
     }
     return spgemm_window_impl(h, alg, A, B, C, opts, s);
+}
+
+stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
+                                   const float* weights, float margin, stc_learned_stats* stats,
+                                   const stc_opts* opts, stc_stream s) {
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->nnz = 0;
+    C->rowptr = nullptr;
+    C->col = nullptr;
+    C->val = nullptr;
+    if (B->ncols > RK_MAX_COLS) {
+        // wider outputs: the exact two-pass path (no capacity to predict)
+        if (stats) {
+            stats->rows = -1;
+            stats->overflow_rows = 0;
+            stats->scratch_entries = 0;
+            stats->mean_abs_log2_error = -1.0;
+        }
+        stc_status st = stc_spgemm_impl(h, alg, A, B, C, opts, s);
+        if (stats) stats->nnz = C->nnz;
+        return st;
+    }
+    return spgemm_learned_impl(h, alg, A, B, C, weights, margin, stats, !(opts && opts->skip_validation), s);
 }

@@ -454,3 +454,20 @@ extern "C" stc_status stc_mfbc(stc_handle* h, const stc_csr* G, const int32_t* s
     if (batch < 1 || batch > 256 || !bc_out) return STC_ERR_INVALID_ARG;
     return stc_mfbc_impl(h, G, sources, nsources, batch, bc_out, stream);
 }
+
+extern "C" stc_status stc_contract_spgemm_learned(stc_handle* h, stc_algebra alg, const stc_csr* A,
+                                                  const stc_csr* B, stc_csr* C, const float* weights, float margin,
+                                                  stc_learned_stats* stats, const stc_opts* opts,
+                                                  stc_stream stream) {
+    if (!h || !C) return STC_ERR_INVALID_ARG;
+    if (!alg_valid(alg)) return STC_ERR_ALGEBRA;
+    stc_status st = stc_check_csr_host(A);
+    if (st != STC_OK) return st;
+    if ((st = stc_check_csr_host(B)) != STC_OK) return st;
+    if (A->ncols != B->nrows) return STC_ERR_SHAPE;
+    if (!(margin >= 0.0f) || margin > 64.0f) return STC_ERR_INVALID_ARG;
+    if (opts)
+        for (int r : opts->reserved)
+            if (r != 0) return STC_ERR_INVALID_ARG;
+    return stc_spgemm_learned_impl(h, alg, A, B, C, weights, margin, stats, opts, stream);
+}

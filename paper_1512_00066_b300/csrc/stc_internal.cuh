@@ -178,6 +178,18 @@ stc_status stc_mfbc_sssp_impl(stc_handle* h, const stc_csr* G, const int32_t* so
 stc_status stc_mfbc_impl(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsrc, int32_t batch,
                          double* bc, stc_stream s);
 
+stc_status stc_features_impl(stc_handle* h, StcScratch& sc, const stc_csr* A, const stc_csr* B, float* feat,
+                             stc_stream s);
+stc_status stc_mlp_forward_impl(stc_handle* h, const float* w, const float* feat, int64_t n, float* y,
+                                stc_stream s);
+stc_status stc_mlp_grad_impl(stc_handle* h, const float* w, const float* feat, const float* target,
+                             const int32_t* idx, int64_t n, float scale, float* grad, float* loss, stc_stream s);
+stc_status stc_mlp_adam_impl(stc_handle* h, float* w, float* m, float* v, float* grad, int64_t step, float lr,
+                             stc_stream s);
+stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
+                                   const float* weights, float margin, stc_learned_stats* stats,
+                                   const stc_opts* opts, stc_stream s);
+
 // Inclusive scan in place of n int64 values (device), using scratch from sc.
 stc_status stc_inclusive_scan_i64(stc_handle* h, StcScratch& sc, int64_t* data, int64_t n,
                                   stc_stream s);

@@ -1,0 +1,153 @@
+"""Learned output sizing on the GPU: features, perceptron forward/gradient and
+training against the fp64 oracle, and the learned single-pass SpGEMM against the
+plain two-pass one (identical structure whatever the model predicts)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from gpu_util import compare_values, need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ALL = [O.PT_F32, O.PT_F64, O.MP_I32, O.MP_F32, O.BOOL, O.MULTPATH]
+
+
+@pytest.fixture(scope="module")
+def H():
+    need_gpu()
+    import paper_1512_00066_b300 as stc
+    return stc.Handle()
+
+
+def bf16_weights(w: torch.Tensor) -> np.ndarray:
+    return w.to(torch.bfloat16).to(torch.float64).cpu().numpy()
+
+
+def test_features_match_oracle(H):
+    A = W.rmat(11, seed=2)
+    B = W.rmat(11, seed=3)
+    f = H.row_features(to_dev(A), to_dev(B)).cpu().numpy()
+    ref = O.row_features(A, B)
+    assert np.array_equal(f[:, 3:67], ref[:, 3:].astype(np.float32))  # sketch: exact
+    assert np.allclose(f[:, :3], ref[:, :3], rtol=1e-6, atol=1e-6)
+    assert np.all(f[:, 67] == 0)
+
+
+def test_mlp_forward_and_gradient_match_oracle(H):
+    import paper_1512_00066_b300 as stc
+    w = stc.mlp_init(seed=5)
+    A = W.rmat(10, seed=4)
+    feat = H.row_features(to_dev(A), to_dev(A))
+    n = feat.shape[0]
+    target = torch.linspace(0, 8, n, device="cuda")
+    wd = bf16_weights(w)
+    x = feat[:, :67].double().cpu().numpy()
+    y = H.mlp_forward(w, feat).cpu().numpy()
+    yr = O.mlp_forward(wd, x)
+    assert np.all(np.abs(y - yr) <= 1e-4 * (1 + np.abs(yr)))
+    g, loss = H.mlp_grad(w, feat, target)
+    gr, Lr = O.mlp_grad(wd, x, target.double().cpu().numpy())
+    g = g.double().cpu().numpy()
+    assert np.linalg.norm(g - gr) <= 1e-3 * np.linalg.norm(gr)
+    assert abs(float(loss) / n - Lr) <= 1e-4 * Lr
+
+
+def _pairs(stc, seeds):
+    """Training matrices: R-MAT scales 11-14 (seeds >= 1; the evaluation graph is
+    seed 0), ER and banded matrices."""
+    out = []
+    for s in seeds:
+        for m in (W.rmat(11 + s % 4, seed=s), W.er_fixed_degree(2048 << (s % 2), 4 + 4 * (s % 4), seed=s),
+                  W.banded(4096, 1 + 8 * (s % 4), 0.5, seed=s)):
+            d = to_dev(m)
+            out.append((d, d))
+    return out
+
+
+@pytest.fixture(scope="module")
+def trained(H):
+    import paper_1512_00066_b300 as stc
+    feat, target = stc.training_rows(H, _pairs(stc, range(1, 9)))
+    w = stc.mlp_init(seed=1)
+    losses = H.mlp_train(w, feat, target, batch=2048, epochs=40, lr=2e-3, seed=3)
+    return w, losses
+
+
+def test_training_lowers_the_loss(trained):
+    w, losses = trained
+    assert losses[-1] < 0.2 * losses[0] and losses[-1] < 0.5
+
+
+def _same(alg, C, R):
+    rp, col, val = C.to_host()
+    rp2, col2, val2 = R.to_host()
+    assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
+    if alg in (O.PT_F32, O.PT_F64):
+        # same products, possibly another summation order
+        assert np.allclose(val.astype(np.float64), val2.astype(np.float64), rtol=1e-4 if alg == O.PT_F32 else 1e-12,
+                           atol=1e-5)
+    else:
+        assert val.tobytes() == val2.tobytes()
+
+
+def _vals(alg, nnz, seed):
+    rng = np.random.default_rng(seed)
+    if alg in (O.PT_F32, O.MP_F32):
+        return rng.random(nnz).astype(np.float32)
+    if alg == O.PT_F64:
+        return rng.random(nnz)
+    if alg == O.BOOL:
+        return rng.integers(0, 2, nnz).astype(np.uint8)
+    return rng.integers(1, 100, nnz).astype(np.int32)
+
+
+@pytest.mark.parametrize("alg", ALL)
+def test_learned_equals_plain_for_any_model(H, trained, alg):
+    import paper_1512_00066_b300 as stc
+    w, _ = trained
+    A = W.rmat(13, seed=9)
+    A.val = _vals(alg, A.nnz, 1)
+    B = A.with_val(_vals(alg if alg != O.MULTPATH else O.MP_I32, A.nnz, 2)) if alg != O.MULTPATH else \
+        A.with_val(W.multpath_values(A.nnz, 20, 5, 2))
+    dA, dB = to_dev(A), to_dev(B)
+    plain = H.spgemm(alg, dA, dB)
+    under = torch.zeros(stc.MLP_NUM_WEIGHTS, dtype=torch.float32, device="cuda")  # predicts 0: capacity 8
+    for weights, margin in ((w, 0.25), (None, 0.0), (under, 0.0)):
+        C, st = H.spgemm_learned(alg, dA, dB, weights, margin)
+        _same(alg, C, plain)
+        assert st["nnz"] == plain.nnz
+    C, st = H.spgemm_learned(alg, dA, dB, under, 0.0)
+    assert st["overflow_rows"] > 0  # the fallback really ran
+
+
+def test_learned_rows_against_oracle(H, trained):
+    w, _ = trained
+    A = W.rmat(12, seed=11)
+    A.val = W.weights_unit01(A.nnz, 1).astype(np.float32)
+    C, st = H.spgemm_learned(O.PT_F32, to_dev(A), to_dev(A), w, 0.25)
+    rp, col, val = C.to_host()
+    ptr, rcol, rval, rabs = O.spgemm(O.PT_F32, A, A, want_abs=True)
+    assert np.array_equal(rp, ptr) and np.array_equal(col, rcol)
+    compare_values(O.PT_F32, val, rval, rabs)
+
+
+def test_what_the_model_gains(H, trained):
+    """Trained model vs the upper-bound single pass on a held-out R-MAT: the model
+    sizes the scratch far below the bound while few rows overflow."""
+    w, _ = trained
+    A = W.rmat(14, seed=0)
+    A.val = W.weights_unit01(A.nnz, 0).astype(np.float32)
+    dA = to_dev(A)
+    _, st_ub = H.spgemm_learned(O.PT_F32, dA, dA, None, 0.0)
+    _, st_ml = H.spgemm_learned(O.PT_F32, dA, dA, w, 0.5)
+    print("scratch ub", st_ub["scratch_entries"], "model", st_ml["scratch_entries"], "nnz", st_ml["nnz"],
+          "overflow", st_ml["overflow_rows"], "/", st_ml["rows"], "err", st_ml["mean_abs_log2_error"])
+    assert st_ub["overflow_rows"] == 0
+    # scratch beyond the exact size: the model removes at least half of the bound's
+    excess_ub = st_ub["scratch_entries"] - st_ub["nnz"]
+    excess_ml = st_ml["scratch_entries"] - st_ml["nnz"]
+    assert excess_ml <= 0.5 * excess_ub
+    assert st_ml["overflow_rows"] <= 0.05 * st_ml["rows"]
+    assert 0 <= st_ml["mean_abs_log2_error"] < 0.5
