@@ -33,6 +33,11 @@ import workloads as W  # noqa: E402
 METRIC = "SpGEMM semiring-ops/s & MFBC GTEPS, learned+batched vs plain form on one B300"
 UNIT = "semiring-ops/s"
 L2_BYTES = 126 * 1024 * 1024
+# DRAM bytes (read + write) per output entry of the fp64 numeric rank kernel, from
+# the ncu capture in profiles/k_numeric_rank_fp64_rmat16.md (R-MAT scale 16:
+# 2.002e9 bytes for 163,809,247 entries).  Traffic grows with the output (B stays
+# in L2), so a full launch is scaled by its nnz(C).
+NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = 2.002e9 / 163809247
 
 
 def peaks():
@@ -296,7 +301,10 @@ def run_stc(args):
                        "l2": "flushed between timed steps (write of 2x L2)",
                        "ops_per_step": ops_total // args.steps},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "k_numeric (fp64 SpGEMM numeric pass)",
+                         "frac": achieved / hbm,
+                         "traffic": (NUMERIC_FP64_DRAM_BYTES_PER_ENTRY * nnzC if wl["scale"] else None),
+                         "traffic_note": "ncu capture at R-MAT scale 16 scaled by nnz(C)",
+                         "kernel": "k_numeric_rank (fp64 SpGEMM numeric pass)",
                          "peak_source": peak_kind, "algorithmic_bytes": compulsory, "kernel_ms": num_ms,
                          "gather_model_bytes": gather_model},
             "gpu_launches": launches,
