@@ -505,6 +505,7 @@ constexpr int RK_MAX_COLS = 1 << 18;        // 32 KB bitmap
 constexpr int RK_NT = 1024;     // numeric kernel: one CTA per SM, large value buffer
 constexpr int RK_SYM_NT = 256;  // symbolic kernel: more rows in flight per SM
 constexpr size_t RK_SMEM_TARGET = 224 * 1024;  // one CTA per SM
+constexpr double RK_RECORD_BUDGET = 24e9;        // bytes of stored rank records
 
 template <int NT>
 struct TaskSmem {
@@ -629,6 +630,28 @@ __device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t* summ, int col)
     }
 }
 
+struct RankLayout {
+    size_t bits, summ, wpre, cellbase, winfirst, vals, scol, sig, total;
+};
+
+__host__ __device__ inline size_t rk_align(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline RankLayout rank_layout(int ncell, int vcap, int maxwin, size_t acc_bytes,
+                                                  bool multpath) {
+    RankLayout L;
+    const size_t NW = size_t(ncell) * 32;
+    L.bits = 0;
+    L.summ = rk_align(L.bits + NW * 4);
+    L.wpre = rk_align(L.summ + size_t(ncell) * 4);
+    L.cellbase = rk_align(L.wpre + NW * 2);
+    L.winfirst = rk_align(L.cellbase + (size_t(ncell) + 1) * 4);
+    L.vals = rk_align(L.winfirst + (size_t(maxwin) + 1) * 4);
+    L.scol = rk_align(L.vals + size_t(vcap) * acc_bytes);
+    L.sig = rk_align(L.scol + size_t(vcap) * 4);
+    L.total = multpath ? rk_align(L.sig + size_t(vcap) * 8) : L.sig;
+    return L;
+}
+
 // Persistent-CTA row loop over a row list of global rows: thread 0 resolves the
 // row's matrix into shared memory.  Returns the global row or -1.
 __device__ __forceinline__ int64_t next_row_b(int* counter, int nlist, const int32_t* rowlist, const SpgRows& R,
@@ -649,6 +672,7 @@ __device__ __forceinline__ int64_t next_row_b(int* counter, int nlist, const int
         }
         s_row[0] = gi;
         s_row[1] = li;
+        s_row[2] = r;
     }
     __syncthreads();
     return s_row[0];
@@ -657,16 +681,24 @@ __device__ __forceinline__ int64_t next_row_b(int* counter, int nlist, const int
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
-                int* __restrict__ counter, int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz) {
+                int* __restrict__ counter, int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz,
+                uint4* __restrict__ rec) {
     extern __shared__ uint4 smem_raw[];
+    // same offsets as the numeric kernel's layout (bitmap, summary, word prefix, cell prefix)
+    const RankLayout L = rank_layout(ncell_max, 0, 0, 4, false);
     const int NWmax = ncell_max * 32;
-    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw);
-    uint32_t* summ = bits + NWmax;  // one summary word per cell
+    unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(sm + L.bits);
+    uint32_t* summ = reinterpret_cast<uint32_t*>(sm + L.summ);  // one summary word per cell
+    uint16_t* wpre = reinterpret_cast<uint16_t*>(sm + L.wpre);
+    int* cellbase = reinterpret_cast<int*>(sm + L.cellbase);
+    const int rec16 = int(L.winfirst / 16);  // record size in 16-byte words
     __shared__ TaskSmem<NT> ts;
     __shared__ SpgArgs s_args;
-    __shared__ int64_t s_row[2];
+    __shared__ int64_t s_row[3];
     __shared__ int s_red[NT / 32 + 1];
-    for (int w = threadIdx.x; w < NWmax + ncell_max; w += NT) bits[w] = 0u;
+    for (int w = threadIdx.x; w < NWmax; w += NT) bits[w] = 0u;
+    for (int c = threadIdx.x; c < ncell_max; c += NT) summ[c] = 0u;
     const int nlist = *nlist_ptr;
     int local_max = 0;
     for (;;) {
@@ -684,17 +716,62 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
             });
             __syncthreads();
         }
-        int cnt = 0;
-        for (int w = threadIdx.x; w < NW; w += NT) {
-            const uint32_t b = bits[w];
-            if (b) {
-                cnt += __popc(b);
-                bits[w] = 0u;
-            }
-        }
-        for (int c = threadIdx.x; c < g.ncell; c += NT) summ[c] = 0u;
         int tot;
-        (void)block_exclusive_scan<NT, int>(cnt, s_red, tot);
+        if (rec) {
+            // ranks: word prefix inside each cell and the cells' exclusive prefix;
+            // the whole rank structure is stored for the numeric pass
+            constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;
+            int cnt[CPT];
+            int ctot = 0;
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = threadIdx.x * CPT + q;
+                int n = 0;
+                if (c < g.ncell) {
+                    uint32_t sw = summ[c];
+                    while (sw) {
+                        const int w = c * 32 + __ffs(sw) - 1;
+                        sw &= sw - 1;
+                        wpre[w] = uint16_t(n);
+                        n += __popc(bits[w]);
+                    }
+                }
+                cnt[q] = n;
+                ctot += n;
+            }
+            int ex = block_exclusive_scan<NT, int>(ctot, s_red, tot);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = threadIdx.x * CPT + q;
+                if (c < g.ncell) cellbase[c] = ex;
+                ex += cnt[q];
+            }
+            if (threadIdx.x == 0) cellbase[g.ncell] = tot;
+            __syncthreads();
+            uint4* dst = rec + s_row[2] * int64_t(rec16);
+            for (int q = threadIdx.x; q < rec16; q += NT) dst[q] = smem_raw[q];
+            __syncthreads();
+            for (int c = threadIdx.x; c < g.ncell; c += NT) {
+                uint32_t sw = summ[c];
+                summ[c] = 0u;
+                while (sw) {
+                    const int w = c * 32 + __ffs(sw) - 1;
+                    sw &= sw - 1;
+                    bits[w] = 0u;
+                }
+            }
+        } else {
+            int cnt = 0;
+            for (int w = threadIdx.x; w < NW; w += NT) {
+                const uint32_t b = bits[w];
+                if (b) {
+                    cnt += __popc(b);
+                    bits[w] = 0u;
+                }
+            }
+            for (int c = threadIdx.x; c < g.ncell; c += NT) summ[c] = 0u;
+            (void)block_exclusive_scan<NT, int>(cnt, s_red, tot);
+        }
         if (threadIdx.x == 0) {
             row_nnz[gi] = tot;
             local_max = max(local_max, tot);
@@ -789,34 +866,12 @@ __global__ void k_batch_bounds(SpgRows R, const int64_t* __restrict__ c_ptr, int
         out[b] = c_ptr[R.row_off[b]];
 }
 
-struct RankLayout {
-    size_t bits, summ, wpre, cellbase, winfirst, vals, scol, sig, total;
-};
-
-__host__ __device__ inline size_t rk_align(size_t x) { return (x + 15) & ~size_t(15); }
-
-__host__ __device__ inline RankLayout rank_layout(int ncell, int vcap, int maxwin, size_t acc_bytes,
-                                                  bool multpath) {
-    RankLayout L;
-    const size_t NW = size_t(ncell) * 32;
-    L.bits = 0;
-    L.summ = rk_align(L.bits + NW * 4);
-    L.wpre = rk_align(L.summ + size_t(ncell) * 4);
-    L.cellbase = rk_align(L.wpre + NW * 2);
-    L.winfirst = rk_align(L.cellbase + (size_t(ncell) + 1) * 4);
-    L.vals = rk_align(L.winfirst + (size_t(maxwin) + 1) * 4);
-    L.scol = rk_align(L.vals + size_t(vcap) * acc_bytes);
-    L.sig = rk_align(L.scol + size_t(vcap) * 4);
-    L.total = multpath ? rk_align(L.sig + size_t(vcap) * 8) : L.sig;
-    return L;
-}
-
 template <int ALG, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                int* __restrict__ counter, RankOut out, int32_t* __restrict__ c_col,
-               void* __restrict__ c_val, int* __restrict__ flags) {
+               void* __restrict__ c_val, int* __restrict__ flags, const uint4* __restrict__ rec) {
     using T = Tr<ALG>;
     using AT = typename T::A;
     using BT = typename T::B;
@@ -835,7 +890,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
     __shared__ TaskSmem<NT> ts;
     __shared__ AT s_aval[NT];
     __shared__ SpgArgs s_args;
-    __shared__ int64_t s_row[2];
+    __shared__ int64_t s_row[3];
     __shared__ int s_warp[NT / 32 + 1];
     __shared__ int s_nwin;
 
@@ -861,6 +916,16 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         const int64_t o0 = out.ptr[gi];
         const int64_t o1 = out.cap ? o0 + out.cap[gi] : out.ptr[gi + 1];
 
+        int total;
+        if (rec) {
+            // the symbolic pass stored this row's bitmap, word prefixes and cell prefixes
+            const int rec16 = int(L.winfirst / 16);
+            const uint4* src = rec + s_row[2] * int64_t(rec16);
+            for (int q = threadIdx.x; q < rec16; q += NT) smem_raw[q] = src[q];
+            __syncthreads();
+            total = cellbase[ncell];
+            __syncthreads();
+        } else {
         // 1) bitmap of the row's columns
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
             const int ntasks = load_tasks<NT, AT, false>(g, nullptr, 0, p0, ahi, 0, 0, ts, nullptr);
@@ -870,7 +935,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             __syncthreads();
         }
 
-        // 2) ranks: word prefix inside each cell, cell prefix, windows; columns of C
+        // 2) ranks: word prefix inside each cell, cell prefix
         constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;  // cells per thread (upper bound)
         int cnt[CPT];
         int ctot = 0;
@@ -879,10 +944,10 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             const int c = threadIdx.x * CPT + q;
             int n = 0;
             if (c < ncell) {
-                uint32_t s = summ[c];
-                while (s) {
-                    const int w = c * 32 + __ffs(s) - 1;
-                    s &= s - 1;
+                uint32_t sw = summ[c];
+                while (sw) {
+                    const int w = c * 32 + __ffs(sw) - 1;
+                    sw &= sw - 1;
                     wpre[w] = uint16_t(n);
                     n += __popc(bits[w]);
                 }
@@ -890,13 +955,13 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             cnt[q] = n;
             ctot += n;
         }
-        int total;
         int ex = block_exclusive_scan<NT, int>(ctot, s_warp, total);
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
             const int c = threadIdx.x * CPT + q;
             if (c < ncell) cellbase[c] = ex;
             ex += cnt[q];
+        }
         }
         if (threadIdx.x == 0) {
             cellbase[ncell] = total;
@@ -1051,7 +1116,7 @@ struct RankCfg {
 template <int ALG, int NT, int MINB>
 stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
                                const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
-                               int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+                               int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, stc_stream s) {
     auto kern = k_numeric_rank<ALG, NT, MINB>;
     STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)));
     int per_sm = 0;
@@ -1060,7 +1125,7 @@ stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, c
     int64_t grid = int64_t(per_sm) * h->num_sms;
     if (grid > NR) grid = NR > 0 ? NR : 1;
     kern<<<unsigned(grid), NT, cfg.smem, s>>>(R, ncell_max, cfg.vcap, cfg.maxwin, rowlist, nlist, counter, out,
-                                              c_col, c_val, h->d_flags);
+                                              c_col, c_val, h->d_flags, rec);
     STC_LAUNCH_CHECK();
     stc_count(h);
     return STC_OK;
@@ -1069,24 +1134,24 @@ stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, c
 template <int ALG>
 stc_status run_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
                             const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
-                            int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+                            int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, stc_stream s) {
     if (cfg.small)
         return launch_numeric_rank<ALG, 256, 4>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
-                                                NR, s);
+                                                NR, rec, s);
     return launch_numeric_rank<ALG, RK_NT, 1>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
-                                              NR, s);
+                                              NR, rec, s);
 }
 
 stc_status run_numeric_any(stc_handle* h, int alg, const SpgRows& R, int ncell_max, const RankCfg& cfg,
                            const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
-                           int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+                           int32_t* c_col, void* c_val, int64_t NR, stc_stream s, const uint4* rec = nullptr) {
     switch (alg) {
-    case ALG_PT_F32: return run_numeric_rank<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
-    case ALG_PT_F64: return run_numeric_rank<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
-    case ALG_MP_I32: return run_numeric_rank<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
-    case ALG_MP_F32: return run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
-    case ALG_BOOL: return run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
-    case ALG_MULTPATH: return run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, s);
+    case ALG_PT_F32: return run_numeric_rank<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
+    case ALG_PT_F64: return run_numeric_rank<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
+    case ALG_MP_I32: return run_numeric_rank<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
+    case ALG_MP_F32: return run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
+    case ALG_BOOL: return run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
+    case ALG_MULTPATH: return run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
     default: return STC_ERR_ALGEBRA;
     }
 }
@@ -1188,8 +1253,16 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         stc_count(h, 3);
     }
     stc_mark(h, s, 2);
+    // stored rank records (bitmap, word and cell prefixes per listed row) when they
+    // fit the budget; otherwise the numeric pass rebuilds them
+    const size_t rec_bytes = rank_layout(ncell_max, 0, 0, 4, false).winfirst;
+    uint4* rec = nullptr;
+    if (NR > 0 && double(NR) * double(rec_bytes) <= RK_RECORD_BUDGET) {
+        rec = sc.get<uint4>(size_t(NR) * (rec_bytes / 16));
+        if (!rec) return fail(STC_ERR_OOM);
+    }
     if (NR > 0) {
-        const size_t smem = size_t(ncell_max) * 33 * 4;
+        const size_t smem = rec_bytes;
         auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
         STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         int per_sm = 0;
@@ -1197,7 +1270,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         if (per_sm < 1) return fail(STC_ERR_CUDA);
         int64_t grid = int64_t(per_sm) * h->num_sms;
         if (grid > NR) grid = NR;
-        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell_max, rowlist, nlist, counters, c_ptr + 1, max_nnz);
+        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell_max, rowlist, nlist, counters, c_ptr + 1, max_nnz, rec);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h);
     }
@@ -1271,7 +1344,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         RankOut out{};
         out.ptr = c_ptr;
         if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, nlist, counters + 1, out, c_col, c_val, NR,
-                                  s)) != STC_OK)
+                                  s, rec)) != STC_OK)
             return fail(st);
     }
     stc_mark(h, s, 5);
