@@ -513,6 +513,7 @@ struct TaskSmem {
     int len[NT];      // segment length
     int64_t lo[NT];   // first B position of the segment
     int warp[NT / 32 + 1];
+    int next;         // next unclaimed warp task (warps claim tasks dynamically)
 };
 
 // Segments of the chunk [p0, p0+NT) of A_i: whole B rows, or (ctab != null) the
@@ -549,6 +550,7 @@ __device__ __forceinline__ int load_tasks(const SpgArgs& g, const int32_t* __res
     ts.len[threadIdx.x] = len;
     ts.lo[threadIdx.x] = lo;
     if (WITH_VAL) s_aval[threadIdx.x] = av;
+    if (threadIdx.x == 0) ts.next = NT / 32;  // tasks 0..NT/32-1 go to warps 0..NT/32-1
     __syncthreads();
     return total;
 }
@@ -556,10 +558,10 @@ __device__ __forceinline__ int load_tasks(const SpgArgs& g, const int32_t* __res
 // Run op(p, col, j) for every product of the loaded chunk (p: B position,
 // j: index of the A entry in the chunk).  Columns are loaded RK_SUB/32 at a time.
 template <int NT, class Op>
-__device__ __forceinline__ void walk_tasks(const SpgArgs& g, const TaskSmem<NT>& ts, int ntasks, Op op) {
+__device__ __forceinline__ void walk_tasks(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks, Op op) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int U = RK_SUB / 32;
-    for (int t = wid; t < ntasks; t += NT / 32) {
+    for (int t = wid; t < ntasks;) {
         const int j = find_seg<NT>(ts.pre, t);
         const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
         const int64_t end = ts.lo[j] + ts.len[j];
@@ -581,22 +583,26 @@ __device__ __forceinline__ void walk_tasks(const SpgArgs& g, const TaskSmem<NT>&
                 if (p < end) op(p, col[u], j);
             }
         }
+        int nt = 0;
+        if (lane == 0) nt = atomicAdd(&ts.next, 1);
+        t = __shfl_sync(0xffffffffu, nt, 0);
     }
 }
 
 // As walk_tasks, also loading the B values of the task up front:
 // op(p, col, val, j).
-template <int NT, class BT, class Op>
-__device__ __forceinline__ void walk_tasks_val(const SpgArgs& g, const TaskSmem<NT>& ts, int ntasks,
-                                               const BT* __restrict__ bval, Op op) {
+template <int NT, class AT, class BT, class Op>
+__device__ __forceinline__ void walk_tasks_val(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
+                                               const AT* s_aval, const BT* __restrict__ bval, Op op) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int U = RK_SUB / 32;
-    for (int t = wid; t < ntasks; t += NT / 32) {
+    for (int t = wid; t < ntasks;) {
         const int j = find_seg<NT>(ts.pre, t);
         const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
         const int64_t end = ts.lo[j] + ts.len[j];
         const int64_t span = end - start;
         const int nu = span >= RK_SUB ? U : int((span + 31) >> 5);
+        const AT a = s_aval[j];
         int col[U];
         BT val[U];
 #pragma unroll
@@ -615,9 +621,12 @@ __device__ __forceinline__ void walk_tasks_val(const SpgArgs& g, const TaskSmem<
         for (int u = 0; u < U; ++u) {
             if (u < nu) {
                 const int64_t p = start + lane + 32 * u;
-                if (p < end) op(p, col[u], val[u], j);
+                if (p < end) op(col[u], val[u], a);
             }
         }
+        int nt = 0;
+        if (lane == 0) nt = atomicAdd(&ts.next, 1);
+        t = __shfl_sync(0xffffffffu, nt, 0);
     }
 }
 
@@ -630,8 +639,23 @@ __device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t* summ, int col)
     }
 }
 
+// Shared-memory layout of the numeric rank kernel; its prefix [0, winfirst) is
+// also the per-row record the symbolic pass stores:
+//   wb[NW]        uint2 per bitmap word: x = the word's bits, y = rank (position in
+//                 the output row) of the word's first present column
+//   summ[ncell]   bit w%32 of summ[w/32] set when word w is non-zero
+//   cellbase[ncell+1]  rank of the first present column of each 1024-column cell
+__device__ __forceinline__ void set_bit2(uint32_t* wbx, uint32_t* summ, int col) {
+    const int w = col >> 5;
+    const uint32_t m = 1u << (col & 31);
+    if (!(wbx[2 * w] & m)) {
+        uint32_t old = atomicOr(&wbx[2 * w], m);
+        if (old == 0u) atomicOr(&summ[w >> 5], 1u << (w & 31));
+    }
+}
+
 struct RankLayout {
-    size_t bits, summ, wpre, cellbase, winfirst, vals, scol, sig, total;
+    size_t wb, summ, cellbase, winfirst, vals, scol, sig, total;
 };
 
 __host__ __device__ inline size_t rk_align(size_t x) { return (x + 15) & ~size_t(15); }
@@ -640,15 +664,31 @@ __host__ __device__ inline RankLayout rank_layout(int ncell, int vcap, int maxwi
                                                   bool multpath) {
     RankLayout L;
     const size_t NW = size_t(ncell) * 32;
-    L.bits = 0;
-    L.summ = rk_align(L.bits + NW * 4);
-    L.wpre = rk_align(L.summ + size_t(ncell) * 4);
-    L.cellbase = rk_align(L.wpre + NW * 2);
+    L.wb = 0;
+    L.summ = rk_align(L.wb + NW * 8);
+    L.cellbase = rk_align(L.summ + size_t(ncell) * 4);
     L.winfirst = rk_align(L.cellbase + (size_t(ncell) + 1) * 4);
     L.vals = rk_align(L.winfirst + (size_t(maxwin) + 1) * 4);
     L.scol = rk_align(L.vals + size_t(vcap) * acc_bytes);
     L.sig = rk_align(L.scol + size_t(vcap) * 4);
     L.total = multpath ? rk_align(L.sig + size_t(vcap) * 8) : L.sig;
+    return L;
+}
+
+// Shared-memory layout of the symbolic rank kernel: compact bitmap, summary, per
+// word prefix inside its cell, cell prefix.
+struct SymLayout {
+    size_t bits, summ, wpre, cellbase, total;
+};
+
+__host__ __device__ inline SymLayout sym_layout(int ncell) {
+    SymLayout L;
+    const size_t NW = size_t(ncell) * 32;
+    L.bits = 0;
+    L.summ = rk_align(NW * 4);
+    L.wpre = rk_align(L.summ + size_t(ncell) * 4);
+    L.cellbase = rk_align(L.wpre + NW * 2);
+    L.total = rk_align(L.cellbase + (size_t(ncell) + 1) * 4);
     return L;
 }
 
@@ -684,15 +724,15 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
                 int* __restrict__ counter, int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz,
                 uint4* __restrict__ rec) {
     extern __shared__ uint4 smem_raw[];
-    // same offsets as the numeric kernel's layout (bitmap, summary, word prefix, cell prefix)
-    const RankLayout L = rank_layout(ncell_max, 0, 0, 4, false);
+    const SymLayout L = sym_layout(ncell_max);
+    const RankLayout LR = rank_layout(ncell_max, 0, 0, 4, false);  // record layout
     const int NWmax = ncell_max * 32;
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
     uint32_t* bits = reinterpret_cast<uint32_t*>(sm + L.bits);
     uint32_t* summ = reinterpret_cast<uint32_t*>(sm + L.summ);  // one summary word per cell
     uint16_t* wpre = reinterpret_cast<uint16_t*>(sm + L.wpre);
     int* cellbase = reinterpret_cast<int*>(sm + L.cellbase);
-    const int rec16 = int(L.winfirst / 16);  // record size in 16-byte words
+    const int64_t rec_bytes = int64_t(LR.winfirst);
     __shared__ TaskSmem<NT> ts;
     __shared__ SpgArgs s_args;
     __shared__ int64_t s_row[3];
@@ -748,8 +788,21 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
             }
             if (threadIdx.x == 0) cellbase[g.ncell] = tot;
             __syncthreads();
-            uint4* dst = rec + s_row[2] * int64_t(rec16);
-            for (int q = threadIdx.x; q < rec16; q += NT) dst[q] = smem_raw[q];
+            // the record, in the numeric kernel's layout: (bits, rank of the word) pairs,
+            // the summary and the cell prefix
+            unsigned char* dst = reinterpret_cast<unsigned char*>(rec) + s_row[2] * rec_bytes;
+            uint4* dwb = reinterpret_cast<uint4*>(dst + LR.wb);
+            for (int q = threadIdx.x; q < NWmax / 2; q += NT) {
+                const int w = 2 * q;
+                const uint32_t b0 = bits[w], b1 = bits[w + 1];
+                const int c = w >> 5;  // w and w + 1 share a cell
+                dwb[q] = make_uint4(b0, b0 ? uint32_t(cellbase[c] + wpre[w]) : 0u, b1,
+                                    b1 ? uint32_t(cellbase[c] + wpre[w + 1]) : 0u);
+            }
+            uint32_t* dsumm = reinterpret_cast<uint32_t*>(dst + LR.summ);
+            for (int c = threadIdx.x; c < ncell_max; c += NT) dsumm[c] = summ[c];
+            int* dcb = reinterpret_cast<int*>(dst + LR.cellbase);
+            for (int c = threadIdx.x; c <= ncell_max; c += NT) dcb[c] = c <= g.ncell ? cellbase[c] : tot;
             __syncthreads();
             for (int c = threadIdx.x; c < g.ncell; c += NT) {
                 uint32_t sw = summ[c];
@@ -879,9 +932,9 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
     extern __shared__ uint4 smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
     const RankLayout L = rank_layout(ncell_max, vcap, maxwin, sizeof(Acc), ALG == ALG_MULTPATH);
-    uint32_t* bits = reinterpret_cast<uint32_t*>(sm + L.bits);
+    uint2* wb = reinterpret_cast<uint2*>(sm + L.wb);
+    uint32_t* wbx = reinterpret_cast<uint32_t*>(sm + L.wb);  // x of word w at 2w, y at 2w + 1
     uint32_t* summ = reinterpret_cast<uint32_t*>(sm + L.summ);
-    uint16_t* wpre = reinterpret_cast<uint16_t*>(sm + L.wpre);
     int* cellbase = reinterpret_cast<int*>(sm + L.cellbase);
     int* winfirst = reinterpret_cast<int*>(sm + L.winfirst);
     Acc* vals = reinterpret_cast<Acc*>(sm + L.vals);
@@ -894,7 +947,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
     __shared__ int s_warp[NT / 32 + 1];
     __shared__ int s_nwin;
 
-    for (int w = threadIdx.x; w < ncell_max * 32; w += NT) bits[w] = 0u;
+    for (int w = threadIdx.x; w < ncell_max * 32; w += NT) wb[w] = make_uint2(0u, 0u);
     for (int c = threadIdx.x; c < ncell_max; c += NT) summ[c] = 0u;
     for (int r = threadIdx.x; r < vcap; r += NT) {
         vals[r] = T::empty();
@@ -930,12 +983,12 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
             const int ntasks = load_tasks<NT, AT, false>(g, nullptr, 0, p0, ahi, 0, 0, ts, nullptr);
             walk_tasks<NT>(g, ts, ntasks, [&](int64_t, int col, int) {
-                if ((uint64_t)col < (uint64_t)g.ncols) set_bit(bits, summ, col);
+                if ((uint64_t)col < (uint64_t)g.ncols) set_bit2(wbx, summ, col);
             });
             __syncthreads();
         }
 
-        // 2) ranks: word prefix inside each cell, cell prefix
+        // 2) ranks: prefix inside each cell, cells' prefix, then absolute word ranks
         constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;  // cells per thread (upper bound)
         int cnt[CPT];
         int ctot = 0;
@@ -948,8 +1001,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                 while (sw) {
                     const int w = c * 32 + __ffs(sw) - 1;
                     sw &= sw - 1;
-                    wpre[w] = uint16_t(n);
-                    n += __popc(bits[w]);
+                    wbx[2 * w + 1] = uint32_t(n);
+                    n += __popc(wbx[2 * w]);
                 }
             }
             cnt[q] = n;
@@ -959,7 +1012,15 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
             const int c = threadIdx.x * CPT + q;
-            if (c < ncell) cellbase[c] = ex;
+            if (c < ncell) {
+                cellbase[c] = ex;
+                uint32_t sw = summ[c];
+                while (sw) {
+                    const int w = c * 32 + __ffs(sw) - 1;
+                    sw &= sw - 1;
+                    wbx[2 * w + 1] += uint32_t(ex);
+                }
+            }
             ex += cnt[q];
         }
         }
@@ -994,30 +1055,29 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             const int rcount = cellbase[ch] - rb;
             const int32_t* tab = nwin > 1 ? g.ctab : nullptr;
             auto rank_of = [&](int col) -> int {
-                const int w = col >> 5;
-                return cellbase[col >> RK_CELL_SHIFT] + wpre[w] +
-                       __popc(bits[w] & ((1u << (col & 31)) - 1u)) - rb;
+                const uint2 e = wb[col >> 5];
+                return int(e.y) + __popc(e.x & ((1u << (col & 31)) - 1u)) - rb;
             };
             for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
                 const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
-                walk_tasks_val<NT, BT>(g, ts, ntasks, bval, [&](int64_t, int col, const BT& b, int j) {
+                walk_tasks_val<NT, AT, BT>(g, ts, ntasks, s_aval, bval, [&](int col, const BT& b, const AT a) {
                     if ((uint64_t)col >= (uint64_t)g.ncols) return;
                     const int r = rank_of(col);
                     if ((unsigned)r >= (unsigned)rcount) return;
                     scol[r] = col;
-                    if constexpr (ALG == ALG_MULTPATH) atomicMin(&vals[r], s_aval[j] + b.d);
-                    else T::combine(vals, r, s_aval[j], b);
+                    if constexpr (ALG == ALG_MULTPATH) atomicMin(&vals[r], a + b.d);
+                    else T::combine(vals, r, a, b);
                 });
                 __syncthreads();
             }
             if constexpr (ALG == ALG_MULTPATH) {
                 for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
                     const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
-                    walk_tasks_val<NT, BT>(g, ts, ntasks, bval, [&](int64_t, int col, const BT& b, int j) {
+                    walk_tasks_val<NT, AT, BT>(g, ts, ntasks, s_aval, bval, [&](int col, const BT& b, const AT a) {
                         if ((uint64_t)col >= (uint64_t)g.ncols) return;
                         const int r = rank_of(col);
                         if ((unsigned)r >= (unsigned)rcount) return;
-                        if (s_aval[j] + b.d == vals[r]) atomicAdd(&sig[r], b.s);
+                        if (a + b.d == vals[r]) atomicAdd(&sig[r], b.s);
                     });
                     __syncthreads();
                 }
@@ -1048,7 +1108,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             while (s) {
                 const int w = c * 32 + __ffs(s) - 1;
                 s &= s - 1;
-                bits[w] = 0u;
+                wbx[2 * w] = 0u;
             }
         }
     }
@@ -1262,7 +1322,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         if (!rec) return fail(STC_ERR_OOM);
     }
     if (NR > 0) {
-        const size_t smem = rec_bytes;
+        const size_t smem = sym_layout(ncell_max).total;
         auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
         STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         int per_sm = 0;
