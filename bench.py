@@ -283,6 +283,7 @@ def run_stc(args):
     forms = {}
     if not args.no_forms and wl["scale"] is not None and rank == 0:
         H.set_timing(False)
+        forms["bellman_ford_drivers"] = measure_bf_drivers(stc, H, wl)
         forms["learned_vs_plain"] = measure_learned(stc, H, wl, dev)
         forms["batched_vs_per_call"] = measure_batched(stc, H)
         forms["mfbc"] = measure_mfbc(stc, H)
@@ -403,6 +404,19 @@ def measure_batched(stc, H):
     return {"unit": UNIT, "workload": "4096 pairs, rows power-law [64,16384] exp 2.1, U{4..64}/row, N(0,1) fp32",
             "products": nprod, "batched": nprod / t_b, "per_call": nprod / t_p,
             "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p}}
+
+
+def measure_bf_drivers(stc, H, wl):
+    """Bellman-Ford (min,+) fp32 from vertex 0 on the workload graph with the three
+    drivers: host loop (one launch + one read-back per round), one cooperative
+    persistent launch, one CUDA graph with a conditional WHILE node."""
+    A = wl["A"]
+    dg = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["g32"])
+    out = {"unit": "ms", "workload": "rmat18 (min,+) fp32 from vertex 0"}
+    for name, mode in (("host_loop", 0), ("persistent", 1), ("cuda_graph", 2)):
+        H.bellman_ford(stc.MIN_PLUS_F32, dg, 0, persistent=mode)  # warm
+        out[name] = 1e3 * _timed(lambda: H.bellman_ford(stc.MIN_PLUS_F32, dg, 0, persistent=mode), 5)
+    return out
 
 
 def measure_mfbc(stc, H, scale=22, nsrc=256):

@@ -239,9 +239,12 @@ STC_API stc_status stc_check_device_status(stc_handle* h, stc_stream stream);
  * Each round relaxes only the out-edges of vertices whose distance decreased in
  * the previous round (frontier), which reaches the same fixed point as full
  * relaxation: for fp32 the minimum over paths of the left-to-right rounded path
- * sums, bit for bit.  `persistent` = 1 runs all rounds inside one cooperative
- * launch with a device-side convergence test; 0 launches one kernel per round
- * and reads the frontier size on the host each round.  Synchronises `stream`.
+ * sums, bit for bit.  `persistent` selects the driver: 0 launches one kernel per
+ * round and reads the frontier size on the host each round; 1 runs all rounds
+ * inside one cooperative launch with a bounded grid barrier and a device-side
+ * convergence test; 2 launches one CUDA graph whose conditional WHILE node
+ * repeats {relaxation round, termination test}, the test setting the loop
+ * condition on the device (no host round trip per round).  Synchronises `stream`.
  * Errors: STC_ERR_NEG_CYCLE when round |V| still lowers a distance (a negative
  * cycle is reachable), STC_ERR_TIMEOUT when a bounded grid barrier gives up,
  * plus the argument and CSR errors above.

@@ -332,9 +332,13 @@ class Handle:
     def check_device_status(self, stream=None):
         _check(lib().stc_check_device_status(self._h, _stream_ptr(stream)), "stc_check_device_status")
 
-    def bellman_ford(self, alg: int, G: DeviceCsr, source: int, persistent: bool = True,
+    def bellman_ford(self, alg: int, G: DeviceCsr, source: int, persistent=True,
                      dist: Optional[torch.Tensor] = None, stream=None):
-        """Shortest distances from `source` over out-edge CSR G; returns (dist, rounds)."""
+        """Shortest distances from `source` over out-edge CSR G; returns (dist, rounds).
+
+        persistent: False / 0 host loop, True / 1 cooperative persistent launch,
+        2 or "graph" CUDA graph with a conditional WHILE node."""
+        persistent = 2 if persistent == "graph" else int(persistent)
         if dist is None:
             dist = torch.empty(G.nrows, dtype=torch.int32 if alg == MIN_PLUS_I32 else torch.float32,
                                device=G.col.device)
@@ -342,7 +346,7 @@ class Handle:
         relax = ctypes.c_int64(0)
         g = G._c()
         st = lib().stc_bellman_ford(self._h, alg, ctypes.byref(g), int(source), dist.data_ptr(),
-                                    ctypes.byref(rounds), ctypes.byref(relax), 1 if persistent else 0,
+                                    ctypes.byref(rounds), ctypes.byref(relax), persistent,
                                     _stream_ptr(stream))
         _check(st, "stc_bellman_ford")
         self.last_relaxations = int(relax.value)

@@ -164,6 +164,36 @@ __global__ void __launch_bounds__(BF_NT) k_bf_persistent(BfArgs a, typename BfT<
     if (blockIdx.x == 0 && threadIdx.x == 0) *rounds_out = changed_rounds;
 }
 
+// Graph form: the round index lives on the device; the body of a conditional
+// WHILE node runs this kernel then k_bf_check.
+template <int ALG>
+__global__ void __launch_bounds__(BF_NT) k_bf_round_dev(BfArgs a, typename BfT<ALG>::D* dist, const int* d_round) {
+    const int r = *d_round;
+    const int ncur = a.cnt[r % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt[(r + 2) % 3] = 0;
+    relax_round<ALG>(a, dist, r, a.frontier[r & 1], ncur, a.frontier[(r + 1) & 1], &a.cnt[(r + 1) % 3]);
+}
+
+// Termination test of the graph form (one thread): stop when the round produced
+// an empty frontier, or flag a negative cycle when |V| rounds all changed
+// something; otherwise advance the round and run the body again.
+__global__ void k_bf_check(BfArgs a, int* d_round, int* d_changed, int* flags, cudaGraphConditionalHandle loop) {
+    const int r = *d_round;
+    const int nnext = a.cnt[(r + 1) % 3];
+    unsigned go = 0;
+    if (nnext > 0) {
+        const int changed = *d_changed + 1;
+        *d_changed = changed;
+        if (int64_t(changed) >= a.n) {
+            atomicOr(flags, STC_FLAG_NEG_CYCLE);
+        } else {
+            *d_round = r + 1;
+            go = 1;
+        }
+    }
+    cudaGraphSetConditional(loop, go);
+}
+
 template <int ALG>
 __global__ void k_bf_finish(int64_t n, const typename BfT<ALG>::D* key, void* out) {
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
@@ -188,7 +218,8 @@ stc_status run_bf(stc_handle* h, const stc_csr* G, int32_t source, void* dist_ou
     a.frontier[0] = sc.get<int32_t>(size_t(n));
     a.frontier[1] = sc.get<int32_t>(size_t(n));
     a.stamp = sc.get<int>(size_t(n));
-    int* ints = sc.get<int>(16);  // [0..2] counters, [4..5] barrier, [6] rounds, [8..9] relaxations
+    int* ints = sc.get<int>(16);  // [0..2] counters, [4..5] barrier, [6] rounds, [8..9] relaxations,
+                                  // [10] round and [11] changed rounds of the graph form
     D* dist = ALG == ALG_MP_I32 ? reinterpret_cast<D*>(dist_out) : sc.get<D>(size_t(n));
     if (sc.failed) return STC_ERR_OOM;
     a.cnt = ints;
@@ -222,6 +253,63 @@ stc_status run_bf(stc_handle* h, const stc_csr* G, int32_t source, void* dist_ou
         STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[2], a.relax, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[1], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
         STC_CUDA_TRY(cudaStreamSynchronize(s));
+        rounds = reinterpret_cast<int*>(&h->h_stage[0])[0];
+    } else if (persistent == 2) {
+        // graph form: one CUDA graph whose conditional WHILE node repeats {round, check}
+        int* d_round = ints + 10;
+        int* d_changed = ints + 11;
+        int* flags = h->d_flags;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        stc_status gst = STC_OK;
+        do {
+            if (cudaGraphCreate(&graph, 0) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
+            cudaGraphConditionalHandle loop;
+            if (cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+                gst = STC_ERR_CUDA;
+                break;
+            }
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = loop;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            if (cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            void* round_args[] = {&a, &dist, &d_round};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void*)k_bf_round_dev<ALG>;
+            kp.gridDim = dim3(h->num_sms * 4);
+            kp.blockDim = dim3(BF_NT);
+            kp.kernelParams = round_args;
+            cudaGraphNode_t n1, n2;
+            if (cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
+            void* check_args[] = {&a, &d_round, &d_changed, &flags, &loop};
+            cudaKernelNodeParams kc = {};
+            kc.func = (void*)k_bf_check;
+            kc.gridDim = dim3(1);
+            kc.blockDim = dim3(1);
+            kc.kernelParams = check_args;
+            if (cudaGraphAddKernelNode(&n2, body, &n1, 1, &kc) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
+            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
+            if (cudaGraphLaunch(exec, s) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
+            stc_count(h, 2);  // the body's two kernels (repeated on the device)
+        } while (0);
+        if (gst != STC_OK) {
+            (void)cudaGetLastError();
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            return gst;
+        }
+        stc_mark(h, s, 2);
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[0], d_changed, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[1], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[2], a.relax, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        const cudaError_t se = cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        STC_CUDA_TRY(se);
         rounds = reinterpret_cast<int*>(&h->h_stage[0])[0];
     } else {
         // plain form: one launch per round, frontier size read back each round

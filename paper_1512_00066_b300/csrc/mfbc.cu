@@ -26,7 +26,6 @@
 namespace {
 
 constexpr int MF_NT = 256;       // one thread per source of the batch
-constexpr int MF_MAX_S = 256;
 constexpr int MF_ITEM_EDGES = 1024;  // out-edges of one vertex handled by one block
 constexpr int MF_INF = STC_MIN_PLUS_I32_IDENTITY;
 
@@ -127,7 +126,11 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st, i
         for (int64_t p = e0; p < e1; ++p) {
             const int32_t v = g.col[p];
             if ((uint64_t)v >= (uint64_t)g.n) continue;
-            if (act) atomicMin(&st.dn[int64_t(v) * S + s], du + edge_len(g, p));
+            if (act) {
+                const int cand = du + edge_len(g, p);
+                int* dst = &st.dn[int64_t(v) * S + s];
+                if (cand < *dst) atomicMin(dst, cand);  // most candidates cannot improve
+            }
             if (s == 0 && atomicExch(&st.stamp[v], round) != round)
                 st.list[1][atomicAdd(&st.cnt[1], 1)] = v;
         }

@@ -422,6 +422,7 @@ extern "C" stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc
     if (st != STC_OK) return st;
     if (G->nrows != G->ncols) return STC_ERR_SHAPE;
     if (source < 0 || source >= G->nrows) return STC_ERR_INVALID_ARG;
+    if (persistent < 0 || persistent > 2) return STC_ERR_INVALID_ARG;
     return stc_bellman_ford_impl(h, alg, G, source, dist_out, rounds_out, relaxations_out, persistent,
                                  stream);
 }

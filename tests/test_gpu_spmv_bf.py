@@ -90,7 +90,7 @@ def test_spmm_all_algebras(H, alg, ncol, accumulate):
         assert got.tobytes() == ref.tobytes()
 
 
-@pytest.mark.parametrize("persistent", [True, False])
+@pytest.mark.parametrize("persistent", [True, False, "graph"])
 def test_bellman_ford_rmat14(H, persistent):
     G = W.rmat(14, seed=21)
     G.val = W.weights_int(G.nnz, 1, 1000, 22)
@@ -114,6 +114,8 @@ def test_bellman_ford_rmat18_full_size(H):
     assert d.cpu().numpy().tobytes() == ref.tobytes()
     d2, r2 = H.bellman_ford(O.MP_F32, to_dev(G), 0, persistent=False)
     assert d2.cpu().numpy().tobytes() == ref.tobytes()
+    d3, r3 = H.bellman_ford(O.MP_F32, to_dev(G), 0, persistent="graph")
+    assert d3.cpu().numpy().tobytes() == ref.tobytes()
 
 
 def test_bellman_ford_closed_forms_and_cycles(H):
@@ -121,7 +123,7 @@ def test_bellman_ford_closed_forms_and_cycles(H):
     n = 1000
     L = W.csr_from_coo(np.arange(n - 1), np.arange(1, n), n, n)
     L.val = np.full(n - 1, 7, np.int32)
-    for persistent in (True, False):
+    for persistent in (True, False, "graph"):
         d, r = H.bellman_ford(O.MP_I32, to_dev(L), 0, persistent=persistent)
         assert np.array_equal(d.cpu().numpy(), 7 * np.arange(n)) and r == n - 1
         d, r = H.bellman_ford(O.MP_I32, to_dev(L), 500, persistent=persistent)
@@ -133,13 +135,13 @@ def test_bellman_ford_closed_forms_and_cycles(H):
     rows = np.repeat(np.arange(3000), np.diff(G.rowptr))
     G.val = (rng.integers(1, 50, G.nnz) + pot[G.col] - pot[rows]).astype(np.int32)
     ref, _ = O.bellman_ford(O.MP_I32, G, 0)
-    for persistent in (True, False):
+    for persistent in (True, False, "graph"):
         d, _ = H.bellman_ford(O.MP_I32, to_dev(G), 0, persistent=persistent)
         assert np.array_equal(d.cpu().numpy(), ref)
     # reachable negative cycle -> status
     C = W.csr_from_coo([0, 1, 2], [1, 2, 1], 3, 3)
     C.val = np.array([4, 2, -3], np.int32)
-    for persistent in (True, False):
+    for persistent in (True, False, "graph"):
         with pytest.raises(stc.StcError) as e:
             H.bellman_ford(O.MP_I32, to_dev(C), 0, persistent=persistent)
         assert e.value.status == 7
