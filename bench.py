@@ -428,11 +428,27 @@ def measure_mfbc(stc, H, scale=22, nsrc=256):
     out = {"unit": "GTEPS", "workload": f"rmat{scale}, {nsrc} sources (one batch)", "edges": G.nnz}
     for name, val in (("unit_lengths", None), ("int_lengths_1_255", W.weights_int(G.nnz, 1, 255, seed=1))):
         d = stc.DeviceCsr.from_host(G.nrows, G.ncols, G.rowptr, G.col, val)
-        t = _timed(lambda: H.mfbc(d, src, batch=nsrc), 1)
-        out[name] = nsrc * G.nnz / t / 1e9
-        out[name + "_ms"] = 1e3 * t
+        for drv in ("graph", "host"):
+            H.set_round_driver(drv)
+            t = _timed(lambda: H.mfbc(d, src, batch=nsrc), 1)
+            key = name if drv == "graph" else name + "_host_driver"
+            out[key] = nsrc * G.nnz / t / 1e9
+            out[key + "_ms"] = 1e3 * t
+        H.set_round_driver("graph")
         del d
         torch.cuda.empty_cache()
+    # many small batches: the per-round host round trip against one graph per batch
+    Gs = W.rmat(16, seed=0)
+    srcs = W.sample_sources(Gs, 1024, seed=0)
+    ds = stc.DeviceCsr.from_host(Gs.nrows, Gs.ncols, Gs.rowptr, Gs.col, W.weights_int(Gs.nnz, 1, 255, seed=1))
+    small = {"workload": "rmat16, int lengths 1..255, 1024 sources in batches of 64"}
+    for drv in ("graph", "host"):
+        H.set_round_driver(drv)
+        t = _timed(lambda: H.mfbc(ds, srcs, batch=64), 3)
+        small[drv + "_ms"] = 1e3 * t
+        small[drv + "_gteps"] = len(srcs) * Gs.nnz / t / 1e9
+    H.set_round_driver("graph")
+    out["small_batches"] = small
     return out
 
 

@@ -264,8 +264,10 @@ STC_API stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc_cs
  * d_out (device, int32 [G->nrows][nsources]) receives d_s(v) (INT_MAX/2 when v is
  * unreachable from s); sigma_out (device, fp64 [G->nrows][nsources]) the number of
  * shortest s-v paths (exact while below 2^53).  *rounds_out (host, may be NULL):
- * rounds run.  Synchronises `stream` once per round.  Errors: argument/CSR
- * errors, STC_ERR_INVALID_ARG for a length < 1.
+ * rounds run.  The rounds run under the handle's round driver (see
+ * stc_set_round_driver); either way the call synchronises `stream` before it
+ * returns.  Errors: argument/CSR errors, STC_ERR_INVALID_ARG for a length < 1 or
+ * a graph with nrows + nnz / 1024 + 2 above INT32_MAX.
  */
 STC_API stc_status stc_mfbc_sssp(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources,
                                  int32_t* d_out, double* sigma_out, int32_t* rounds_out, stc_stream stream);
@@ -278,10 +280,26 @@ STC_API stc_status stc_mfbc_sssp(stc_handle* h, const stc_csr* G, const int32_t*
  * Directed; no normalisation or halving.  Sources are processed in batches of
  * `batch` (1..256) columns at a time; device memory ~ 32 * G->nrows * batch bytes.
  * G, sources and lengths as for stc_mfbc_sssp; bc_out: device fp64 [G->nrows],
- * overwritten.  Synchronises `stream` once per round of each phase.
+ * overwritten.  Runs under the handle's round driver; synchronises `stream`
+ * before it returns.
  */
 STC_API stc_status stc_mfbc(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources,
                             int32_t batch, double* bc_out, stc_stream stream);
+
+/*
+ * Round driver of the multi-round betweenness-centrality calls above (the paper
+ * runs its iterations from the host; this is a device-side form of the same loop).
+ *   driver = 0: host-driven -- each round's kernels are launched from the host,
+ *               which reads the loop condition back after every round (one
+ *               stream synchronisation per round);
+ *   driver = 1: (default) each batch is one CUDA graph launch: the forward and
+ *               backward round loops are conditional WHILE nodes whose condition
+ *               a one-thread check kernel sets on the device, so no round needs
+ *               the host.
+ * Both drivers launch the same kernels and give identical results.  Errors:
+ * STC_ERR_INVALID_ARG for a null handle or another value.
+ */
+STC_API stc_status stc_set_round_driver(stc_handle* h, int32_t driver);
 
 /*
  * Learned output sizing (no counterpart in the paper, which leaves SpGEMM and

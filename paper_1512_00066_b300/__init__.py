@@ -113,6 +113,8 @@ def lib():
                                            ctypes.POINTER(i32), ctypes.POINTER(i64), i32, p]
             L.stc_bellman_ford.restype = ctypes.c_int
             L.stc_set_timing.argtypes = [p, i32]
+            L.stc_set_round_driver.argtypes = [p, i32]
+            L.stc_set_round_driver.restype = ctypes.c_int
             L.stc_set_timing.restype = ctypes.c_int
             L.stc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_float), i32]
             L.stc_phase_times.restype = i32
@@ -430,6 +432,12 @@ class Handle:
                             int(batch), bc.data_ptr(), _stream_ptr(stream))
         _check(st, "stc_mfbc")
         return bc
+
+    def set_round_driver(self, driver: str = "graph"):
+        """Round loops of mfbc / mfbc_sssp: "graph" (one CUDA graph launch per
+        batch, conditional WHILE nodes) or "host" (host-driven rounds)."""
+        code = {"host": 0, "graph": 1}[driver]
+        _check(lib().stc_set_round_driver(self._h, code), "stc_set_round_driver")
 
     # -------------------------------------------------------------- instrumentation
 

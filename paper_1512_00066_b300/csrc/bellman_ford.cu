@@ -236,7 +236,7 @@ stc_status run_bf(stc_handle* h, const stc_csr* G, int32_t source, void* dist_ou
     stc_mark(h, s, 1);
 
     int rounds = 0;
-    if (persistent) {
+    if (persistent == 1) {
         int per_sm = 0;
         STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bf_persistent<ALG>, BF_NT, 0));
         if (per_sm < 1) return STC_ERR_CUDA;

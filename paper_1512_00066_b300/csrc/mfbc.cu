@@ -28,6 +28,19 @@ namespace {
 constexpr int MF_NT = 256;       // one thread per source of the batch
 constexpr int MF_ITEM_EDGES = 1024;  // out-edges of one vertex handled by one block
 constexpr int MF_INF = STC_MIN_PLUS_I32_IDENTITY;
+constexpr int MF_BLOCKS_PER_SM = 8;  // fixed grids of the round kernels (2048 threads per SM)
+
+// Device counters (MfState::cnt).  Both round loops keep their round index and
+// list sizes here, so a round never needs a value from the host.
+enum : int {
+    MF_C_READY = 0,    // [0], [1]: backward ready-list sizes (by round parity)
+    MF_C_TOUCHED = 2,  // forward touched-list size
+    MF_C_ITEMS = 3,    // [3], [4]: forward work-item counts (by round parity)
+    MF_C_FROUND = 5,   // forward round index
+    MF_C_BROUND = 6,   // backward round index
+    MF_C_GO = 7,       // 1 while the last checked loop goes on (read by the host driver)
+    MF_C_NUM = 8,
+};
 
 struct MfGraph {
     int64_t n, nnz;
@@ -44,14 +57,28 @@ struct MfState {
     double* dl;      // [n][S] multiplicity not yet propagated; dependency backward
     double* dln;     // [n][S] multiplicity gathered in the round
     int* stamp;      // [n] round stamp of list membership
-    int32_t* list[2];  // frontier / touched lists
-    int64_t* iprefix;  // work-item prefix over the frontier
-    int* cnt;        // [0] frontier size, [1] touched size, [2] next size
+    int32_t* list[2];  // forward: list[1] touched vertices; backward: ready lists
+    int2* items[2];    // forward frontier work items {vertex, chunk of MF_ITEM_EDGES edges}
+    int* cnt;          // MF_C_* counters
 };
 
 __device__ __forceinline__ int edge_len(const MfGraph& g, int64_t p) { return g.w ? g.w[p] : 1; }
 
-__global__ void k_mf_init(MfGraph g, MfState st, const int32_t* __restrict__ src) {
+// Select a double-buffered array by parity without indexing the kernel
+// parameter (a dynamic index would copy the struct to local memory).
+template <class T>
+__device__ __forceinline__ T* mf_pick(T* const (&a)[2], int k) { return (k & 1) ? a[1] : a[0]; }
+
+// Work items of a frontier vertex: one per MF_ITEM_EDGES out-edges, at least one
+// (the item with chunk 0 also clears the vertex's pending multiplicity).
+__device__ __forceinline__ int mf_chunks(const MfGraph& g, int32_t u) {
+    int64_t lo, hi;
+    row_range(g.ptr, u, g.nnz, lo, hi);
+    const int64_t c = (hi - lo + MF_ITEM_EDGES - 1) / MF_ITEM_EDGES;
+    return c > 1 ? int(c) : 1;
+}
+
+__global__ void k_mf_init(MfGraph g, MfState st) {
     const int S = st.S;
     const int64_t tot = g.n * S;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < tot;
@@ -65,61 +92,49 @@ __global__ void k_mf_init(MfGraph g, MfState st, const int32_t* __restrict__ src
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < g.n;
          v += int64_t(gridDim.x) * blockDim.x)
         st.stamp[v] = -1;
+    if (blockIdx.x == 0 && threadIdx.x < MF_C_NUM) st.cnt[threadIdx.x] = 0;
 }
 
-// Sources: distance 0, one path, one pending multiplicity; frontier = sources.
+// Sources: distance 0, one path, one pending multiplicity; their work items form
+// the frontier of round 0.
 __global__ void k_mf_seed(MfGraph g, MfState st, const int32_t* __restrict__ src) {
     const int s = threadIdx.x;
     if (s < st.S) {
-        const int64_t v = src[s];
-        const int64_t i = v * st.S + s;
+        const int32_t v = src[s];
+        const int64_t i = int64_t(v) * st.S + s;
         st.d[i] = 0;
         st.dn[i] = 0;
         st.sig[i] = 1.0;
         st.dl[i] = 1.0;
-        if (atomicExch(&st.stamp[v], -2) != -2) st.list[0][atomicAdd(&st.cnt[0], 1)] = int32_t(v);
+        if (atomicExch(&st.stamp[v], -2) != -2) {
+            const int nch = mf_chunks(g, v);
+            const int base = atomicAdd(&st.cnt[MF_C_ITEMS], nch);
+            for (int c = 0; c < nch; ++c) st.items[0][base + c] = make_int2(v, c);
+        }
     }
 }
 
-// Work items of the frontier: vertex u contributes ceil(deg(u) / MF_ITEM_EDGES).
-__global__ void k_mf_items(MfGraph g, const int32_t* __restrict__ F, const int* __restrict__ nF,
-                           int64_t* __restrict__ count) {
-    const int n = *nF;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int64_t lo, hi;
-        row_range(g.ptr, F[i], g.nnz, lo, hi);
-        count[i] = (hi - lo + MF_ITEM_EDGES - 1) / MF_ITEM_EDGES;
-    }
-}
-
-// Locate work item t: frontier index j (largest with prefix[j] <= t, prefix inclusive
-// of the item counts shifted: excl[j] = incl[j] - count[j]).
-__device__ __forceinline__ int mf_find(const int64_t* __restrict__ incl, int n, int64_t t) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (incl[mid] > t) hi = mid; else lo = mid + 1;
-    }
-    return lo;
+// Edge range of a work item.
+__device__ __forceinline__ void mf_item_edges(const MfGraph& g, int2 it, int64_t& e0, int64_t& e1) {
+    int64_t lo, hi;
+    row_range(g.ptr, it.x, g.nnz, lo, hi);
+    e0 = lo + int64_t(it.y) * MF_ITEM_EDGES;
+    e1 = min(hi, e0 + MF_ITEM_EDGES);
 }
 
 // Phase A of a round: dn[v][s] = min(dn[v][s], d[u][s] + w) over frontier edges
 // with pending multiplicity; every target is listed once as touched.
-__global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st, int round) {
+__global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st) {
     const int S = st.S;
     const int s = threadIdx.x;
-    const int nF = st.cnt[0];
-    if (nF == 0) return;
-    const int64_t nitems = st.iprefix[nF - 1];
-    const int32_t* F = st.list[0];
-    for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
-        const int j = mf_find(st.iprefix, nF, t);
-        const int64_t first = j > 0 ? st.iprefix[j - 1] : 0;
-        const int32_t u = F[j];
-        int64_t lo, hi;
-        row_range(g.ptr, u, g.nnz, lo, hi);
-        const int64_t e0 = lo + (t - first) * MF_ITEM_EDGES;
-        const int64_t e1 = min(hi, e0 + MF_ITEM_EDGES);
+    const int r = st.cnt[MF_C_FROUND];
+    const int nitems = st.cnt[MF_C_ITEMS + (r & 1)];
+    const int2* __restrict__ F = mf_pick(st.items, r);
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        const int2 it = F[t];
+        const int32_t u = it.x;
+        int64_t e0, e1;
+        mf_item_edges(g, it, e0, e1);
         const bool act = s < S && st.dl[int64_t(u) * S + s] > 0.0;
         const int du = act ? st.d[int64_t(u) * S + s] : 0;
         if (!__syncthreads_or(act)) continue;
@@ -131,8 +146,8 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st, i
                 int* dst = &st.dn[int64_t(v) * S + s];
                 if (cand < *dst) atomicMin(dst, cand);  // most candidates cannot improve
             }
-            if (s == 0 && atomicExch(&st.stamp[v], round) != round)
-                st.list[1][atomicAdd(&st.cnt[1], 1)] = v;
+            if (s == 0 && atomicExch(&st.stamp[v], r) != r)
+                st.list[1][atomicAdd(&st.cnt[MF_C_TOUCHED], 1)] = v;
         }
     }
 }
@@ -141,18 +156,14 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st, i
 __global__ void __launch_bounds__(MF_NT) k_mf_relax_add(MfGraph g, MfState st) {
     const int S = st.S;
     const int s = threadIdx.x;
-    const int nF = st.cnt[0];
-    if (nF == 0) return;
-    const int64_t nitems = st.iprefix[nF - 1];
-    const int32_t* F = st.list[0];
-    for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
-        const int j = mf_find(st.iprefix, nF, t);
-        const int64_t first = j > 0 ? st.iprefix[j - 1] : 0;
-        const int32_t u = F[j];
-        int64_t lo, hi;
-        row_range(g.ptr, u, g.nnz, lo, hi);
-        const int64_t e0 = lo + (t - first) * MF_ITEM_EDGES;
-        const int64_t e1 = min(hi, e0 + MF_ITEM_EDGES);
+    const int r = st.cnt[MF_C_FROUND];
+    const int nitems = st.cnt[MF_C_ITEMS + (r & 1)];
+    const int2* __restrict__ F = mf_pick(st.items, r);
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        const int2 it = F[t];
+        const int32_t u = it.x;
+        int64_t e0, e1;
+        mf_item_edges(g, it, e0, e1);
         const double m = s < S ? st.dl[int64_t(u) * S + s] : 0.0;
         const bool act = m > 0.0;
         const int du = act ? st.d[int64_t(u) * S + s] : 0;
@@ -167,24 +178,28 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_add(MfGraph g, MfState st) {
     }
 }
 
-// The frontier has sent its multiplicities.
+// The frontier has sent its multiplicities (each vertex once: its chunk-0 item).
 __global__ void __launch_bounds__(MF_NT) k_mf_clear_frontier(MfState st) {
     const int S = st.S;
-    const int nF = st.cnt[0];
-    for (int b = blockIdx.x; b < nF; b += gridDim.x) {
-        const int32_t u = st.list[0][b];
-        if (threadIdx.x < S) st.dl[int64_t(u) * S + threadIdx.x] = 0.0;
+    const int r = st.cnt[MF_C_FROUND];
+    const int nitems = st.cnt[MF_C_ITEMS + (r & 1)];
+    const int2* __restrict__ F = mf_pick(st.items, r);
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        const int2 it = F[t];
+        if (it.y == 0 && threadIdx.x < S) st.dl[int64_t(it.x) * S + threadIdx.x] = 0.0;
     }
 }
 
-// Apply the round to every touched vertex; those with pending multiplicity form
-// the next frontier (written to list[0] after the swap done by the host driver:
-// here into list[0] of the next round, passed as `next`).
-__global__ void __launch_bounds__(MF_NT) k_mf_update(MfState st, int32_t* __restrict__ next,
-                                                     int* __restrict__ cnt_next) {
+// Apply the round to every touched vertex; those left with pending multiplicity
+// append their work items to the frontier of the next round.
+__global__ void __launch_bounds__(MF_NT) k_mf_update(MfGraph g, MfState st) {
     const int S = st.S;
     const int s = threadIdx.x;
-    const int nT = st.cnt[1];
+    const int r = st.cnt[MF_C_FROUND];
+    const int nT = st.cnt[MF_C_TOUCHED];
+    int2* __restrict__ next = mf_pick(st.items, r + 1);
+    int* ncnt = &st.cnt[MF_C_ITEMS + ((r + 1) & 1)];
+    __shared__ int s_base, s_nch;
     for (int b = blockIdx.x; b < nT; b += gridDim.x) {
         const int32_t v = st.list[1][b];
         bool act = false;
@@ -205,16 +220,44 @@ __global__ void __launch_bounds__(MF_NT) k_mf_update(MfState st, int32_t* __rest
             }
             st.dln[i] = 0.0;
         }
-        if (__syncthreads_or(act) && s == 0) next[atomicAdd(cnt_next, 1)] = v;
+        if (!__syncthreads_or(act)) continue;
+        if (s == 0) {
+            s_nch = mf_chunks(g, v);
+            s_base = atomicAdd(ncnt, s_nch);
+        }
+        __syncthreads();
+        for (int c = s; c < s_nch; c += blockDim.x) next[s_base + c] = make_int2(v, c);
+        __syncthreads();
     }
+}
+
+// End of a forward round (one thread): stop when the next frontier is empty (or,
+// as a guard, after |V| + 2 rounds, flagged); otherwise advance the round index
+// and empty the lists the next round fills.  In the graph driver the result is
+// the condition of the WHILE node; the host driver reads MF_C_GO.
+__global__ void k_mf_fwd_check(MfState st, int64_t n, int* flags, int in_graph, cudaGraphConditionalHandle loop) {
+    const int r = st.cnt[MF_C_FROUND];
+    const int nnext = st.cnt[MF_C_ITEMS + ((r + 1) & 1)];
+    unsigned go = 0;
+    if (nnext > 0) {
+        if (int64_t(r) + 1 > n + 1) {
+            atomicOr(flags, STC_FLAG_NEG_CYCLE);
+        } else {
+            st.cnt[MF_C_FROUND] = r + 1;
+            st.cnt[MF_C_ITEMS + (r & 1)] = 0;
+            st.cnt[MF_C_TOUCHED] = 0;
+            go = 1;
+        }
+    }
+    st.cnt[MF_C_GO] = int(go);
+    if (in_graph) cudaGraphSetConditional(loop, go);
 }
 
 // ------------------------------------------------------------------- backward
 
 // c[v][s] = number of out-edges v -> x on a shortest path from s (into st.dn);
 // vertices with a reachable source and no successor are ready.
-__global__ void __launch_bounds__(MF_NT) k_mf_succ(MfGraph g, MfState st, int32_t* __restrict__ ready,
-                                                   int* __restrict__ nready) {
+__global__ void __launch_bounds__(MF_NT) k_mf_succ(MfGraph g, MfState st) {
     const int S = st.S;
     const int s = threadIdx.x;
     for (int64_t v = blockIdx.x; v < g.n; v += gridDim.x) {
@@ -235,17 +278,22 @@ __global__ void __launch_bounds__(MF_NT) k_mf_succ(MfGraph g, MfState st, int32_
             st.dl[i] = 0.0;
         }
         const bool rd = dv < MF_INF && c == 0;
-        if (__syncthreads_or(rd) && s == 0) ready[atomicAdd(nready, 1)] = int32_t(v);
+        if (__syncthreads_or(rd) && s == 0) st.list[0][atomicAdd(&st.cnt[MF_C_READY], 1)] = int32_t(v);
     }
 }
 
 // One backward round over the ready vertices (in-edge CSR gt: row w lists v -> w).
-__global__ void __launch_bounds__(MF_NT) k_mf_back(MfGraph gt, MfState st, const int32_t* __restrict__ ready,
-                                                   const int* __restrict__ nready, int32_t* __restrict__ next,
-                                                   int* __restrict__ nnext, int round) {
+// Round r reads ready list r & 1 and fills the other one.
+__global__ void __launch_bounds__(MF_NT) k_mf_back(MfGraph gt, MfState st) {
     const int S = st.S;
     const int s = threadIdx.x;
-    const int nR = *nready;
+    const int r = st.cnt[MF_C_BROUND];
+    const int cur = r & 1;
+    const int nR = st.cnt[MF_C_READY + cur];
+    const int32_t* __restrict__ ready = mf_pick(st.list, cur);
+    int32_t* __restrict__ next = mf_pick(st.list, cur ^ 1);
+    int* nnext = &st.cnt[MF_C_READY + (cur ^ 1)];
+    const int stamp = r + (1 << 30);  // disjoint from the forward rounds' stamps
     for (int b = blockIdx.x; b < nR; b += gridDim.x) {
         const int32_t w = ready[b];
         const int64_t iw = int64_t(w) * S + s;
@@ -269,11 +317,31 @@ __global__ void __launch_bounds__(MF_NT) k_mf_back(MfGraph gt, MfState st, const
             if (st.d[iv] + edge_len(gt, p) == dw) {
                 atomicAdd(&st.dl[iv], st.sig[iv] * coef);
                 // the source whose count reaches zero lists v (once per round)
-                if (atomicSub(&st.dn[iv], 1) == 1 && atomicExch(&st.stamp[v], round) != round)
+                if (atomicSub(&st.dn[iv], 1) == 1 && atomicExch(&st.stamp[v], stamp) != stamp)
                     next[atomicAdd(nnext, 1)] = v;
             }
         }
     }
+}
+
+// End of a backward round (one thread), as k_mf_fwd_check.  Every vertex becomes
+// ready at most once per source, so more than |V| + 1 rounds means a fault of the
+// successor counts (flagged as internal).
+__global__ void k_mf_back_check(MfState st, int64_t n, int* flags, int in_graph, cudaGraphConditionalHandle loop) {
+    const int r = st.cnt[MF_C_BROUND];
+    const int nnext = st.cnt[MF_C_READY + ((r + 1) & 1)];
+    unsigned go = 0;
+    if (nnext > 0) {
+        if (int64_t(r) + 1 > n + 1) {
+            atomicOr(flags, STC_FLAG_INTERNAL);
+        } else {
+            st.cnt[MF_C_BROUND] = r + 1;
+            st.cnt[MF_C_READY + (r & 1)] = 0;
+            go = 1;
+        }
+    }
+    st.cnt[MF_C_GO] = int(go);
+    if (in_graph) cudaGraphSetConditional(loop, go);
 }
 
 // bc[v] += sum over sources s != v of delta_s(v).
@@ -345,46 +413,181 @@ unsigned grid_for(stc_handle* h, int64_t work, int per_sm) {
     return unsigned(work < cap ? work : cap);
 }
 
-// Forward phase for one batch (sources on the device, S of them).
-stc_status mf_forward(stc_handle* h, StcScratch& sc, const MfGraph& g, MfState& st, const int32_t* d_src,
-                      int64_t* d_count, stc_stream s, int* rounds_out) {
-    STC_CUDA_TRY(cudaMemsetAsync(st.cnt, 0, 4 * sizeof(int), s));
-    k_mf_init<<<grid_for(h, g.n * st.S / 256 + 1, 16), 256, 0, s>>>(g, st, d_src);
-    k_mf_seed<<<1, MF_NT, 0, s>>>(g, st, d_src);
+// One batch: sources on the device (S = st.S of them); bc == null runs the
+// forward phase only.
+struct MfBatch {
+    MfGraph g, gt;
+    MfState st;
+    const int32_t* src;
+    double* bc;
+};
+
+unsigned mf_round_grid(stc_handle* h) { return unsigned(h->num_sms * MF_BLOCKS_PER_SM); }
+unsigned mf_init_grid(stc_handle* h, const MfBatch& b) { return grid_for(h, b.g.n * b.st.S / 256 + 1, 16); }
+
+// Host driver: each round's kernels, then MF_C_GO read back (one synchronisation
+// per round).
+stc_status mf_run_host(stc_handle* h, const MfBatch& b, stc_stream s) {
+    const MfGraph& g = b.g;
+    const MfState& st = b.st;
+    const unsigned rg = mf_round_grid(h);
+    const cudaGraphConditionalHandle none = 0;
+    int* go = reinterpret_cast<int*>(&h->h_stage[4]);
+    k_mf_init<<<mf_init_grid(h, b), 256, 0, s>>>(g, st);
+    k_mf_seed<<<1, MF_NT, 0, s>>>(g, st, b.src);
     STC_LAUNCH_CHECK();
     stc_count(h, 2);
-    int* h_cnt = reinterpret_cast<int*>(&h->h_stage[4]);
-    int rounds = 0;
-    for (int r = 0;; ++r) {
-        // the frontier is list[0] with size cnt[0]
-        STC_CUDA_TRY(cudaMemcpyAsync(h_cnt, &st.cnt[0], sizeof(int), cudaMemcpyDeviceToHost, s));
+    for (;;) {
+        k_mf_relax_min<<<rg, MF_NT, 0, s>>>(g, st);
+        k_mf_relax_add<<<rg, MF_NT, 0, s>>>(g, st);
+        k_mf_clear_frontier<<<rg, MF_NT, 0, s>>>(st);
+        k_mf_update<<<rg, MF_NT, 0, s>>>(g, st);
+        k_mf_fwd_check<<<1, 1, 0, s>>>(st, g.n, h->d_flags, 0, none);
+        STC_LAUNCH_CHECK();
+        stc_count(h, 5);
+        STC_CUDA_TRY(cudaMemcpyAsync(go, &st.cnt[MF_C_GO], sizeof(int), cudaMemcpyDeviceToHost, s));
         STC_CUDA_TRY(cudaStreamSynchronize(s));
-        const int nF = *h_cnt;
-        if (nF == 0) break;
-        if (int64_t(r) > g.n + 1) {
-            int f = STC_FLAG_NEG_CYCLE;
-            STC_CUDA_TRY(cudaMemcpyAsync(h->d_flags, &f, sizeof(int), cudaMemcpyHostToDevice, s));
-            break;
-        }
-        ++rounds;
-        k_mf_items<<<grid_for(h, (nF + 255) / 256, 8), 256, 0, s>>>(g, st.list[0], &st.cnt[0], d_count);
-        STC_LAUNCH_CHECK();
-        stc_count(h);
-        stc_status e = stc_inclusive_scan_i64(h, sc, d_count, nF, s);
-        if (e != STC_OK) return e;
-        st.iprefix = d_count;
-        STC_CUDA_TRY(cudaMemsetAsync(&st.cnt[1], 0, 2 * sizeof(int), s));
-        const unsigned gb = grid_for(h, int64_t(nF) * 4, 16);
-        k_mf_relax_min<<<gb, MF_NT, 0, s>>>(g, st, r);
-        k_mf_relax_add<<<gb, MF_NT, 0, s>>>(g, st);
-        k_mf_clear_frontier<<<grid_for(h, nF, 16), MF_NT, 0, s>>>(st);
-        // next frontier into the frontier list slot after the update reads it
-        k_mf_update<<<grid_for(h, int64_t(nF) * 8, 16), MF_NT, 0, s>>>(st, st.list[0], &st.cnt[2]);
-        STC_LAUNCH_CHECK();
-        stc_count(h, 4);
-        STC_CUDA_TRY(cudaMemcpyAsync(&st.cnt[0], &st.cnt[2], sizeof(int), cudaMemcpyDeviceToDevice, s));
+        if (!*go) break;
     }
-    if (rounds_out) *rounds_out = rounds;
+    if (!b.bc) return STC_OK;
+    k_mf_succ<<<grid_for(h, g.n, 32), MF_NT, 0, s>>>(g, st);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    for (;;) {
+        k_mf_back<<<rg, MF_NT, 0, s>>>(b.gt, st);
+        k_mf_back_check<<<1, 1, 0, s>>>(st, g.n, h->d_flags, 0, none);
+        STC_LAUNCH_CHECK();
+        stc_count(h, 2);
+        STC_CUDA_TRY(cudaMemcpyAsync(go, &st.cnt[MF_C_GO], sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!*go) break;
+    }
+    k_mf_bc<<<grid_for(h, g.n, 32), MF_NT, 0, s>>>(st, g.n, b.src, b.bc);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return STC_OK;
+}
+
+// Graph driver: one CUDA graph per batch shape,
+//   init -> seed -> WHILE{relax_min -> relax_add -> clear -> update -> check}
+//        [-> successors -> WHILE{back -> check} -> bc],
+// each WHILE condition set on the device by its check kernel, so a batch is one
+// graph launch with no host round trip.  Kernel arguments (state pointers, S) are
+// fixed at build time; the batch's sources are copied into `src` before a launch.
+struct MfGraphExec {
+    cudaStream_t stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int S = -1;
+    int nodes = 0;
+    explicit MfGraphExec(stc_stream s) : stream(static_cast<cudaStream_t>(s)) {}
+    void reset() {
+        if (exec) {
+            (void)cudaStreamSynchronize(stream);  // no launch of it left in flight
+            cudaGraphExecDestroy(exec);
+        }
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        S = -1;
+        nodes = 0;
+    }
+    ~MfGraphExec() { reset(); }
+};
+
+cudaError_t mf_add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, const cudaGraphNode_t* dep, const void* func,
+                          unsigned grid, unsigned block, void** args) {
+    cudaKernelNodeParams p = {};
+    p.func = const_cast<void*>(func);
+    p.gridDim = dim3(grid);
+    p.blockDim = dim3(block);
+    p.kernelParams = args;
+    return cudaGraphAddKernelNode(node, gr, dep, dep ? 1 : 0, &p);
+}
+
+cudaError_t mf_add_while(cudaGraph_t top, cudaGraphNode_t* node, const cudaGraphNode_t* dep,
+                         cudaGraphConditionalHandle* cond, cudaGraph_t* body) {
+    cudaError_t e = cudaGraphConditionalHandleCreate(cond, top, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = *cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(node, top, dep, nullptr, dep ? 1 : 0, &cp);
+    if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+    return e;
+}
+
+#define MF_G(call)                                  \
+    do {                                            \
+        const cudaError_t e_ = (call);              \
+        if (e_ != cudaSuccess) return e_;           \
+    } while (0)
+
+cudaError_t mf_build_graph(stc_handle* h, MfBatch b, MfGraphExec& x) {
+    x.reset();
+    MF_G(cudaGraphCreate(&x.graph, 0));
+    const unsigned rg = mf_round_grid(h);
+    int* flags = h->d_flags;
+    int in_graph = 1;
+    int64_t n = b.g.n;
+    cudaGraphNode_t n_init, n_seed, n_fw;
+    void* a_init[] = {&b.g, &b.st};
+    MF_G(mf_add_kernel(x.graph, &n_init, nullptr, (const void*)k_mf_init, mf_init_grid(h, b), 256, a_init));
+    void* a_seed[] = {&b.g, &b.st, &b.src};
+    MF_G(mf_add_kernel(x.graph, &n_seed, &n_init, (const void*)k_mf_seed, 1, MF_NT, a_seed));
+    cudaGraphConditionalHandle hf;
+    cudaGraph_t fb;
+    MF_G(mf_add_while(x.graph, &n_fw, &n_seed, &hf, &fb));
+    {
+        cudaGraphNode_t k1, k2, k3, k4, k5;
+        void* a_gs[] = {&b.g, &b.st};
+        void* a_st[] = {&b.st};
+        void* a_chk[] = {&b.st, &n, &flags, &in_graph, &hf};
+        MF_G(mf_add_kernel(fb, &k1, nullptr, (const void*)k_mf_relax_min, rg, MF_NT, a_gs));
+        MF_G(mf_add_kernel(fb, &k2, &k1, (const void*)k_mf_relax_add, rg, MF_NT, a_gs));
+        MF_G(mf_add_kernel(fb, &k3, &k2, (const void*)k_mf_clear_frontier, rg, MF_NT, a_st));
+        MF_G(mf_add_kernel(fb, &k4, &k3, (const void*)k_mf_update, rg, MF_NT, a_gs));
+        MF_G(mf_add_kernel(fb, &k5, &k4, (const void*)k_mf_fwd_check, 1, 1, a_chk));
+    }
+    x.nodes = 7;
+    if (b.bc) {
+        cudaGraphNode_t n_succ, n_bw, n_bc;
+        void* a_succ[] = {&b.g, &b.st};
+        MF_G(mf_add_kernel(x.graph, &n_succ, &n_fw, (const void*)k_mf_succ, grid_for(h, n, 32), MF_NT, a_succ));
+        cudaGraphConditionalHandle hb;
+        cudaGraph_t bb;
+        MF_G(mf_add_while(x.graph, &n_bw, &n_succ, &hb, &bb));
+        cudaGraphNode_t k1, k2;
+        void* a_back[] = {&b.gt, &b.st};
+        void* a_chk[] = {&b.st, &n, &flags, &in_graph, &hb};
+        MF_G(mf_add_kernel(bb, &k1, nullptr, (const void*)k_mf_back, rg, MF_NT, a_back));
+        MF_G(mf_add_kernel(bb, &k2, &k1, (const void*)k_mf_back_check, 1, 1, a_chk));
+        void* a_bc[] = {&b.st, &n, &b.src, &b.bc};
+        MF_G(mf_add_kernel(x.graph, &n_bc, &n_bw, (const void*)k_mf_bc, grid_for(h, n, 32), MF_NT, a_bc));
+        x.nodes = 11;
+    }
+    MF_G(cudaGraphInstantiate(&x.exec, x.graph, 0));
+    x.S = b.st.S;
+    return cudaSuccess;
+}
+
+#undef MF_G
+
+// Run one batch with the handle's driver (graphs are rebuilt when S changes).
+stc_status mf_run(stc_handle* h, const MfBatch& b, MfGraphExec& x, stc_stream s) {
+    if (h->round_driver == 0) return mf_run_host(h, b, s);
+    if (x.S != b.st.S) {
+        const cudaError_t e = mf_build_graph(h, b, x);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            x.reset();
+            return STC_ERR_CUDA;
+        }
+    }
+    STC_CUDA_TRY(cudaGraphLaunch(x.exec, s));
+    stc_count(h, x.nodes);  // each node once (the device repeats the loop bodies)
     return STC_OK;
 }
 
@@ -407,20 +610,36 @@ stc_status mf_check(stc_handle* h, const MfGraph& g, stc_stream s) {
     return STC_OK;
 }
 
-stc_status mf_alloc_state(StcScratch& sc, int64_t n, int S, MfState& st, int64_t** d_count) {
-    const size_t ns = size_t(n) * size_t(S);
+stc_status mf_alloc_state(StcScratch& sc, const MfGraph& g, int S, MfState& st) {
+    // item and list indices are int
+    if (g.n + g.nnz / MF_ITEM_EDGES + 2 > int64_t(INT32_MAX)) return STC_ERR_INVALID_ARG;
+    const size_t n = size_t(g.n);
+    const size_t ns = n * size_t(S);
+    const size_t ni = n + size_t(g.nnz / MF_ITEM_EDGES) + 1;  // each vertex once per round
     st.S = S;
     st.d = sc.get<int>(ns);
     st.dn = sc.get<int>(ns);
     st.sig = sc.get<double>(ns);
     st.dl = sc.get<double>(ns);
     st.dln = sc.get<double>(ns);
-    st.stamp = sc.get<int>(size_t(n));
-    st.list[0] = sc.get<int32_t>(size_t(n));
-    st.list[1] = sc.get<int32_t>(size_t(n));
-    st.cnt = sc.get<int>(8);
-    *d_count = sc.get<int64_t>(size_t(n));
+    st.stamp = sc.get<int>(n);
+    st.list[0] = sc.get<int32_t>(n);
+    st.list[1] = sc.get<int32_t>(n);
+    st.items[0] = sc.get<int2>(ni);
+    st.items[1] = sc.get<int2>(ni);
+    st.cnt = sc.get<int>(MF_C_NUM);
     return sc.failed ? STC_ERR_OOM : STC_OK;
+}
+
+stc_status mf_read_flags(stc_handle* h, stc_stream s) {
+    STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[6], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    const int f = reinterpret_cast<int*>(&h->h_stage[6])[0];
+    if (f) {
+        STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+        return stc_flags_to_status(f);
+    }
+    return STC_OK;
 }
 
 }  // namespace
@@ -432,24 +651,20 @@ stc_status stc_mfbc_sssp_impl(stc_handle* h, const stc_csr* G, const int32_t* so
     stc_status st = stc_validate_csr_async(h, G, s);
     if (st != STC_OK) return st;
     if ((st = mf_check(h, g, s)) != STC_OK) return st;
-    MfState ms;
-    int64_t* d_count = nullptr;
-    if ((st = mf_alloc_state(sc, g.n, nsrc, ms, &d_count)) != STC_OK) return st;
+    MfBatch b{g, MfGraph{0, 0, nullptr, nullptr, nullptr}, MfState{}, nullptr, nullptr};
+    if ((st = mf_alloc_state(sc, g, nsrc, b.st)) != STC_OK) return st;
     int32_t* d_src = sc.get<int32_t>(size_t(nsrc));
     if (!d_src) return STC_ERR_OOM;
+    b.src = d_src;
     STC_CUDA_TRY(cudaMemcpyAsync(d_src, sources, sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, s));
-    if ((st = mf_forward(h, sc, g, ms, d_src, d_count, s, rounds_out)) != STC_OK) return st;
-    STC_CUDA_TRY(cudaMemcpyAsync(d_out, ms.d, sizeof(int) * size_t(g.n) * nsrc, cudaMemcpyDeviceToDevice, s));
-    STC_CUDA_TRY(cudaMemcpyAsync(sigma_out, ms.sig, sizeof(double) * size_t(g.n) * nsrc,
+    MfGraphExec x(s);
+    if ((st = mf_run(h, b, x, s)) != STC_OK) return st;
+    STC_CUDA_TRY(cudaMemcpyAsync(d_out, b.st.d, sizeof(int) * size_t(g.n) * nsrc, cudaMemcpyDeviceToDevice, s));
+    STC_CUDA_TRY(cudaMemcpyAsync(sigma_out, b.st.sig, sizeof(double) * size_t(g.n) * nsrc,
                                  cudaMemcpyDeviceToDevice, s));
-    int f = 0;
-    STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[6], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-    STC_CUDA_TRY(cudaStreamSynchronize(s));
-    f = reinterpret_cast<int*>(&h->h_stage[6])[0];
-    if (f) {
-        STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
-        return stc_flags_to_status(f);
-    }
+    STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[5], &b.st.cnt[MF_C_FROUND], sizeof(int), cudaMemcpyDeviceToHost, s));
+    if ((st = mf_read_flags(h, s)) != STC_OK) return st;  // synchronises
+    if (rounds_out) *rounds_out = reinterpret_cast<int*>(&h->h_stage[5])[0] + 1;
     return STC_OK;
 }
 
@@ -475,47 +690,20 @@ stc_status stc_mfbc_impl(stc_handle* h, const stc_csr* G, const int32_t* sources
     k_tr_fill<<<grid_for(h, g.n * 32 / 256 + 1, 16), 256, 0, s>>>(g, tptr, cursor, tcol, tw);
     STC_LAUNCH_CHECK();
     stc_count(h);
-    MfGraph gt{g.n, g.nnz, tptr, tcol, tw};
 
-    MfState ms;
-    int64_t* d_count = nullptr;
-    if ((st = mf_alloc_state(sc, g.n, batch, ms, &d_count)) != STC_OK) return st;
+    MfBatch b{g, MfGraph{g.n, g.nnz, tptr, tcol, tw}, MfState{}, nullptr, bc};
+    if ((st = mf_alloc_state(sc, g, batch, b.st)) != STC_OK) return st;
     int32_t* d_src = sc.get<int32_t>(size_t(batch));
     if (!d_src) return STC_ERR_OOM;
+    b.src = d_src;
     k_mf_zero<<<grid_for(h, g.n / 256 + 1, 16), 256, 0, s>>>(bc, g.n);
     STC_LAUNCH_CHECK();
     stc_count(h);
-    int* h_cnt = reinterpret_cast<int*>(&h->h_stage[5]);
+    MfGraphExec x(s);
     for (int32_t b0 = 0; b0 < nsrc; b0 += batch) {
-        const int S = nsrc - b0 < batch ? nsrc - b0 : batch;
-        ms.S = S;
-        STC_CUDA_TRY(cudaMemcpyAsync(d_src, sources + b0, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
-        if ((st = mf_forward(h, sc, g, ms, d_src, d_count, s, nullptr)) != STC_OK) return st;
-        // backward: successor counts, then ready rounds (lists reuse the frontier lists)
-        STC_CUDA_TRY(cudaMemsetAsync(ms.cnt, 0, 4 * sizeof(int), s));
-        k_mf_succ<<<grid_for(h, g.n, 32), MF_NT, 0, s>>>(g, ms, ms.list[0], &ms.cnt[0]);
-        STC_LAUNCH_CHECK();
-        stc_count(h);
-        for (int r = 0, cur = 0;; ++r, cur ^= 1) {
-            STC_CUDA_TRY(cudaMemcpyAsync(h_cnt, &ms.cnt[cur], sizeof(int), cudaMemcpyDeviceToHost, s));
-            STC_CUDA_TRY(cudaStreamSynchronize(s));
-            if (*h_cnt == 0) break;
-            STC_CUDA_TRY(cudaMemsetAsync(&ms.cnt[cur ^ 1], 0, sizeof(int), s));
-            k_mf_back<<<grid_for(h, *h_cnt, 16), MF_NT, 0, s>>>(gt, ms, ms.list[cur], &ms.cnt[cur],
-                                                                ms.list[cur ^ 1], &ms.cnt[cur ^ 1], r + (1 << 30));
-            STC_LAUNCH_CHECK();
-            stc_count(h);
-        }
-        k_mf_bc<<<grid_for(h, g.n, 32), MF_NT, 0, s>>>(ms, g.n, d_src, bc);
-        STC_LAUNCH_CHECK();
-        stc_count(h);
+        b.st.S = nsrc - b0 < batch ? nsrc - b0 : batch;
+        STC_CUDA_TRY(cudaMemcpyAsync(d_src, sources + b0, sizeof(int32_t) * b.st.S, cudaMemcpyHostToDevice, s));
+        if ((st = mf_run(h, b, x, s)) != STC_OK) return st;
     }
-    STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[6], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-    STC_CUDA_TRY(cudaStreamSynchronize(s));
-    const int f = reinterpret_cast<int*>(&h->h_stage[6])[0];
-    if (f) {
-        STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
-        return stc_flags_to_status(f);
-    }
-    return STC_OK;
+    return mf_read_flags(h, s);
 }

@@ -448,6 +448,12 @@ extern "C" stc_status stc_mfbc_sssp(stc_handle* h, const stc_csr* G, const int32
     return stc_mfbc_sssp_impl(h, G, sources, nsources, d_out, sigma_out, rounds_out, stream);
 }
 
+extern "C" stc_status stc_set_round_driver(stc_handle* h, int32_t driver) {
+    if (!h || driver < 0 || driver > 1) return STC_ERR_INVALID_ARG;
+    h->round_driver = driver;
+    return STC_OK;
+}
+
 extern "C" stc_status stc_mfbc(stc_handle* h, const stc_csr* G, const int32_t* sources, int32_t nsources,
                                int32_t batch, double* bc_out, stc_stream stream) {
     stc_status st = mfbc_args(h, G, sources, nsources);

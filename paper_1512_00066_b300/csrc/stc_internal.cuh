@@ -24,6 +24,7 @@ struct stc_handle {
     cudaEvent_t ev[9] = {};        // phase boundary events (created on first use)
     int nphases = 0;               // phases recorded by the last timed call
     int64_t launches = 0;          // kernels launched by this handle
+    int round_driver = 1;          // multi-round loops: 0 host-driven, 1 CUDA graph
 };
 
 // Record phase boundary `idx` (0 = start of the call) when timing is enabled.

@@ -118,3 +118,31 @@ def test_rmat22_full_size_forward_sampled(H):
         sj = sig[:, j].cpu().numpy()
         assert np.array_equal(dj, np.where(rd < 0, INF, rd))
         assert np.array_equal(sj, rs)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_round_drivers_agree(H, weighted):
+    """Host-driven rounds and the one-graph-per-batch driver give identical
+    results; the graph driver counts each of its nodes once per batch."""
+    G = graph(12, 11, weighted)
+    src = W.sample_sources(G, 70, seed=12)
+    dG = to_dev(G)
+    out = {}
+    try:
+        for drv in ("host", "graph"):
+            H.set_round_driver(drv)
+            k0 = H.kernel_launches()
+            d, sig, rounds = H.mfbc_sssp(dG, src[:40])
+            k1 = H.kernel_launches()
+            bc = H.mfbc(dG, src, batch=32).cpu().numpy()  # 3 batches, the last one partial
+            k2 = H.kernel_launches()
+            out[drv] = (d.cpu().numpy(), sig.cpu().numpy(), rounds, bc, k1 - k0, k2 - k1)
+    finally:
+        H.set_round_driver("graph")
+    h, g = out["host"], out["graph"]
+    assert np.array_equal(h[0], g[0]) and np.array_equal(h[1], g[1]) and h[2] == g[2]
+    bc_close(g[3], O.brandes(G, src, weighted))
+    bc_close(h[3], g[3])
+    # host: 5 kernels per forward round; graph: 7 nodes for the forward call
+    assert h[4] >= 2 + 5 * h[2] and g[4] < h[4]
+    assert g[5] < h[5]

@@ -148,3 +148,21 @@ def test_bellman_ford_closed_forms_and_cycles(H):
     # the handle stays usable
     d, _ = H.bellman_ford(O.MP_I32, to_dev(L), 0)
     assert np.array_equal(d.cpu().numpy(), 7 * np.arange(n))
+
+
+def test_bellman_ford_drivers_are_distinct(H):
+    """Each driver runs its own launch pattern: the host loop launches one kernel
+    per round, the cooperative form one kernel in all, and the graph form counts
+    the two kernels of its WHILE body once (the device repeats them)."""
+    n = 1000
+    L = W.csr_from_coo(np.arange(n - 1), np.arange(1, n), n, n)
+    L.val = np.full(n - 1, 7, np.int32)
+    G = to_dev(L)
+    launches = {}
+    for persistent in (True, False, "graph"):
+        k0 = H.kernel_launches()
+        d, r = H.bellman_ford(O.MP_I32, G, 0, persistent=persistent)
+        launches[persistent] = H.kernel_launches() - k0
+        assert np.array_equal(d.cpu().numpy(), 7 * np.arange(n)) and r == n - 1
+    assert launches["graph"] == launches[True] + 1
+    assert launches[False] >= launches[True] + n - 2
