@@ -26,6 +26,8 @@ namespace {
 
 constexpr int SP_NT = 512;   // threads per CTA of the symbolic and numeric kernels
 constexpr int NBINS = 48;    // bin 0: ub == 0; bin b >= 1: 2^(b-1) <= ub < 2^b
+constexpr int BIN_COPY = NBINS;       // rows with a single stored A entry (rank path)
+constexpr int NBINS_ALL = NBINS + 1;
 constexpr int SYM_MAX_COLS = 1 << 19;  // symbolic bitmap width (64 KB)
 
 struct SpgArgs {
@@ -89,6 +91,8 @@ template <> struct Tr<ALG_PT_F32> {
         atomicAdd(&acc[c], __fmul_rn(a, b));
     }
     static __device__ __forceinline__ C out(Acc v) { return v; }
+    // the output of an entry with exactly one product (added to an empty accumulator)
+    static __device__ __forceinline__ C one(A a, B b) { return __fadd_rn(0.0f, __fmul_rn(a, b)); }
 };
 template <> struct Tr<ALG_PT_F64> {
     using A = double; using B = double; using C = double; using Acc = double;
@@ -97,6 +101,7 @@ template <> struct Tr<ALG_PT_F64> {
         atomicAdd(&acc[c], a * b);
     }
     static __device__ __forceinline__ C out(Acc v) { return v; }
+    static __device__ __forceinline__ C one(A a, B b) { return __dadd_rn(0.0, __dmul_rn(a, b)); }
 };
 template <> struct Tr<ALG_MP_I32> {
     using A = int; using B = int; using C = int; using Acc = int;
@@ -107,6 +112,7 @@ template <> struct Tr<ALG_MP_I32> {
         atomicMin(&acc[c], a + b);
     }
     static __device__ __forceinline__ C out(Acc v) { return v; }
+    static __device__ __forceinline__ C one(A a, B b) { return a + b; }
 };
 template <> struct Tr<ALG_MP_F32> {
     using A = float; using B = float; using C = float; using Acc = unsigned;
@@ -115,6 +121,7 @@ template <> struct Tr<ALG_MP_F32> {
         atomicMin(&acc[c], f32_to_ordered(__fadd_rn(a, b)));
     }
     static __device__ __forceinline__ C out(Acc v) { return ordered_to_f32(v); }
+    static __device__ __forceinline__ C one(A a, B b) { return ordered_to_f32(f32_to_ordered(__fadd_rn(a, b))); }
 };
 template <> struct Tr<ALG_BOOL> {
     using A = uint8_t; using B = uint8_t; using C = uint8_t; using Acc = unsigned;
@@ -123,10 +130,18 @@ template <> struct Tr<ALG_BOOL> {
         if (a != 0 && b != 0 && acc[c] == 0u) atomicOr(&acc[c], 1u);
     }
     static __device__ __forceinline__ C out(Acc v) { return uint8_t(v != 0u); }
+    static __device__ __forceinline__ C one(A a, B b) { return uint8_t(a != 0 && b != 0); }
 };
 template <> struct Tr<ALG_MULTPATH> {
     using A = int; using B = DSig; using C = DSig; using Acc = int;  // distance part
     static __device__ __forceinline__ Acc empty() { return INT_MAX; }
+    static __device__ __forceinline__ C one(A a, B b) {
+        DSig o;
+        o.d = a + b.d;
+        o.pad = 0;
+        o.s = 0.0 + b.s;
+        return o;
+    }
 };
 
 // ----------------------------------------------------------------- row analysis + binning
@@ -164,7 +179,9 @@ __global__ void k_row_ub(SpgArgs g, int64_t* __restrict__ ub, int* __restrict__ 
         if (s_bins[t]) atomicAdd(&bin_count[t], s_bins[t]);
 }
 
-// Exclusive offsets of the bins, heaviest bin first; empty rows (bin 0) are not listed.
+// Exclusive offsets of the bins, heaviest bin first; empty rows (bin 0) are not
+// listed.  *nlist counts the rows of bins 1..NBINS-1; the rows of BIN_COPY (when
+// used) follow them.
 __global__ void k_bin_offsets(const int* __restrict__ bin_count, int* __restrict__ cursor,
                               int* __restrict__ nlist) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -173,28 +190,31 @@ __global__ void k_bin_offsets(const int* __restrict__ bin_count, int* __restrict
             cursor[b] = off;
             off += bin_count[b];
         }
-        cursor[0] = off;
         *nlist = off;
+        cursor[BIN_COPY] = off;
+        cursor[0] = off + bin_count[BIN_COPY];
     }
 }
 
 // Scatter of row ids into their bins (order inside a bin is arbitrary: rows are
 // independent).  Block-aggregated: one global atomic per bin per block.
+// single (may be null): non-zero for the rows of BIN_COPY.
 __global__ void __launch_bounds__(512) k_bin_scatter(int64_t nA, const int64_t* __restrict__ ub,
+                                                     const int64_t* __restrict__ single,
                                                      int* __restrict__ cursor,
                                                      int32_t* __restrict__ rowlist) {
-    __shared__ int s_cnt[NBINS];
-    __shared__ int s_base[NBINS];
-    for (int t = threadIdx.x; t < NBINS; t += blockDim.x) s_cnt[t] = 0;
+    __shared__ int s_cnt[NBINS_ALL];
+    __shared__ int s_base[NBINS_ALL];
+    for (int t = threadIdx.x; t < NBINS_ALL; t += blockDim.x) s_cnt[t] = 0;
     __syncthreads();
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     int bin = 0, local = 0;
     if (i < nA) {
-        bin = bin_of(ub[i]);
+        bin = (single && single[i] > 0) ? BIN_COPY : bin_of(ub[i]);
         if (bin > 0) local = atomicAdd(&s_cnt[bin], 1);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < NBINS; t += blockDim.x)
+    for (int t = threadIdx.x; t < NBINS_ALL; t += blockDim.x)
         s_base[t] = (t > 0 && s_cnt[t]) ? atomicAdd(&cursor[t], s_cnt[t]) : 0;
     __syncthreads();
     if (i < nA && bin > 0) rowlist[s_base[bin] + local] = int32_t(i);
@@ -274,6 +294,18 @@ __device__ __forceinline__ int find_seg(const int* pre, int f) {
     for (int step = NT / 2; step > 0; step >>= 1)
         if (pre[j + step] <= f) j += step;
     return j;
+}
+
+// find_seg for a warp-uniform f, by two ballot rounds: over coarse[g] = pre[32 g]
+// to pick the group of 32 entries, then over that group (every lane of the warp
+// calls it with the same f; NT a multiple of 32, <= 1024).
+template <int NT>
+__device__ __forceinline__ int find_seg_warp(const int* pre, const int* coarse, int f, int lane) {
+    constexpr int G = NT / 32;
+    const unsigned m1 = __ballot_sync(0xffffffffu, lane < G && coarse[lane] <= f);
+    const int grp = 31 - __clz(m1);  // m1 != 0: pre[0] == 0 <= f
+    const unsigned m2 = __ballot_sync(0xffffffffu, pre[grp * 32 + lane] <= f);
+    return grp * 32 + 31 - __clz(m2);
 }
 
 // Persistent-CTA row loop: returns the next listed row or -1.
@@ -506,14 +538,16 @@ constexpr int RK_NT = 1024;     // numeric kernel: one CTA per SM, large value b
 constexpr int RK_SYM_NT = 256;  // symbolic kernel: more rows in flight per SM
 constexpr size_t RK_SMEM_TARGET = 224 * 1024;  // one CTA per SM
 constexpr double RK_RECORD_BUDGET = 24e9;        // bytes of stored rank records
+constexpr int RK_SPARSE_MAX_WORDS = 4096;         // sparse record: at most this many non-zero words
 
 template <int NT>
 struct TaskSmem {
-    int pre[NT];      // exclusive prefix of the warp-task counts of the chunk's segments
-    int len[NT];      // segment length
-    int64_t lo[NT];   // first B position of the segment
+    int pre[NT];         // exclusive prefix of the warp-task counts of the chunk's segments
+    int coarse[NT / 32]; // pre[32 g], contiguous (read by 32 lanes without bank conflicts)
+    int len[NT];         // segment length
+    int64_t lo[NT];      // first B position of the segment
     int warp[NT / 32 + 1];
-    int next;         // next unclaimed warp task (warps claim tasks dynamically)
+    int next;            // next unclaimed warp task (warps claim tasks dynamically)
 };
 
 // Segments of the chunk [p0, p0+NT) of A_i: whole B rows, or (ctab != null) the
@@ -547,6 +581,7 @@ __device__ __forceinline__ int load_tasks(const SpgArgs& g, const int32_t* __res
     int total;
     int ex = block_exclusive_scan<NT, int>((len + RK_SUB - 1) / RK_SUB, ts.warp, total);
     ts.pre[threadIdx.x] = ex;
+    if ((threadIdx.x & 31) == 0) ts.coarse[threadIdx.x >> 5] = ex;
     ts.len[threadIdx.x] = len;
     ts.lo[threadIdx.x] = lo;
     if (WITH_VAL) s_aval[threadIdx.x] = av;
@@ -562,7 +597,7 @@ __device__ __forceinline__ void walk_tasks(const SpgArgs& g, TaskSmem<NT>& ts, i
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int U = RK_SUB / 32;
     for (int t = wid; t < ntasks;) {
-        const int j = find_seg<NT>(ts.pre, t);
+        const int j = find_seg_warp<NT>(ts.pre, ts.coarse, t, lane);
         const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
         const int64_t end = ts.lo[j] + ts.len[j];
         // warp-uniform number of 32-entry steps of this task (short B rows stop early)
@@ -589,15 +624,57 @@ __device__ __forceinline__ void walk_tasks(const SpgArgs& g, TaskSmem<NT>& ts, i
     }
 }
 
-// As walk_tasks, also loading the B values of the task up front:
-// op(p, col, val, j).
-template <int NT, class AT, class BT, class Op>
-__device__ __forceinline__ void walk_tasks_val(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
-                                               const AT* s_aval, const BT* __restrict__ bval, Op op) {
+// Symbolic walk: set the bitmap bit of every product's column.  All the task's
+// bitmap reads are issued before its atomics (a read after an atomic would wait
+// for it), and the summary bits are derived from the bitmap afterwards.
+template <int NT>
+__device__ __forceinline__ void walk_tasks_bits(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
+                                                uint32_t* bits) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int U = RK_SUB / 32;
     for (int t = wid; t < ntasks;) {
-        const int j = find_seg<NT>(ts.pre, t);
+        const int j = find_seg_warp<NT>(ts.pre, ts.coarse, t, lane);
+        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
+        const int64_t end = ts.lo[j] + ts.len[j];
+        const int64_t span = end - start;
+        const int nu = span >= RK_SUB ? U : int((span + 31) >> 5);
+        int col[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            col[u] = -1;
+            if (u < nu) {
+                const int64_t p = start + lane + 32 * u;
+                if (p < end) col[u] = g.b_col[p];
+            }
+        }
+        int nt = 0;
+        if (lane == 0) nt = atomicAdd(&ts.next, 1);
+        uint32_t cur[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            cur[u] = (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) ? bits[col[u] >> 5] : ~0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) {
+                const uint32_t m = 1u << (col[u] & 31);
+                if (!(cur[u] & m)) atomicOr(&bits[col[u] >> 5], m);
+            }
+        }
+        t = __shfl_sync(0xffffffffu, nt, 0);
+    }
+}
+
+// Numeric walk: load the task's columns and B values up front, then for every
+// valid column map it to its rank in the current window with rank_of and apply
+// upd(r, col, b, a) when the rank is in [0, rcount).
+template <int NT, class AT, class BT, class RankF, class UpdF>
+__device__ __forceinline__ void walk_tasks_rank(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
+                                                const AT* s_aval, const BT* __restrict__ bval, int rcount,
+                                                RankF rank_of, UpdF upd) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int U = RK_SUB / 32;
+    for (int t = wid; t < ntasks;) {
+        const int j = find_seg_warp<NT>(ts.pre, ts.coarse, t, lane);
         const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
         const int64_t end = ts.lo[j] + ts.len[j];
         const int64_t span = end - start;
@@ -607,35 +684,25 @@ __device__ __forceinline__ void walk_tasks_val(const SpgArgs& g, TaskSmem<NT>& t
         BT val[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            col[u] = -1;
             if (u < nu) {
                 const int64_t p = start + lane + 32 * u;
                 if (p < end) {
                     col[u] = g.b_col[p];
                     val[u] = bval[p];
-                } else {
-                    col[u] = -1;
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (u < nu) {
-                const int64_t p = start + lane + 32 * u;
-                if (p < end) op(col[u], val[u], a);
+            if (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) {
+                const int r = rank_of(col[u]);
+                if ((unsigned)r < (unsigned)rcount) upd(r, col[u], val[u], a);
             }
         }
         int nt = 0;
         if (lane == 0) nt = atomicAdd(&ts.next, 1);
         t = __shfl_sync(0xffffffffu, nt, 0);
-    }
-}
-
-__device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t* summ, int col) {
-    const int w = col >> 5;
-    const uint32_t m = 1u << (col & 31);
-    if (!(bits[w] & m)) {
-        uint32_t old = atomicOr(&bits[w], m);
-        if (old == 0u) atomicOr(&summ[w >> 5], 1u << (w & 31));
     }
 }
 
@@ -692,14 +759,34 @@ __host__ __device__ inline SymLayout sym_layout(int ncell) {
     return L;
 }
 
-// Persistent-CTA row loop over a row list of global rows: thread 0 resolves the
-// row's matrix into shared memory.  Returns the global row or -1.
-__device__ __forceinline__ int64_t next_row_b(int* counter, int nlist, const int32_t* rowlist, const SpgRows& R,
-                                              SpgArgs* s_args, int64_t* s_row) {
+// Persistent-CTA row loop over a row list of global rows.  Thread 0 claims rows
+// two ahead: it holds one claimed row whose list entry is already loaded and one
+// whose entry is being loaded, so moving to the next row waits on neither the
+// claim nor the list read.  Thread 0 resolves the row's matrix into shared memory.
+struct RowClaim {
+    int r1;        // claimed list position, entry loaded into g1
+    int64_t g1;
+    int r2;        // claimed list position, entry not loaded yet
+};
+
+__device__ __forceinline__ void claim_init(RowClaim& c, int* counter, int nlist, const int32_t* rowlist) {
+    if (threadIdx.x == 0) {
+        c.r1 = atomicAdd(counter, 1);
+        c.g1 = c.r1 < nlist ? rowlist[c.r1] : -1;
+        c.r2 = atomicAdd(counter, 1);
+    }
+}
+
+// Returns the global row or -1; s_row = {global row, row in its matrix, list position}.
+__device__ __forceinline__ int64_t next_row_b(RowClaim& c, int* counter, int nlist, const int32_t* rowlist,
+                                              const SpgRows& R, SpgArgs* s_args, int64_t* s_row) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const int r = atomicAdd(counter, 1);
-        const int64_t gi = r < nlist ? rowlist[r] : -1;
+        const int r = c.r1;
+        const int64_t gi = c.g1;
+        c.r1 = c.r2;
+        c.g1 = c.r2 < nlist ? rowlist[c.r2] : -1;
+        c.r2 = atomicAdd(counter, 1);
         int64_t li = gi;
         if (gi >= 0) {
             if (R.table) {
@@ -722,7 +809,7 @@ template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                 int* __restrict__ counter, int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz,
-                uint4* __restrict__ rec) {
+                uint4* __restrict__ rec, int2* __restrict__ rec_meta, int sparse_max) {
     extern __shared__ uint4 smem_raw[];
     const SymLayout L = sym_layout(ncell_max);
     const RankLayout LR = rank_layout(ncell_max, 0, 0, 4, false);  // record layout
@@ -740,9 +827,11 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
     for (int w = threadIdx.x; w < NWmax; w += NT) bits[w] = 0u;
     for (int c = threadIdx.x; c < ncell_max; c += NT) summ[c] = 0u;
     const int nlist = *nlist_ptr;
+    RowClaim rc;
+    claim_init(rc, counter, nlist, rowlist);
     int local_max = 0;
     for (;;) {
-        const int64_t gi = next_row_b(counter, nlist, rowlist, R, &s_args, s_row);
+        const int64_t gi = next_row_b(rc, counter, nlist, rowlist, R, &s_args, s_row);
         if (gi < 0) break;
         const SpgArgs& g = s_args;
         const int64_t i = s_row[1];
@@ -751,13 +840,20 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
         row_range(g.a_ptr, i, g.nnzA, alo, ahi);
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
             const int ntasks = load_tasks<NT, int, false>(g, nullptr, 0, p0, ahi, 0, 0, ts, nullptr);
-            walk_tasks<NT>(g, ts, ntasks, [&](int64_t, int col, int) {
-                if ((uint64_t)col < (uint64_t)g.ncols) set_bit(bits, summ, col);
-            });
+            walk_tasks_bits<NT>(g, ts, ntasks, bits);
             __syncthreads();
         }
         int tot;
         if (rec) {
+            // summary bits: one ballot per 32 words
+            {
+                const int lane = threadIdx.x & 31;
+                for (int c = threadIdx.x >> 5; c < g.ncell; c += NT / 32) {
+                    const unsigned m = __ballot_sync(0xffffffffu, bits[c * 32 + lane] != 0u);
+                    if (lane == 0) summ[c] = m;
+                }
+                __syncthreads();
+            }
             // ranks: word prefix inside each cell and the cells' exclusive prefix;
             // the whole rank structure is stored for the numeric pass
             constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;
@@ -788,21 +884,54 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
             }
             if (threadIdx.x == 0) cellbase[g.ncell] = tot;
             __syncthreads();
-            // the record, in the numeric kernel's layout: (bits, rank of the word) pairs,
-            // the summary and the cell prefix
             unsigned char* dst = reinterpret_cast<unsigned char*>(rec) + s_row[2] * rec_bytes;
-            uint4* dwb = reinterpret_cast<uint4*>(dst + LR.wb);
-            for (int q = threadIdx.x; q < NWmax / 2; q += NT) {
-                const int w = 2 * q;
-                const uint32_t b0 = bits[w], b1 = bits[w + 1];
-                const int c = w >> 5;  // w and w + 1 share a cell
-                dwb[q] = make_uint4(b0, b0 ? uint32_t(cellbase[c] + wpre[w]) : 0u, b1,
-                                    b1 ? uint32_t(cellbase[c] + wpre[w + 1]) : 0u);
+            // light rows (one rank window in the numeric pass, few non-zero words): only
+            // the non-zero words, as (bits, word << 18 | rank of the word's first column)
+            bool sparse = false;
+            if (tot <= sparse_max) {
+                int nz = 0;
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) {
+                    const int c = threadIdx.x * CPT + q;
+                    if (c < g.ncell) nz += __popc(summ[c]);
+                }
+                int nzt;
+                int zex = block_exclusive_scan<NT, int>(nz, s_red, nzt);
+                if (nzt <= RK_SPARSE_MAX_WORDS) {
+                    sparse = true;
+                    uint2* dsp = reinterpret_cast<uint2*>(dst);
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) {
+                        const int c = threadIdx.x * CPT + q;
+                        if (c < g.ncell) {
+                            uint32_t sw = summ[c];
+                            while (sw) {
+                                const int w = c * 32 + __ffs(sw) - 1;
+                                sw &= sw - 1;
+                                dsp[zex++] = make_uint2(bits[w], (uint32_t(w) << 18) | uint32_t(cellbase[c] + wpre[w]));
+                            }
+                        }
+                    }
+                    if (threadIdx.x == 0) rec_meta[s_row[2]] = make_int2(nzt, tot);
+                }
             }
-            uint32_t* dsumm = reinterpret_cast<uint32_t*>(dst + LR.summ);
-            for (int c = threadIdx.x; c < ncell_max; c += NT) dsumm[c] = summ[c];
-            int* dcb = reinterpret_cast<int*>(dst + LR.cellbase);
-            for (int c = threadIdx.x; c <= ncell_max; c += NT) dcb[c] = c <= g.ncell ? cellbase[c] : tot;
+            if (!sparse) {
+                // the dense record, in the numeric kernel's layout: (bits, rank of the
+                // word) pairs, the summary and the cell prefix
+                uint4* dwb = reinterpret_cast<uint4*>(dst + LR.wb);
+                for (int q = threadIdx.x; q < NWmax / 2; q += NT) {
+                    const int w = 2 * q;
+                    const uint32_t b0 = bits[w], b1 = bits[w + 1];
+                    const int c = w >> 5;  // w and w + 1 share a cell
+                    dwb[q] = make_uint4(b0, b0 ? uint32_t(cellbase[c] + wpre[w]) : 0u, b1,
+                                        b1 ? uint32_t(cellbase[c] + wpre[w + 1]) : 0u);
+                }
+                uint32_t* dsumm = reinterpret_cast<uint32_t*>(dst + LR.summ);
+                for (int c = threadIdx.x; c < ncell_max; c += NT) dsumm[c] = summ[c];
+                int* dcb = reinterpret_cast<int*>(dst + LR.cellbase);
+                for (int c = threadIdx.x; c <= ncell_max; c += NT) dcb[c] = c <= g.ncell ? cellbase[c] : tot;
+                if (threadIdx.x == 0) rec_meta[s_row[2]] = make_int2(-1, tot);
+            }
             __syncthreads();
             for (int c = threadIdx.x; c < g.ncell; c += NT) {
                 uint32_t sw = summ[c];
@@ -857,10 +986,13 @@ __global__ void k_cell_offsets(SpgRows R) {
     }
 }
 
-// Row analysis over global rows (batch-aware): ub and log2 bins.
-__global__ void k_row_ub_b(SpgRows R, int64_t NR, int64_t* __restrict__ ub, int* __restrict__ bin_count) {
-    __shared__ int s_bins[NBINS];
-    for (int t = threadIdx.x; t < NBINS; t += blockDim.x) s_bins[t] = 0;
+// Row analysis over global rows (batch-aware): ub and log2 bins.  With single !=
+// null, a row with one stored entry whose B row is not empty goes to BIN_COPY and
+// its output count is final: single[gi] = ub (one product per output column).
+__global__ void k_row_ub_b(SpgRows R, int64_t NR, int64_t* __restrict__ ub, int* __restrict__ bin_count,
+                           int64_t* __restrict__ single) {
+    __shared__ int s_bins[NBINS_ALL];
+    for (int t = threadIdx.x; t < NBINS_ALL; t += blockDim.x) s_bins[t] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -890,12 +1022,55 @@ __global__ void k_row_ub_b(SpgRows R, int64_t NR, int64_t* __restrict__ ub, int*
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
         if (lane == 0) {
             ub[gi] = sum;
-            atomicAdd(&s_bins[bin_of(sum)], 1);
+            const bool one = single && hi - lo == 1 && sum > 0;
+            if (one) single[gi] = sum;
+            atomicAdd(&s_bins[one ? BIN_COPY : bin_of(sum)], 1);
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < NBINS; t += blockDim.x)
+    for (int t = threadIdx.x; t < NBINS_ALL; t += blockDim.x)
         if (s_bins[t]) atomicAdd(&bin_count[t], s_bins[t]);
+}
+
+// Rows with a single stored entry a = A_ik: C_i = f(a, B_k) entry by entry, in B_k's
+// column order (each output column has exactly one product, so no (+) applies).
+// Warp per row over rowlist[*nlist, *nlist + *ncopy).
+template <int ALG>
+__global__ void __launch_bounds__(256) k_copy_rows(SpgRows R, const int32_t* __restrict__ rowlist,
+                                                   const int* __restrict__ nlist_ptr,
+                                                   const int* __restrict__ ncopy_ptr,
+                                                   const int64_t* __restrict__ c_ptr, int32_t* __restrict__ c_col,
+                                                   void* __restrict__ c_val) {
+    using T = Tr<ALG>;
+    using AT = typename T::A;
+    using BT = typename T::B;
+    auto* cval = static_cast<typename T::C*>(c_val);
+    const int lane = threadIdx.x & 31;
+    const int first = *nlist_ptr, n = *ncopy_ptr;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < n; q += nwarps) {
+        const int64_t gi = rowlist[first + q];
+        SpgArgs g;
+        int64_t i = gi;
+        if (R.table) {
+            const int b = batch_of(R, gi);
+            g = R.table[b];
+            i = gi - R.row_off[b];
+        } else {
+            g = R.one;
+        }
+        const int64_t p = g.a_ptr[i];
+        const int32_t k = g.a_col[p];
+        const AT a = static_cast<const AT*>(g.a_val)[p];
+        int64_t bl, bh;
+        row_range(g.b_ptr, k, g.nnzB, bl, bh);
+        const int64_t o0 = c_ptr[gi] - bl;
+        const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
+        for (int64_t e = bl + lane; e < bh; e += 32) {
+            c_col[o0 + e] = g.b_col[e];
+            cval[o0 + e] = T::one(a, bval[e]);
+        }
+    }
 }
 
 // Per-batch row pointers: rp[row_off[b] + b + i] = c_ptr[row_off[b] + i] - c_ptr[row_off[b]].
@@ -924,7 +1099,8 @@ __global__ void __launch_bounds__(NT, MINB)
 k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                int* __restrict__ counter, RankOut out, int32_t* __restrict__ c_col,
-               void* __restrict__ c_val, int* __restrict__ flags, const uint4* __restrict__ rec) {
+               void* __restrict__ c_val, int* __restrict__ flags, const uint4* __restrict__ rec,
+               const int2* __restrict__ rec_meta) {
     using T = Tr<ALG>;
     using AT = typename T::A;
     using BT = typename T::B;
@@ -954,11 +1130,13 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         if constexpr (ALG == ALG_MULTPATH) sig[r] = 0.0;
     }
     const int nlist = *nlist_ptr;
+    RowClaim rc;
+    claim_init(rc, counter, nlist, rowlist);
     const int vstep = vcap - RK_CELL;  // rank span that starts a new window
     auto* cval = static_cast<typename T::C*>(c_val);
 
     for (;;) {
-        const int64_t gi = next_row_b(counter, nlist, rowlist, R, &s_args, s_row);
+        const int64_t gi = next_row_b(rc, counter, nlist, rowlist, R, &s_args, s_row);
         if (gi < 0) break;
         const SpgArgs& g = s_args;
         const int64_t i = s_row[1];
@@ -970,14 +1148,31 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         const int64_t o1 = out.cap ? o0 + out.cap[gi] : out.ptr[gi + 1];
 
         int total;
+        bool sparse = false;  // one rank window, no cell prefixes
         if (rec) {
             // the symbolic pass stored this row's bitmap, word prefixes and cell prefixes
+            // (dense), or only its non-zero words with their ranks (sparse)
             const int rec16 = int(L.winfirst / 16);
             const uint4* src = rec + s_row[2] * int64_t(rec16);
-            for (int q = threadIdx.x; q < rec16; q += NT) smem_raw[q] = src[q];
-            __syncthreads();
-            total = cellbase[ncell];
-            __syncthreads();
+            const int2 meta = rec_meta[s_row[2]];
+            if (meta.x >= 0) {
+                sparse = true;
+                const uint2* sp = reinterpret_cast<const uint2*>(src);
+                for (int q = threadIdx.x; q < meta.x; q += NT) {
+                    const uint2 e = sp[q];
+                    const int w = int(e.y >> 18);
+                    wb[w] = make_uint2(e.x, e.y & 0x3ffffu);
+                    atomicOr(&summ[w >> 5], 1u << (w & 31));
+                }
+                if (threadIdx.x == 0) cellbase[0] = 0;
+                total = meta.y;
+                __syncthreads();
+            } else {
+                for (int q = threadIdx.x; q < rec16; q += NT) smem_raw[q] = src[q];
+                __syncthreads();
+                total = cellbase[ncell];
+                __syncthreads();
+            }
         } else {
         // 1) bitmap of the row's columns
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
@@ -1036,12 +1231,15 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         }
         __syncthreads();
         const bool fits = total <= int(o1 - o0);
-        for (int c = threadIdx.x; c < ncell; c += NT) {
-            const int wc = cellbase[c] / vstep;
-            if (c == 0 || (cellbase[c - 1] / vstep) != wc) winfirst[wc] = c;
+        if (!sparse) {
+            for (int c = threadIdx.x; c < ncell; c += NT) {
+                const int wc = cellbase[c] / vstep;
+                if (c == 0 || (cellbase[c - 1] / vstep) != wc) winfirst[wc] = c;
+            }
         }
         if (threadIdx.x == 0) {
-            const int nw = (total > 0 && fits) ? cellbase[ncell - 1] / vstep + 1 : 0;
+            const int nw = (total > 0 && fits) ? (sparse ? 1 : cellbase[ncell - 1] / vstep + 1) : 0;
+            if (sparse) winfirst[0] = 0;
             winfirst[nw] = ncell;
             s_nwin = nw;
         }
@@ -1060,25 +1258,21 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             };
             for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
                 const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
-                walk_tasks_val<NT, AT, BT>(g, ts, ntasks, s_aval, bval, [&](int col, const BT& b, const AT a) {
-                    if ((uint64_t)col >= (uint64_t)g.ncols) return;
-                    const int r = rank_of(col);
-                    if ((unsigned)r >= (unsigned)rcount) return;
-                    scol[r] = col;
-                    if constexpr (ALG == ALG_MULTPATH) atomicMin(&vals[r], a + b.d);
-                    else T::combine(vals, r, a, b);
-                });
+                walk_tasks_rank<NT, AT, BT>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
+                                            [&](int r, int col, const BT& b, const AT a) {
+                                                scol[r] = col;
+                                                if constexpr (ALG == ALG_MULTPATH) atomicMin(&vals[r], a + b.d);
+                                                else T::combine(vals, r, a, b);
+                                            });
                 __syncthreads();
             }
             if constexpr (ALG == ALG_MULTPATH) {
                 for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
                     const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
-                    walk_tasks_val<NT, AT, BT>(g, ts, ntasks, s_aval, bval, [&](int col, const BT& b, const AT a) {
-                        if ((uint64_t)col >= (uint64_t)g.ncols) return;
-                        const int r = rank_of(col);
-                        if ((unsigned)r >= (unsigned)rcount) return;
-                        if (a + b.d == vals[r]) atomicAdd(&sig[r], b.s);
-                    });
+                    walk_tasks_rank<NT, AT, BT>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
+                                                [&](int r, int, const BT& b, const AT a) {
+                                                    if (a + b.d == vals[r]) atomicAdd(&sig[r], b.s);
+                                                });
                     __syncthreads();
                 }
             }
@@ -1176,7 +1370,7 @@ struct RankCfg {
 template <int ALG, int NT, int MINB>
 stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
                                const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
-                               int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, stc_stream s) {
+                               int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, const int2* rec_meta, stc_stream s) {
     auto kern = k_numeric_rank<ALG, NT, MINB>;
     STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)));
     int per_sm = 0;
@@ -1185,7 +1379,7 @@ stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, c
     int64_t grid = int64_t(per_sm) * h->num_sms;
     if (grid > NR) grid = NR > 0 ? NR : 1;
     kern<<<unsigned(grid), NT, cfg.smem, s>>>(R, ncell_max, cfg.vcap, cfg.maxwin, rowlist, nlist, counter, out,
-                                              c_col, c_val, h->d_flags, rec);
+                                              c_col, c_val, h->d_flags, rec, rec_meta);
     STC_LAUNCH_CHECK();
     stc_count(h);
     return STC_OK;
@@ -1194,26 +1388,44 @@ stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, c
 template <int ALG>
 stc_status run_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
                             const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
-                            int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, stc_stream s) {
+                            int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, const int2* rec_meta, stc_stream s) {
     if (cfg.small)
         return launch_numeric_rank<ALG, 256, 4>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
-                                                NR, rec, s);
+                                                NR, rec, rec_meta, s);
     return launch_numeric_rank<ALG, RK_NT, 1>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
-                                              NR, rec, s);
+                                              NR, rec, rec_meta, s);
 }
 
 stc_status run_numeric_any(stc_handle* h, int alg, const SpgRows& R, int ncell_max, const RankCfg& cfg,
                            const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
-                           int32_t* c_col, void* c_val, int64_t NR, stc_stream s, const uint4* rec = nullptr) {
+                           int32_t* c_col, void* c_val, int64_t NR, stc_stream s, const uint4* rec = nullptr,
+                           const int2* rec_meta = nullptr) {
     switch (alg) {
-    case ALG_PT_F32: return run_numeric_rank<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
-    case ALG_PT_F64: return run_numeric_rank<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
-    case ALG_MP_I32: return run_numeric_rank<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
-    case ALG_MP_F32: return run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
-    case ALG_BOOL: return run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
-    case ALG_MULTPATH: return run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, s);
+    case ALG_PT_F32: return run_numeric_rank<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
+    case ALG_PT_F64: return run_numeric_rank<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
+    case ALG_MP_I32: return run_numeric_rank<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
+    case ALG_MP_F32: return run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
+    case ALG_BOOL: return run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
+    case ALG_MULTPATH: return run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
     default: return STC_ERR_ALGEBRA;
     }
+}
+
+stc_status run_copy_any(stc_handle* h, int alg, const SpgRows& R, const int32_t* rowlist, const int* nlist,
+                        const int* ncopy, const int64_t* c_ptr, int32_t* c_col, void* c_val, stc_stream s) {
+    const unsigned grid = unsigned(h->num_sms * 8);
+    switch (alg) {
+    case ALG_PT_F32: k_copy_rows<ALG_PT_F32><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
+    case ALG_PT_F64: k_copy_rows<ALG_PT_F64><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
+    case ALG_MP_I32: k_copy_rows<ALG_MP_I32><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
+    case ALG_MP_F32: k_copy_rows<ALG_MP_F32><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
+    case ALG_BOOL: k_copy_rows<ALG_BOOL><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
+    case ALG_MULTPATH: k_copy_rows<ALG_MULTPATH><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
+    default: return STC_ERR_ALGEBRA;
+    }
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return STC_OK;
 }
 
 RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max) {
@@ -1294,21 +1506,21 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     }
     int64_t* ub = sc.get<int64_t>(size_t(NR));
     int32_t* rowlist = sc.get<int32_t>(size_t(NR));
-    int* ints = sc.get<int>(2 * NBINS + 8);
+    int* ints = sc.get<int>(2 * NBINS_ALL + 8);
     int64_t* bounds_d = sc.get<int64_t>(size_t(nb) + 1);
     if (sc.failed) return fail(STC_ERR_OOM);
-    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS + 8), s) != cudaSuccess) return fail(STC_ERR_CUDA);
+    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS_ALL + 8), s) != cudaSuccess) return fail(STC_ERR_CUDA);
     int* bin_count = ints;
-    int* cursor = ints + NBINS;
-    int* nlist = ints + 2 * NBINS;
-    int* counters = ints + 2 * NBINS + 1;  // [0] symbolic, [1] numeric
-    int* max_nnz = ints + 2 * NBINS + 4;
+    int* cursor = ints + NBINS_ALL;
+    int* nlist = ints + 2 * NBINS_ALL;
+    int* counters = ints + 2 * NBINS_ALL + 1;  // [0] symbolic, [1] numeric
+    int* max_nnz = ints + 2 * NBINS_ALL + 4;
     if (NR > 0) {
         int64_t blocks = (NR * 32 + 255) / 256;
         if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count);
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, c_ptr + 1);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
-        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, cursor, rowlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, c_ptr + 1, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h, 3);
     }
@@ -1317,9 +1529,11 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     // fit the budget; otherwise the numeric pass rebuilds them
     const size_t rec_bytes = rank_layout(ncell_max, 0, 0, 4, false).winfirst;
     uint4* rec = nullptr;
+    int2* rec_meta = nullptr;  // per record: (number of words of a sparse record or -1, row count)
     if (NR > 0 && double(NR) * double(rec_bytes) <= RK_RECORD_BUDGET) {
         rec = sc.get<uint4>(size_t(NR) * (rec_bytes / 16));
-        if (!rec) return fail(STC_ERR_OOM);
+        rec_meta = sc.get<int2>(size_t(NR));
+        if (!rec || !rec_meta) return fail(STC_ERR_OOM);
     }
     if (NR > 0) {
         const size_t smem = sym_layout(ncell_max).total;
@@ -1330,7 +1544,8 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         if (per_sm < 1) return fail(STC_ERR_CUDA);
         int64_t grid = int64_t(per_sm) * h->num_sms;
         if (grid > NR) grid = NR;
-        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell_max, rowlist, nlist, counters, c_ptr + 1, max_nnz, rec);
+        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell_max, rowlist, nlist, counters, c_ptr + 1, max_nnz, rec,
+                                                     rec_meta, cfg.vcap - RK_CELL);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h);
     }
@@ -1404,7 +1619,9 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         RankOut out{};
         out.ptr = c_ptr;
         if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, nlist, counters + 1, out, c_col, c_val, NR,
-                                  s, rec)) != STC_OK)
+                                  s, rec, rec_meta)) != STC_OK)
+            return fail(st);
+        if ((st = run_copy_any(h, alg, R, rowlist, nlist, bin_count + BIN_COPY, c_ptr, c_col, c_val, s)) != STC_OK)
             return fail(st);
     }
     stc_mark(h, s, 5);
@@ -1545,27 +1762,27 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
     int32_t* ovf = sc.get<int32_t>(size_t(NR));
     int64_t* cap = sc.get<int64_t>(size_t(NR));
     int64_t* soff = sc.get<int64_t>(size_t(NR) + 1);
-    int* ints = sc.get<int>(2 * NBINS + 16);
+    int* ints = sc.get<int>(2 * NBINS_ALL + 16);
     double* err = sc.get<double>(1);
     float* pred = weights ? sc.get<float>(size_t(NR)) : nullptr;
     float* feat = weights ? sc.get<float>(size_t(NR) * STC_MLP_FEAT_STRIDE) : nullptr;
     if (sc.failed) return fail(STC_ERR_OOM);
     int* bin_count = ints;
-    int* cursor = ints + NBINS;
-    int* nlist = ints + 2 * NBINS;
-    int* counters = ints + 2 * NBINS + 1;  // [0] learned pass, [1] overflow pass
-    int* maxcap = ints + 2 * NBINS + 4;
-    int* novf = ints + 2 * NBINS + 5;
-    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS + 16), s) != cudaSuccess ||
+    int* cursor = ints + NBINS_ALL;
+    int* nlist = ints + 2 * NBINS_ALL;
+    int* counters = ints + 2 * NBINS_ALL + 1;  // [0] learned pass, [1] overflow pass
+    int* maxcap = ints + 2 * NBINS_ALL + 4;
+    int* novf = ints + 2 * NBINS_ALL + 5;
+    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS_ALL + 16), s) != cudaSuccess ||
         cudaMemsetAsync(err, 0, sizeof(double), s) != cudaSuccess ||
         cudaMemsetAsync(soff, 0, sizeof(int64_t), s) != cudaSuccess)
         return fail(STC_ERR_CUDA);
     if (NR > 0) {
         int64_t blocks = (NR * 32 + 255) / 256;
         if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count);
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, nullptr);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
-        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, cursor, rowlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, nullptr, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h, 3);
         if (weights) {
@@ -1758,13 +1975,13 @@ static stc_status spgemm_window_impl(stc_handle* h, int alg, const stc_csr* A, c
         const int R = int(Ws / W);
         int64_t* ub = sc.get<int64_t>(size_t(nA));
         rowlist = sc.get<int32_t>(size_t(nA));
-        ints = sc.get<int>(2 * NBINS + 8);
+        ints = sc.get<int>(2 * NBINS_ALL + 8);
         if (sc.failed) return fail(STC_ERR_OOM);
-        if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS + 8), s) != cudaSuccess) return fail(STC_ERR_CUDA);
+        if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS_ALL + 8), s) != cudaSuccess) return fail(STC_ERR_CUDA);
         int* bin_count = ints;
-        int* cursor = ints + NBINS;
-        int* nlist = ints + 2 * NBINS;
-        int* counters = ints + 2 * NBINS + 1;
+        int* cursor = ints + NBINS_ALL;
+        int* nlist = ints + 2 * NBINS_ALL;
+        int* counters = ints + 2 * NBINS_ALL + 1;
         if (g.nwin > 1) {
             int32_t* woff = sc.get<int32_t>(size_t(g.K) * size_t(g.nwin + 1));
             if (!woff) return fail(STC_ERR_OOM);
@@ -1780,7 +1997,7 @@ static stc_status spgemm_window_impl(stc_handle* h, int alg, const stc_csr* A, c
         if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
         k_row_ub<<<unsigned(blocks), 256, 0, s>>>(g, ub, bin_count);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
-        k_bin_scatter<<<unsigned((nA + 511) / 512), 512, 0, s>>>(nA, ub, cursor, rowlist);
+        k_bin_scatter<<<unsigned((nA + 511) / 512), 512, 0, s>>>(nA, ub, nullptr, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h, 3);
         stc_mark(h, s, 2);
@@ -1818,8 +2035,8 @@ static stc_status spgemm_window_impl(stc_handle* h, int alg, const stc_csr* A, c
     if (!c_col || !c_val) return fail(STC_ERR_OOM);
     stc_mark(h, s, 4);
     if (!trivial && nnz > 0) {
-        int* nlist = ints + 2 * NBINS;
-        int* counter = ints + 2 * NBINS + 2;
+        int* nlist = ints + 2 * NBINS_ALL;
+        int* counter = ints + 2 * NBINS_ALL + 2;
         switch (alg) {
         case ALG_PT_F32: st = run_numeric<ALG_PT_F32>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
         case ALG_PT_F64: st = run_numeric<ALG_PT_F64>(h, g, rowlist, nlist, counter, c_ptr, c_col, c_val, nA, s); break;
