@@ -43,6 +43,7 @@ struct SpgArgs {
     int nwin;                          // number of numeric windows
     const int32_t* __restrict__ ctab;  // rank path: [K][ncell+1] per-cell offsets in B rows, or null
     int ncell;                         // rank path: 1024-column cells of the output
+    int col_base;                      // added to every written column (column slabs of a wide B)
 };
 
 // Rows of one matrix (table == null: `one`) or of a batch of independent
@@ -1067,7 +1068,7 @@ __global__ void __launch_bounds__(256) k_copy_rows(SpgRows R, const int32_t* __r
         const int64_t o0 = c_ptr[gi] - bl;
         const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
         for (int64_t e = bl + lane; e < bh; e += 32) {
-            c_col[o0 + e] = g.b_col[e];
+            c_col[o0 + e] = g.b_col[e] + g.col_base;
             cval[o0 + e] = T::one(a, bval[e]);
         }
     }
@@ -1278,7 +1279,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             }
             for (int r = threadIdx.x; r < rcount; r += NT) {
                 if (fits) {
-                    c_col[o0 + rb + r] = scol[r];
+                    c_col[o0 + rb + r] = scol[r] + g.col_base;
                     if constexpr (ALG == ALG_MULTPATH) {
                         DSig o;
                         o.d = vals[r];
@@ -1721,6 +1722,340 @@ SpgArgs make_args(const stc_csr* A, const stc_csr* B) {
 }
 
 
+// ----------------------------------------------------------------- column slabs
+//
+// Outputs wider than RK_MAX_COLS: B is split once into slabs of RK_MAX_COLS
+// columns (B_s = the entries of B with column in [s W, (s+1) W), columns shifted
+// to start at 0), every slab runs the rank path's analysis and symbolic pass, one
+// scan over the per-(row, slab) counts gives C's row pointers and every row's
+// offset per slab, and every slab's numeric pass writes its part of each row in
+// place (C_i is the concatenation of the slabs' parts, columns ascending).
+
+constexpr int SLAB_MAX = 32;  // at most 32 slabs (8,388,608 columns) on this path
+
+struct SlabBases {
+    int64_t base[SLAB_MAX];   // first entry of slab s in the slab arrays
+};
+
+// Per B row k: bnd[k*(S+1) + t] = number of entries of B_k with column < t W.
+// Warp per row; lane t-1 binary-searches boundary t.
+__global__ void k_slab_bounds(const int64_t* __restrict__ b_ptr, const int32_t* __restrict__ b_col, int64_t K,
+                              int64_t nnzB, int S, int32_t* __restrict__ bnd, int64_t* __restrict__ bsptr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < K; k += nw) {
+        int64_t lo, hi;
+        row_range(b_ptr, k, nnzB, lo, hi);
+        int32_t* bk = bnd + k * (S + 1);
+        for (int t = lane; t <= S; t += 32) {
+            int64_t pos;
+            if (t == 0) {
+                pos = lo;
+            } else if (t == S) {
+                pos = hi;
+            } else {
+                const int64_t target = int64_t(t) * RK_MAX_COLS;
+                int64_t a = lo, b = hi;
+                while (a < b) {
+                    const int64_t m = (a + b) >> 1;
+                    if (int64_t(b_col[m]) < target) a = m + 1; else b = m;
+                }
+                pos = a;
+            }
+            bk[t] = int32_t(pos - lo);
+        }
+        __syncwarp();
+        for (int t = lane; t < S; t += 32) bsptr[int64_t(t) * (K + 1) + k + 1] = bk[t + 1] - bk[t];
+    }
+}
+
+// Copy every B row's slab parts into the slab arrays (columns shifted to the slab).
+template <class VT>
+__global__ void k_slab_scatter(const int64_t* __restrict__ b_ptr, const int32_t* __restrict__ b_col,
+                               const VT* __restrict__ b_val, int64_t K, int64_t nnzB, int S,
+                               const int32_t* __restrict__ bnd, const int64_t* __restrict__ bsptr, SlabBases sb,
+                               int32_t* __restrict__ s_col, VT* __restrict__ s_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < K; k += nw) {
+        int64_t lo, hi;
+        row_range(b_ptr, k, nnzB, lo, hi);
+        const int32_t* bk = bnd + k * (S + 1);
+        for (int t = 0; t < S; ++t) {
+            const int64_t src = lo + bk[t], n = bk[t + 1] - bk[t];
+            const int64_t dst = sb.base[t] + bsptr[int64_t(t) * (K + 1) + k];
+            const int32_t shift = int32_t(int64_t(t) * RK_MAX_COLS);
+            for (int64_t e = lane; e < n; e += 32) {
+                s_col[dst + e] = b_col[src + e] - shift;
+                s_val[dst + e] = b_val[src + e];
+            }
+        }
+    }
+}
+
+// c_ptr[i + 1] = sum over slabs of cnt[s NR + i].
+__global__ void k_slab_total(int64_t NR, int S, const int64_t* __restrict__ cnt, int64_t* __restrict__ c_ptr) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NR; i += int64_t(gridDim.x) * blockDim.x) {
+        int64_t t = 0;
+        for (int q = 0; q < S; ++q) t += cnt[int64_t(q) * NR + i];
+        c_ptr[i + 1] = t;
+    }
+}
+
+// off[s NR + i] = c_ptr[i] + sum over slabs q < s of cnt[q NR + i].
+__global__ void k_slab_offsets(int64_t NR, int S, const int64_t* __restrict__ cnt, const int64_t* __restrict__ c_ptr,
+                               int64_t* __restrict__ off) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NR; i += int64_t(gridDim.x) * blockDim.x) {
+        int64_t o = c_ptr[i];
+        for (int q = 0; q < S; ++q) {
+            off[int64_t(q) * NR + i] = o;
+            o += cnt[int64_t(q) * NR + i];
+        }
+    }
+}
+
+stc_status spgemm_slab_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C, bool validate,
+                            stc_stream s) {
+    const int64_t NR = A->nrows, K = A->ncols;
+    const int S = int((B->ncols + RK_MAX_COLS - 1) / RK_MAX_COLS);
+    if (S < 2 || S > SLAB_MAX) return STC_ERR_INVALID_ARG;
+    const size_t vbC = stc_val_bytes(alg, 'C'), vbB = stc_val_bytes(alg, 'B');
+    int64_t* c_ptr = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(NR + 1) * 8, s));
+    if (!c_ptr) return STC_ERR_OOM;
+    int32_t* c_col = nullptr;
+    void* c_val = nullptr;
+    auto fail = [&](stc_status st) {
+        (void)cudaGetLastError();
+        stc_free_bytes(h, c_ptr, s);
+        if (c_col) stc_free_bytes(h, c_col, s);
+        if (c_val) stc_free_bytes(h, c_val, s);
+        return st;
+    };
+    StcScratch sc(h, s);
+    stc_mark(h, s, 0);
+    if (cudaMemsetAsync(c_ptr, 0, size_t(NR + 1) * 8, s) != cudaSuccess) return fail(STC_ERR_CUDA);
+    stc_status st;
+    if (validate) {
+        if ((st = stc_validate_csr_async(h, A, s)) != STC_OK) return fail(st);
+        if ((st = stc_validate_csr_async(h, B, s)) != STC_OK) return fail(st);
+    }
+    stc_mark(h, s, 1);
+
+    // 1) slabs of B
+    int32_t* bnd = sc.get<int32_t>(size_t(K) * size_t(S + 1));
+    int64_t* bsptr = sc.get<int64_t>(size_t(S) * size_t(K + 1));
+    int32_t* s_col = sc.get<int32_t>(size_t(B->nnz) + 1);
+    unsigned char* s_val = sc.get<unsigned char>((size_t(B->nnz) + 1) * vbB);
+    int64_t* cnt = sc.get<int64_t>(size_t(S) * size_t(NR));
+    int64_t* off = sc.get<int64_t>(size_t(S) * size_t(NR));
+    int64_t* ub = sc.get<int64_t>(size_t(NR));
+    int64_t* nnz_scratch = sc.get<int64_t>(size_t(NR));
+    int32_t* ovf = sc.get<int32_t>(size_t(NR));
+    int32_t* rowlists = sc.get<int32_t>(size_t(S) * size_t(NR));
+    const int NI = 2 * NBINS_ALL + 8;
+    int* ints = sc.get<int>(size_t(S) * NI + 8);
+    if (sc.failed) return fail(STC_ERR_OOM);
+    if (cudaMemsetAsync(bsptr, 0, sizeof(int64_t) * size_t(S) * size_t(K + 1), s) != cudaSuccess ||
+        cudaMemsetAsync(cnt, 0, sizeof(int64_t) * size_t(S) * size_t(NR), s) != cudaSuccess ||
+        cudaMemsetAsync(ints, 0, sizeof(int) * (size_t(S) * NI + 8), s) != cudaSuccess)
+        return fail(STC_ERR_CUDA);
+    int* novf = ints + size_t(S) * NI;
+    const unsigned gw = unsigned(h->num_sms * 16);
+    if (K > 0) {
+        k_slab_bounds<<<gw, 256, 0, s>>>(B->rowptr, B->col, K, B->nnz, S, bnd, bsptr);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+        for (int t = 0; t < S; ++t)
+            if ((st = stc_inclusive_scan_i64(h, sc, bsptr + size_t(t) * (K + 1) + 1, K, s)) != STC_OK) return fail(st);
+    }
+    // slab sizes (and the validation flags so far)
+    SlabBases sb{};
+    {
+        int64_t* stage = h->h_stage;
+        for (int t = 0; t < S; ++t) stage[t] = 0;
+        for (int t = 0; t < S && K > 0; ++t)
+            if (cudaMemcpyAsync(&stage[t], bsptr + size_t(t) * (K + 1) + K, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                s) != cudaSuccess)
+                return fail(STC_ERR_CUDA);
+        int* f = reinterpret_cast<int*>(&stage[SLAB_MAX]);
+        *f = 0;
+        if (cudaMemcpyAsync(f, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(STC_ERR_CUDA);
+        if (*f) {
+            const int flags = *f;
+            (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
+            return fail(stc_flags_to_status(flags));
+        }
+        int64_t b = 0;
+        for (int t = 0; t < S; ++t) {
+            sb.base[t] = b;
+            b += stage[t];
+        }
+        if (b != B->nnz) return fail(STC_ERR_CUDA);
+    }
+    if (K > 0 && B->nnz > 0) {
+        switch (vbB) {
+        case 1: k_slab_scatter<uint8_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint8_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint8_t*>(s_val)); break;
+        case 4: k_slab_scatter<uint32_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint32_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint32_t*>(s_val)); break;
+        case 8: k_slab_scatter<uint64_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint64_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint64_t*>(s_val)); break;
+        default: k_slab_scatter<uint4><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint4*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint4*>(s_val)); break;
+        }
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+    }
+    std::vector<SpgArgs> args(S);
+    std::vector<RankCfg> cfgs(S);
+    std::vector<int> ncells(S);
+    size_t rec_total = 0;
+    for (int t = 0; t < S; ++t) {
+        SpgArgs g = make_args(A, B);
+        const int64_t w = B->ncols - int64_t(t) * RK_MAX_COLS;
+        g.ncols = w < RK_MAX_COLS ? w : RK_MAX_COLS;
+        g.ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
+        g.b_ptr = bsptr + size_t(t) * (K + 1);
+        g.b_col = s_col + sb.base[t];
+        g.b_val = s_val + size_t(sb.base[t]) * vbB;
+        g.nnzB = (t + 1 < S ? sb.base[t + 1] : B->nnz) - sb.base[t];
+        g.col_base = int(int64_t(t) * RK_MAX_COLS);
+        args[t] = g;
+        ncells[t] = g.ncell > 0 ? g.ncell : 1;
+        cfgs[t] = rank_config(alg, g.ncols, ncells[t]);
+        if (!cfgs[t].vcap) return fail(STC_ERR_INVALID_ARG);
+        rec_total += size_t(NR) * rank_layout(ncells[t], 0, 0, 4, false).winfirst;
+    }
+    stc_mark(h, s, 2);
+
+    // 2) per slab: analysis, binning, symbolic counts (and stored rank records when
+    //    all slabs' records fit the budget together)
+    const bool use_rec = NR > 0 && double(rec_total) <= RK_RECORD_BUDGET;
+    std::vector<uint4*> recs(S, nullptr);
+    std::vector<int2*> metas(S, nullptr);
+    for (int t = 0; t < S && NR > 0; ++t) {
+        SpgRows R{};
+        R.one = args[t];
+        R.nb = 1;
+        int* ti = ints + size_t(t) * NI;
+        int* bin_count = ti;
+        int* cursor = ti + NBINS_ALL;
+        int* nlist = ti + 2 * NBINS_ALL;
+        int* counters = ti + 2 * NBINS_ALL + 1;
+        int* max_nnz = ti + 2 * NBINS_ALL + 4;
+        int32_t* rowlist = rowlists + size_t(t) * NR;
+        int64_t* cnt_t = cnt + size_t(t) * NR;
+        int64_t blocks = (NR * 32 + 255) / 256;
+        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, cnt_t);
+        k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, cnt_t, cursor, rowlist);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h, 3);
+        if (use_rec) {
+            const size_t rb = rank_layout(ncells[t], 0, 0, 4, false).winfirst;
+            recs[t] = sc.get<uint4>(size_t(NR) * (rb / 16));
+            metas[t] = sc.get<int2>(size_t(NR));
+            if (!recs[t] || !metas[t]) return fail(STC_ERR_OOM);
+        }
+        const size_t smem = sym_layout(ncells[t]).total;
+        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem) != cudaSuccess || per_sm < 1)
+            return fail(STC_ERR_CUDA);
+        int64_t grid = int64_t(per_sm) * h->num_sms;
+        if (grid > NR) grid = NR;
+        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncells[t], rowlist, nlist, counters, cnt_t, max_nnz, recs[t],
+                                                     metas[t], cfgs[t].vcap - RK_CELL);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+    }
+    stc_mark(h, s, 3);
+
+    // 3) row pointers and per-slab row offsets
+    if (NR > 0) {
+        const unsigned gb = unsigned(h->num_sms * 8);
+        k_slab_total<<<gb, 256, 0, s>>>(NR, S, cnt, c_ptr);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        if ((st = stc_inclusive_scan_i64(h, sc, c_ptr + 1, NR, s)) != STC_OK) return fail(st);
+        k_slab_offsets<<<gb, 256, 0, s>>>(NR, S, cnt, c_ptr, off);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h, 2);
+    }
+    int64_t nnz = 0;
+    std::vector<int> max_row(S, 0);
+    {
+        int* mx = reinterpret_cast<int*>(&h->h_stage[SLAB_MAX + 2]);  // S ints
+        int* f = reinterpret_cast<int*>(&h->h_stage[SLAB_MAX]);
+        *f = 0;
+        h->h_stage[SLAB_MAX + 1] = 0;
+        for (int t = 0; t < S; ++t) mx[t] = 0;
+        for (int t = 0; t < S && NR > 0; ++t)
+            if (cudaMemcpyAsync(&mx[t], ints + size_t(t) * NI + 2 * NBINS_ALL + 4, sizeof(int), cudaMemcpyDeviceToHost,
+                                s) != cudaSuccess)
+                return fail(STC_ERR_CUDA);
+        if (cudaMemcpyAsync(&h->h_stage[SLAB_MAX + 1], c_ptr + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(f, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(STC_ERR_CUDA);
+        if (*f) {
+            const int flags = *f;
+            (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
+            return fail(stc_flags_to_status(flags));
+        }
+        nnz = h->h_stage[SLAB_MAX + 1];
+        for (int t = 0; t < S; ++t) max_row[t] = mx[t];
+    }
+    if (nnz < 0) return fail(STC_ERR_CUDA);
+    c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
+    c_val = stc_alloc_bytes(h, size_t(nnz) * vbC, s);
+    if ((!c_col || !c_val) && nnz > 0) return fail(STC_ERR_OOM);
+    stc_mark(h, s, 4);
+
+    // 4) per slab: numeric pass into C at the slab's row offsets
+    for (int t = 0; t < S && nnz > 0; ++t) {
+        StcScratch sct(h, s);  // the slab's cell-offset table, released after its pass
+        SpgRows R{};
+        R.one = args[t];
+        R.nb = 1;
+        if (max_row[t] >= cfgs[t].vcap - RK_CELL) {
+            int32_t* ctab = sct.get<int32_t>(size_t(K) * size_t(ncells[t] + 1));
+            if (!ctab) return fail(STC_ERR_OOM);
+            R.one.ctab = ctab;
+            int64_t bx = (K * (ncells[t] + 1) + 255) / 256;
+            if (bx > int64_t(h->num_sms) * 64) bx = int64_t(h->num_sms) * 64;
+            if (bx < 1) bx = 1;
+            k_cell_offsets<<<dim3(unsigned(bx), 1), 256, 0, s>>>(R);
+            if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+            stc_count(h);
+        }
+        int* ti = ints + size_t(t) * NI;
+        int64_t* cnt_t = cnt + size_t(t) * NR;
+        int64_t* off_t = off + size_t(t) * NR;
+        int32_t* rowlist = rowlists + size_t(t) * NR;
+        RankOut out{};
+        out.ptr = off_t;
+        out.cap = cnt_t;        // exact sizes: no row overflows
+        out.nnz = nnz_scratch;  // receives the same sizes
+        out.ovf = ovf;
+        out.novf = novf;
+        if ((st = run_numeric_any(h, alg, R, ncells[t], cfgs[t], rowlist, ti + 2 * NBINS_ALL, ti + 2 * NBINS_ALL + 2,
+                                  out, c_col, c_val, NR, s, recs[t], metas[t])) != STC_OK)
+            return fail(st);
+        if ((st = run_copy_any(h, alg, R, rowlist, ti + 2 * NBINS_ALL, ti + BIN_COPY, off_t, c_col, c_val, s)) !=
+            STC_OK)
+            return fail(st);
+    }
+    stc_mark(h, s, 5);
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->rowptr = c_ptr;
+    C->col = c_col;
+    C->val = c_val;
+    C->nnz = nnz;
+    return STC_OK;
+}
+
 // Learned single-pass SpGEMM (one matrix, at most RK_MAX_COLS output columns):
 // row analysis, features and perceptron (or the upper bound) give every row a
 // capacity; one numeric pass writes each row into scratch of that capacity and
@@ -2083,6 +2418,8 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
         C->nnz = nnz;
         return STC_OK;
     }
+    if (!(opts && opts->window_cols) && (B->ncols + RK_MAX_COLS - 1) / RK_MAX_COLS <= SLAB_MAX)
+        return spgemm_slab_impl(h, alg, A, B, C, !(opts && opts->skip_validation), s);
     return spgemm_window_impl(h, alg, A, B, C, opts, s);
 }
 

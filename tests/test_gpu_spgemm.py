@@ -120,6 +120,37 @@ def test_rmat14_plus_times_unit_weights_relative(H):
         assert np.max(np.abs(val.astype(np.float64) - rval) / rval) <= tol
 
 
+@pytest.mark.parametrize("alg", ALL)
+def test_wide_output_column_slabs(H, alg):
+    """More than 2^18 output columns: three full column slabs and a ragged fourth."""
+    A = W.random_csr(700, 1200, 30, seed=41, empty_frac=0.05)
+    B = W.random_csr(1200, 3 * (1 << 18) + 12345, 150, seed=42, empty_frac=0.05)
+    A.val = vals(alg, A.nnz, 43, "A")
+    B.val = vals(alg, B.nnz, 44, "B")
+    check(H, alg, A, B)
+
+
+def test_column_slab_boundaries(H):
+    """Entries on both sides of every slab boundary, single-entry rows of A (copy
+    path) next to multi-entry rows, and rows whose products all fall in one slab."""
+    W_ = 1 << 18
+    ncols = 2 * W_ + 1
+    edges = [0, W_ - 1, W_, 2 * W_ - 1, 2 * W_]
+    rows, cols = [], []
+    for k in range(40):
+        picks = sorted(set([edges[k % 5], edges[(k + 2) % 5], (k * 7919) % ncols, (k * 104729) % ncols]))
+        rows += [k] * len(picks)
+        cols += picks
+    B = W.csr_from_coo(np.array(rows), np.array(cols), 40, ncols)
+    B.val = np.arange(1, B.nnz + 1, dtype=np.int32)
+    arow = [0, 1, 1, 2, 2, 2] + [3 + i // 2 for i in range(30)]
+    acol = [5, 0, 9, 1, 2, 3] + [(7 * i) % 40 for i in range(30)]
+    A = W.csr_from_coo(np.array(arow), np.array(acol), 20, 40)
+    A.val = np.arange(1, A.nnz + 1, dtype=np.int32)
+    check(H, O.MP_I32, A, B)
+    check(H, O.PT_F64, A.with_val(A.val.astype(np.float64)), B.with_val(B.val.astype(np.float64)))
+
+
 def test_edge_cases(H):
     import paper_1512_00066_b300 as stc
     # empty A, empty B, 1x1, rows with ub == 0, single column
@@ -198,3 +229,31 @@ def test_rmat18_full_size_sampled(H, alg):
     np.add.at(ub, np.repeat(np.arange(A.nrows), lens), lens[A.col])
     rows = np.unique(np.r_[np.arange(0, A.nrows, 64), np.argsort(ub)[-256:]])
     check(H, alg, A, A, rows=rows)
+
+
+def test_rmat20_column_slabs_full_size_sampled(H):
+    """R-MAT scale 20 A.A in fp32 (2^20 output columns: four column slabs) at full
+    size: every row count against the oracle's exact counts, and every 256th row
+    plus the 64 heaviest rows element by element."""
+    A = W.rmat(20, seed=0)
+    A.val = W.weights_unit01(A.nnz, seed=0).astype(np.float32)
+    lens = np.diff(A.rowptr)
+    ub = np.zeros(A.nrows, np.int64)
+    np.add.at(ub, np.repeat(np.arange(A.nrows), lens), lens[A.col])
+    rows = np.unique(np.r_[np.arange(0, A.nrows, 256), np.argsort(ub)[-64:]])
+    d = to_dev(A)
+    C = H.spgemm(O.PT_F32, d, d)
+    torch.cuda.synchronize()
+    H.check_device_status()
+    rp = C.rowptr.cpu().numpy()
+    assert np.array_equal(np.diff(rp), O.spgemm_count(A, A)), "row counts differ"
+    # gather the sampled rows on the device (C itself is ~78 GB)
+    sel = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows])
+    idx = torch.from_numpy(sel).to(C.col.device)
+    col = C.col[idx].cpu().numpy()
+    val = C.val[idx].cpu().numpy()
+    del C
+    torch.cuda.empty_cache()
+    ptr, rcol, rval, rabs = O.spgemm(O.PT_F32, A, A, rows=rows, want_abs=True)
+    assert np.array_equal(col, rcol)
+    compare_values(O.PT_F32, val, rval, rabs, where="rmat20 sampled")
