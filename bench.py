@@ -34,10 +34,16 @@ METRIC = "SpGEMM semiring-ops/s & MFBC GTEPS, learned+batched vs plain form on o
 UNIT = "semiring-ops/s"
 L2_BYTES = 126 * 1024 * 1024
 # DRAM bytes (read + write) per output entry of the fp64 numeric rank kernel, from
-# the ncu capture in profiles/k_numeric_rank_fp64_rmat16.md (R-MAT scale 16:
-# 2.002e9 bytes for 163,809,247 entries).  Traffic grows with the output (B stays
-# in L2), so a full launch is scaled by its nnz(C).
-NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = 2.002e9 / 163809247
+# the ncu capture in profiles/k_numeric_rank_fp64_rmat16.md (R-MAT scale 16).
+# Traffic grows with the output (B stays in L2), so a full launch is scaled by its
+# nnz(C).  None until a capture of the current kernel is recorded.
+NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = None
+# FP64 peak of the B300 part: 2 FP64 operations (DADD, DMUL or DFMA) per clock per SM
+# (the nominal 1.25 TFLOP/s counting an FMA as two), 148 SMs, 2032 MHz maximum clock.
+FP64_OPS_PER_CLK_SM = 2
+NUM_SMS = 148
+SM_MAX_MHZ = 2032
+FP64_PEAK_TFLOPS = FP64_OPS_PER_CLK_SM * NUM_SMS * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def peaks():
@@ -66,6 +72,16 @@ def products(A: W.Csr, rows=None) -> int:
     if rows is None:
         return int(lens[A.col].sum())
     return int(sum(lens[A.col[A.rowptr[i]:A.rowptr[i + 1]]].sum() for i in rows))
+
+
+_NPROD = {}
+
+
+def nprod_of(A: W.Csr) -> int:
+    key = id(A)
+    if key not in _NPROD:
+        _NPROD[key] = products(A)
+    return _NPROD[key]
 
 
 def csr_bytes(n, nnz, s):
@@ -274,6 +290,9 @@ def run_stc(args):
     num_ms = statistics.mean(i["numeric_ms"] for i in infos)
     hbm, peak_kind = peaks()
     achieved = compulsory / (num_ms / 1e3) / 1e9
+    # the fp64 numeric phase is bound by the FP64 pipe: one DMUL and one DADD (the
+    # shared-memory atomic add) per product
+    fp64_tflops = 2 * nprod_of(A) / (num_ms / 1e3) / 1e12
     gather_model = csr_bytes(n, nnzA, s) + 8 * nnzA + (4 + s) * products(A) + csr_bytes(n, nnzC, s)
 
     # end to end: host (pinned) inputs -> device -> the same step -> results back to host
@@ -301,13 +320,20 @@ def run_stc(args):
                        "n": A.nrows, "nnz": A.nnz, "nnzC": nnzC, "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "flushed between timed steps (write of 2x L2)",
                        "ops_per_step": ops_total // args.steps},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
-                         "traffic": (NUMERIC_FP64_DRAM_BYTES_PER_ENTRY * nnzC if wl["scale"] else None),
-                         "traffic_note": "ncu capture at R-MAT scale 16 scaled by nnz(C)",
-                         "kernel": "k_numeric_rank (fp64 SpGEMM numeric pass)",
-                         "peak_source": peak_kind, "algorithmic_bytes": compulsory, "kernel_ms": num_ms,
-                         "gather_model_bytes": gather_model},
+            "roofline": ({"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": fp64_tflops / FP64_PEAK_TFLOPS,
+                          "traffic": (NUMERIC_FP64_DRAM_BYTES_PER_ENTRY * nnzC
+                                      if NUMERIC_FP64_DRAM_BYTES_PER_ENTRY else None),
+                          "traffic_note": "ncu capture at R-MAT scale 16 scaled by nnz(C)",
+                          "kernel": "k_numeric_rank + k_copy_rows (fp64 SpGEMM numeric phase)",
+                          "peak_source": "derived: 2 FP64 ops/clk/SM x 148 SMs x 2032 MHz",
+                          "algorithmic_flops": 2 * nprod_of(A), "kernel_ms": num_ms,
+                          "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                  "peak_source": peak_kind, "algorithmic_bytes": compulsory},
+                          "gather_model_bytes": gather_model} if wl["scale"] else
+                         {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                          "frac": achieved / hbm, "traffic": None, "kernel": "k_numeric_rank (int32)",
+                          "peak_source": peak_kind, "algorithmic_bytes": compulsory, "kernel_ms": num_ms}),
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "phases_ms": infos[-1],
@@ -347,44 +373,60 @@ def _timed(fn, reps):
 
 def measure_learned(stc, H, wl, dev):
     """Plain two-pass vs learned single pass (trained model) vs upper-bound single
-    pass on the workload's (+,x) fp32 SpGEMM.  The model is trained on R-MAT
-    scales 14-16 (seeds 1..3), ER and banded matrices, never on the measured graph."""
+    pass on (+,x) fp32 A.A for the workload's graph and for R-MAT scale 20 (2^20
+    output columns: four column slabs).  The model is trained on about 1.1M rows of
+    R-MAT scales 14-18 (seeds 1-5), ER and banded matrices, never on a measured
+    graph (seed 0)."""
     import torch
-    A = wl["A"]
     pairs = []
-    for sc in (14, 15, 16):
-        m = W.rmat(sc, seed=sc - 13)
-        d = stc.DeviceCsr.from_host(m.nrows, m.ncols, m.rowptr, m.col, None)
-        pairs.append((d, d))
-    for m in (W.er_fixed_degree(1 << 16, 8, seed=1), W.banded(1 << 16, 16, 0.5, seed=2)):
+    specs = [W.rmat(14, seed=1), W.rmat(15, seed=2), W.rmat(16, seed=3), W.rmat(17, seed=4), W.rmat(18, seed=5),
+             W.er_fixed_degree(1 << 18, 8, seed=1), W.er_fixed_degree(1 << 17, 16, seed=2),
+             W.banded(1 << 17, 16, 0.5, seed=3), W.banded(1 << 16, 4, 0.5, seed=4)]
+    for m in specs:
         d = stc.DeviceCsr.from_host(m.nrows, m.ncols, m.rowptr, m.col, None)
         pairs.append((d, d))
     t0 = time.perf_counter()
     feat, target = stc.training_rows(H, pairs)
+    n_train = int(target.numel())
     w = stc.mlp_init(seed=1)
-    losses = H.mlp_train(w, feat, target, batch=4096, epochs=30, lr=2e-3, seed=3)
+    losses = H.mlp_train(w, feat, target, batch=8192, epochs=20, lr=2e-3, seed=3)
+    torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del feat, target, pairs
-    d32 = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["w32"])
-    nprod = products(A)
-    t_plain = _timed(lambda: H.spgemm(stc.PLUS_TIMES_F32, d32, d32), 3)
-    stats = {}
-
-    def learned(weights, margin, key):
-        C, st = H.spgemm_learned(stc.PLUS_TIMES_F32, d32, d32, weights, margin)
-        stats[key] = st
-        return C
-
-    t_ml = _timed(lambda: learned(w, 0.5, "model"), 3)
-    t_ub = _timed(lambda: learned(None, 0.0, "upper_bound"), 3)
     torch.cuda.empty_cache()
-    return {"unit": UNIT, "workload": "rmat18 (+,x) fp32 A.A",
-            "plain_two_pass": nprod / t_plain, "learned_single_pass": nprod / t_ml,
-            "upper_bound_single_pass": nprod / t_ub,
-            "ms": {"plain": 1e3 * t_plain, "learned": 1e3 * t_ml, "upper_bound": 1e3 * t_ub},
-            "model_stats": stats.get("model"), "upper_bound_stats": stats.get("upper_bound"),
-            "training": {"seconds": t_train, "final_loss": losses[-1] if losses else None,
-                         "epochs": len(losses)}}
+    out = {"unit": UNIT,
+           "training": {"rows": n_train, "seconds": t_train, "final_loss": losses[-1] if losses else None,
+                        "epochs": len(losses)}}
+    graphs = [("rmat18", wl["A"] if wl["scale"] == 18 else W.rmat(18, seed=0)), ("rmat20", W.rmat(20, seed=0))]
+    for name, A in graphs:
+        d32 = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col,
+                                      W.weights_unit01(A.nnz, seed=0).astype(np.float32))
+        nprod = products(A)
+        res = {"workload": f"{name} (+,x) fp32 A.A", "columns": A.ncols}
+        stats = {}
+
+        def learned(weights, margin, key):
+            C, st = H.spgemm_learned(stc.PLUS_TIMES_F32, d32, d32, weights, margin)
+            stats[key] = st
+            return C
+
+        for key, fn in (("plain", lambda: H.spgemm(stc.PLUS_TIMES_F32, d32, d32)),
+                        ("learned", lambda: learned(w, 0.5, "model")),
+                        ("upper_bound", lambda: learned(None, 0.0, "upper_bound"))):
+            try:
+                t = _timed(fn, 3)
+                res[key + "_ms"] = 1e3 * t
+                res[key] = nprod / t
+            except Exception as e:  # the upper-bound scratch can exceed device memory
+                res[key] = None
+                res[key + "_error"] = str(e)[:120]
+            torch.cuda.empty_cache()
+        res["model_stats"] = stats.get("model")
+        res["upper_bound_stats"] = stats.get("upper_bound")
+        out[name] = res
+        del d32
+        torch.cuda.empty_cache()
+    return out
 
 
 def measure_batched(stc, H):
@@ -419,21 +461,26 @@ def measure_bf_drivers(stc, H, wl):
     return out
 
 
-def measure_mfbc(stc, H, scale=22, nsrc=256):
-    """Betweenness centrality, one batch of 256 sources on R-MAT scale 22: GTEPS =
-    sources * edges / time (forward + backward + reduction)."""
+def measure_mfbc(stc, H, scale=22, nsrc=4096, batch=256):
+    """Betweenness centrality on R-MAT scale 22 over a 4096-source sample (16
+    batches of 256): GTEPS = sources * edges / time (forward + backward +
+    reduction), with unit and int32 [1, 255] lengths; the host-driven round loop is
+    timed on one batch beside the graph driver."""
     import torch
     G = W.rmat(scale, seed=0)
     src = W.sample_sources(G, nsrc, seed=0)
-    out = {"unit": "GTEPS", "workload": f"rmat{scale}, {nsrc} sources (one batch)", "edges": G.nnz}
+    out = {"unit": "GTEPS", "workload": f"rmat{scale}, {nsrc} sources in batches of {batch}", "edges": G.nnz}
     for name, val in (("unit_lengths", None), ("int_lengths_1_255", W.weights_int(G.nnz, 1, 255, seed=1))):
         d = stc.DeviceCsr.from_host(G.nrows, G.ncols, G.rowptr, G.col, val)
+        H.set_round_driver("graph")
+        t = _timed(lambda: H.mfbc(d, src, batch=batch), 1)
+        out[name] = len(src) * G.nnz / t / 1e9
+        out[name + "_ms"] = 1e3 * t
+        one = src[:batch]
         for drv in ("graph", "host"):
             H.set_round_driver(drv)
-            t = _timed(lambda: H.mfbc(d, src, batch=nsrc), 1)
-            key = name if drv == "graph" else name + "_host_driver"
-            out[key] = nsrc * G.nnz / t / 1e9
-            out[key + "_ms"] = 1e3 * t
+            t1 = _timed(lambda: H.mfbc(d, one, batch=batch), 1)
+            out[f"{name}_one_batch_{drv}_ms"] = 1e3 * t1
         H.set_round_driver("graph")
         del d
         torch.cuda.empty_cache()

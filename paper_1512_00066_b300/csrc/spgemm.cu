@@ -1679,18 +1679,21 @@ __global__ void k_capacity(int64_t NR, const int64_t* __restrict__ ub, const flo
 }
 
 // Copy every listed row that fit its capacity from the scratch to C (warp per row).
+// The row's size is cnt[i] when cnt != null (c_ptr then holds destinations only),
+// else c_ptr[i + 1] - c_ptr[i].
 template <class V>
 __global__ void k_compact(const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                           const int64_t* __restrict__ soff, const int64_t* __restrict__ cap,
-                          const int64_t* __restrict__ c_ptr, const int32_t* __restrict__ scol,
-                          const V* __restrict__ sval, int32_t* __restrict__ c_col, V* __restrict__ c_val) {
+                          const int64_t* __restrict__ c_ptr, const int64_t* __restrict__ cnt,
+                          const int32_t* __restrict__ scol, const V* __restrict__ sval, int32_t* __restrict__ c_col,
+                          V* __restrict__ c_val) {
     const int lane = threadIdx.x & 31;
     const int nlist = *nlist_ptr;
     int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t r = warp; r < nlist; r += nwarps) {
         const int32_t i = rowlist[r];
-        const int64_t d0 = c_ptr[i], n = c_ptr[i + 1] - d0;
+        const int64_t d0 = c_ptr[i], n = cnt ? cnt[i] : c_ptr[i + 1] - d0;
         if (n > cap[i]) continue;  // overflow: recomputed exactly
         const int64_t s0 = soff[i];
         for (int64_t e = lane; e < n; e += 32) {
@@ -1698,6 +1701,24 @@ __global__ void k_compact(const int32_t* __restrict__ rowlist, const int* __rest
             c_val[d0 + e] = sval[s0 + e];
         }
     }
+}
+
+stc_status run_compact(stc_handle* h, size_t vbytes, const int32_t* rowlist, const int* nlist, int n_rows,
+                       const int64_t* soff, const int64_t* cap, const int64_t* dst, const int64_t* cnt,
+                       const int32_t* scol, const void* sval, int32_t* c_col, void* c_val, stc_stream s) {
+    int64_t blocks = (int64_t(n_rows) * 32 + 255) / 256;
+    if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+    if (blocks < 1) blocks = 1;
+    const unsigned gb = unsigned(blocks);
+    switch (vbytes) {
+    case 1: k_compact<uint8_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint8_t*>(sval), c_col, static_cast<uint8_t*>(c_val)); break;
+    case 4: k_compact<uint32_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint32_t*>(sval), c_col, static_cast<uint32_t*>(c_val)); break;
+    case 8: k_compact<uint64_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint64_t*>(sval), c_col, static_cast<uint64_t*>(c_val)); break;
+    default: k_compact<uint4><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint4*>(sval), c_col, static_cast<uint4*>(c_val)); break;
+    }
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return STC_OK;
 }
 
 SpgArgs make_args(const stc_csr* A, const stc_csr* B) {
@@ -1814,12 +1835,105 @@ __global__ void k_slab_offsets(int64_t NR, int S, const int64_t* __restrict__ cn
     }
 }
 
+// The slabs of B: per slab the rank path's arguments (B_s, its width and column
+// base), a CSR view of B_s and the launch configuration.  Reads the validation
+// flags raised so far (one synchronisation).
+struct Slabs {
+    int S = 0;
+    std::vector<SpgArgs> args;
+    std::vector<stc_csr> view;
+    std::vector<RankCfg> cfg;
+    std::vector<int> ncell;
+};
+
+stc_status build_slabs(stc_handle* h, StcScratch& sc, int alg, const stc_csr* A, const stc_csr* B, int S,
+                       Slabs& out, stc_stream s) {
+    const int64_t K = A->ncols;
+    const size_t vbB = stc_val_bytes(alg, 'B');
+    int32_t* bnd = sc.get<int32_t>(size_t(K) * size_t(S + 1) + 1);
+    int64_t* bsptr = sc.get<int64_t>(size_t(S) * size_t(K + 1));
+    int32_t* s_col = sc.get<int32_t>(size_t(B->nnz) + 1);
+    unsigned char* s_val = sc.get<unsigned char>((size_t(B->nnz) + 1) * vbB);
+    if (sc.failed) return STC_ERR_OOM;
+    STC_CUDA_TRY(cudaMemsetAsync(bsptr, 0, sizeof(int64_t) * size_t(S) * size_t(K + 1), s));
+    const unsigned gw = unsigned(h->num_sms * 16);
+    stc_status st;
+    if (K > 0) {
+        k_slab_bounds<<<gw, 256, 0, s>>>(B->rowptr, B->col, K, B->nnz, S, bnd, bsptr);
+        STC_LAUNCH_CHECK();
+        stc_count(h);
+        for (int t = 0; t < S; ++t)
+            if ((st = stc_inclusive_scan_i64(h, sc, bsptr + size_t(t) * (K + 1) + 1, K, s)) != STC_OK) return st;
+    }
+    // slab sizes and the validation flags so far
+    SlabBases sb{};
+    int64_t* stage = h->h_stage;
+    for (int t = 0; t < S; ++t) stage[t] = 0;
+    for (int t = 0; t < S && K > 0; ++t)
+        STC_CUDA_TRY(cudaMemcpyAsync(&stage[t], bsptr + size_t(t) * (K + 1) + K, sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, s));
+    int* f = reinterpret_cast<int*>(&stage[SLAB_MAX]);
+    *f = 0;
+    STC_CUDA_TRY(cudaMemcpyAsync(f, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*f) {
+        const int flags = *f;
+        STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+        return stc_flags_to_status(flags);
+    }
+    int64_t tot = 0;
+    for (int t = 0; t < S; ++t) {
+        sb.base[t] = tot;
+        tot += stage[t];
+    }
+    if (tot != B->nnz) return STC_ERR_CUDA;
+    if (K > 0 && B->nnz > 0) {
+        switch (vbB) {
+        case 1: k_slab_scatter<uint8_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint8_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint8_t*>(s_val)); break;
+        case 4: k_slab_scatter<uint32_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint32_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint32_t*>(s_val)); break;
+        case 8: k_slab_scatter<uint64_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint64_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint64_t*>(s_val)); break;
+        default: k_slab_scatter<uint4><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint4*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint4*>(s_val)); break;
+        }
+        STC_LAUNCH_CHECK();
+        stc_count(h);
+    }
+    out.S = S;
+    out.args.resize(S);
+    out.view.resize(S);
+    out.cfg.resize(S);
+    out.ncell.resize(S);
+    for (int t = 0; t < S; ++t) {
+        SpgArgs g = make_args(A, B);
+        const int64_t w = B->ncols - int64_t(t) * RK_MAX_COLS;
+        g.ncols = w < RK_MAX_COLS ? w : RK_MAX_COLS;
+        g.ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
+        g.b_ptr = bsptr + size_t(t) * (K + 1);
+        g.b_col = s_col + sb.base[t];
+        g.b_val = s_val + size_t(sb.base[t]) * vbB;
+        g.nnzB = (t + 1 < S ? sb.base[t + 1] : B->nnz) - sb.base[t];
+        g.col_base = int(int64_t(t) * RK_MAX_COLS);
+        out.args[t] = g;
+        stc_csr v{};
+        v.nrows = K;
+        v.ncols = g.ncols;
+        v.nnz = g.nnzB;
+        v.rowptr = const_cast<int64_t*>(g.b_ptr);
+        v.col = const_cast<int32_t*>(g.b_col);
+        v.val = const_cast<void*>(g.b_val);
+        out.view[t] = v;
+        out.ncell[t] = g.ncell > 0 ? g.ncell : 1;
+        out.cfg[t] = rank_config(alg, g.ncols, out.ncell[t]);
+        if (!out.cfg[t].vcap) return STC_ERR_INVALID_ARG;
+    }
+    return STC_OK;
+}
+
 stc_status spgemm_slab_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C, bool validate,
                             stc_stream s) {
     const int64_t NR = A->nrows, K = A->ncols;
     const int S = int((B->ncols + RK_MAX_COLS - 1) / RK_MAX_COLS);
     if (S < 2 || S > SLAB_MAX) return STC_ERR_INVALID_ARG;
-    const size_t vbC = stc_val_bytes(alg, 'C'), vbB = stc_val_bytes(alg, 'B');
+    const size_t vbC = stc_val_bytes(alg, 'C');
     int64_t* c_ptr = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(NR + 1) * 8, s));
     if (!c_ptr) return STC_ERR_OOM;
     int32_t* c_col = nullptr;
@@ -1842,10 +1956,8 @@ stc_status spgemm_slab_impl(stc_handle* h, int alg, const stc_csr* A, const stc_
     stc_mark(h, s, 1);
 
     // 1) slabs of B
-    int32_t* bnd = sc.get<int32_t>(size_t(K) * size_t(S + 1));
-    int64_t* bsptr = sc.get<int64_t>(size_t(S) * size_t(K + 1));
-    int32_t* s_col = sc.get<int32_t>(size_t(B->nnz) + 1);
-    unsigned char* s_val = sc.get<unsigned char>((size_t(B->nnz) + 1) * vbB);
+    Slabs sl;
+    if ((st = build_slabs(h, sc, alg, A, B, S, sl, s)) != STC_OK) return fail(st);
     int64_t* cnt = sc.get<int64_t>(size_t(S) * size_t(NR));
     int64_t* off = sc.get<int64_t>(size_t(S) * size_t(NR));
     int64_t* ub = sc.get<int64_t>(size_t(NR));
@@ -1855,75 +1967,15 @@ stc_status spgemm_slab_impl(stc_handle* h, int alg, const stc_csr* A, const stc_
     const int NI = 2 * NBINS_ALL + 8;
     int* ints = sc.get<int>(size_t(S) * NI + 8);
     if (sc.failed) return fail(STC_ERR_OOM);
-    if (cudaMemsetAsync(bsptr, 0, sizeof(int64_t) * size_t(S) * size_t(K + 1), s) != cudaSuccess ||
-        cudaMemsetAsync(cnt, 0, sizeof(int64_t) * size_t(S) * size_t(NR), s) != cudaSuccess ||
+    if (cudaMemsetAsync(cnt, 0, sizeof(int64_t) * size_t(S) * size_t(NR), s) != cudaSuccess ||
         cudaMemsetAsync(ints, 0, sizeof(int) * (size_t(S) * NI + 8), s) != cudaSuccess)
         return fail(STC_ERR_CUDA);
     int* novf = ints + size_t(S) * NI;
-    const unsigned gw = unsigned(h->num_sms * 16);
-    if (K > 0) {
-        k_slab_bounds<<<gw, 256, 0, s>>>(B->rowptr, B->col, K, B->nnz, S, bnd, bsptr);
-        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
-        stc_count(h);
-        for (int t = 0; t < S; ++t)
-            if ((st = stc_inclusive_scan_i64(h, sc, bsptr + size_t(t) * (K + 1) + 1, K, s)) != STC_OK) return fail(st);
-    }
-    // slab sizes (and the validation flags so far)
-    SlabBases sb{};
-    {
-        int64_t* stage = h->h_stage;
-        for (int t = 0; t < S; ++t) stage[t] = 0;
-        for (int t = 0; t < S && K > 0; ++t)
-            if (cudaMemcpyAsync(&stage[t], bsptr + size_t(t) * (K + 1) + K, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                s) != cudaSuccess)
-                return fail(STC_ERR_CUDA);
-        int* f = reinterpret_cast<int*>(&stage[SLAB_MAX]);
-        *f = 0;
-        if (cudaMemcpyAsync(f, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return fail(STC_ERR_CUDA);
-        if (*f) {
-            const int flags = *f;
-            (void)cudaMemsetAsync(h->d_flags, 0, sizeof(int), s);
-            return fail(stc_flags_to_status(flags));
-        }
-        int64_t b = 0;
-        for (int t = 0; t < S; ++t) {
-            sb.base[t] = b;
-            b += stage[t];
-        }
-        if (b != B->nnz) return fail(STC_ERR_CUDA);
-    }
-    if (K > 0 && B->nnz > 0) {
-        switch (vbB) {
-        case 1: k_slab_scatter<uint8_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint8_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint8_t*>(s_val)); break;
-        case 4: k_slab_scatter<uint32_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint32_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint32_t*>(s_val)); break;
-        case 8: k_slab_scatter<uint64_t><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint64_t*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint64_t*>(s_val)); break;
-        default: k_slab_scatter<uint4><<<gw, 256, 0, s>>>(B->rowptr, B->col, static_cast<const uint4*>(B->val), K, B->nnz, S, bnd, bsptr, sb, s_col, reinterpret_cast<uint4*>(s_val)); break;
-        }
-        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
-        stc_count(h);
-    }
-    std::vector<SpgArgs> args(S);
-    std::vector<RankCfg> cfgs(S);
-    std::vector<int> ncells(S);
+    const std::vector<SpgArgs>& args = sl.args;
+    const std::vector<RankCfg>& cfgs = sl.cfg;
+    const std::vector<int>& ncells = sl.ncell;
     size_t rec_total = 0;
-    for (int t = 0; t < S; ++t) {
-        SpgArgs g = make_args(A, B);
-        const int64_t w = B->ncols - int64_t(t) * RK_MAX_COLS;
-        g.ncols = w < RK_MAX_COLS ? w : RK_MAX_COLS;
-        g.ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
-        g.b_ptr = bsptr + size_t(t) * (K + 1);
-        g.b_col = s_col + sb.base[t];
-        g.b_val = s_val + size_t(sb.base[t]) * vbB;
-        g.nnzB = (t + 1 < S ? sb.base[t + 1] : B->nnz) - sb.base[t];
-        g.col_base = int(int64_t(t) * RK_MAX_COLS);
-        args[t] = g;
-        ncells[t] = g.ncell > 0 ? g.ncell : 1;
-        cfgs[t] = rank_config(alg, g.ncols, ncells[t]);
-        if (!cfgs[t].vcap) return fail(STC_ERR_INVALID_ARG);
-        rec_total += size_t(NR) * rank_layout(ncells[t], 0, 0, 4, false).winfirst;
-    }
+    for (int t = 0; t < S; ++t) rec_total += size_t(NR) * rank_layout(ncells[t], 0, 0, 4, false).winfirst;
     stc_mark(h, s, 2);
 
     // 2) per slab: analysis, binning, symbolic counts (and stored rank records when
@@ -2198,17 +2250,9 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
     if (!c_col || !c_val) return fail(STC_ERR_OOM);
     stc_mark(h, s, 4);
     if (NR > 0 && nnz > 0) {
-        int64_t blocks = (int64_t(n_rows) * 32 + 255) / 256;
-        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        if (blocks < 1) blocks = 1;
-        switch (vbytes) {
-        case 1: k_compact<uint8_t><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, sval, c_col, static_cast<uint8_t*>(c_val)); break;
-        case 4: k_compact<uint32_t><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, reinterpret_cast<const uint32_t*>(sval), c_col, static_cast<uint32_t*>(c_val)); break;
-        case 8: k_compact<uint64_t><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, reinterpret_cast<const uint64_t*>(sval), c_col, static_cast<uint64_t*>(c_val)); break;
-        default: k_compact<uint4><<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, soff, cap, c_ptr, scol, reinterpret_cast<const uint4*>(sval), c_col, static_cast<uint4*>(c_val)); break;
-        }
-        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
-        stc_count(h);
+        if ((st = run_compact(h, vbytes, rowlist, nlist, n_rows, soff, cap, c_ptr, nullptr, scol, sval, c_col, c_val,
+                              s)) != STC_OK)
+            return fail(st);
         if (n_ovf > 0) {
             RankOut out{};
             out.ptr = c_ptr;
@@ -2224,6 +2268,226 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
         stats->scratch_entries = S_total;
         stats->nnz = nnz;
         stats->mean_abs_log2_error = (weights && n_rows > 0) ? err_sum / n_rows : -1.0;
+    }
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->rowptr = c_ptr;
+    C->col = c_col;
+    C->val = c_val;
+    C->nnz = nnz;
+    return STC_OK;
+}
+
+// Learned single pass over column slabs: every slab B_s is its own learned
+// product A B_s (features of A and B_s, model, capacities, one numeric pass into
+// the slab's scratch that records each row's exact size and its overflows);
+// then one scan over the per-(row, slab) sizes places every slab's part of every
+// row in C, the rows that fit are compacted there and the overflowing
+// (row, slab) parts are recomputed exactly in place.
+stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
+                                    const float* weights, float margin, stc_learned_stats* stats, bool validate,
+                                    stc_stream s) {
+    const int64_t NR = A->nrows, K = A->ncols;
+    const int S = int((B->ncols + RK_MAX_COLS - 1) / RK_MAX_COLS);
+    if (S < 2 || S > SLAB_MAX) return STC_ERR_INVALID_ARG;
+    const size_t vbytes = stc_val_bytes(alg, 'C');
+    int64_t* c_ptr = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(NR + 1) * 8, s));
+    if (!c_ptr) return STC_ERR_OOM;
+    int32_t* c_col = nullptr;
+    void* c_val = nullptr;
+    auto fail = [&](stc_status st) {
+        (void)cudaGetLastError();
+        stc_free_bytes(h, c_ptr, s);
+        if (c_col) stc_free_bytes(h, c_col, s);
+        if (c_val) stc_free_bytes(h, c_val, s);
+        return st;
+    };
+    StcScratch sc(h, s);
+    stc_mark(h, s, 0);
+    if (cudaMemsetAsync(c_ptr, 0, size_t(NR + 1) * 8, s) != cudaSuccess) return fail(STC_ERR_CUDA);
+    stc_status st;
+    if (validate) {
+        if ((st = stc_validate_csr_async(h, A, s)) != STC_OK) return fail(st);
+        if ((st = stc_validate_csr_async(h, B, s)) != STC_OK) return fail(st);
+    }
+    stc_mark(h, s, 1);
+    Slabs sl;
+    if ((st = build_slabs(h, sc, alg, A, B, S, sl, s)) != STC_OK) return fail(st);
+    const int NI = 2 * NBINS_ALL + 16;
+    int64_t* ub = sc.get<int64_t>(size_t(NR));
+    int64_t* cnt = sc.get<int64_t>(size_t(S) * size_t(NR));
+    int64_t* off = sc.get<int64_t>(size_t(S) * size_t(NR));
+    int64_t* cap = sc.get<int64_t>(size_t(S) * size_t(NR));
+    int64_t* soff = sc.get<int64_t>(size_t(S) * size_t(NR + 1));
+    int32_t* rowlists = sc.get<int32_t>(size_t(S) * size_t(NR));
+    int32_t* ovfs = sc.get<int32_t>(size_t(S) * size_t(NR));
+    int64_t* nnz_scratch = sc.get<int64_t>(size_t(NR));
+    int32_t* ovf_scratch = sc.get<int32_t>(size_t(NR));
+    int* ints = sc.get<int>(size_t(S) * NI + 8);
+    double* err = sc.get<double>(1);
+    float* pred = weights ? sc.get<float>(size_t(NR)) : nullptr;
+    float* feat = weights ? sc.get<float>(size_t(NR) * STC_MLP_FEAT_STRIDE) : nullptr;
+    if (sc.failed) return fail(STC_ERR_OOM);
+    if (cudaMemsetAsync(cnt, 0, sizeof(int64_t) * size_t(S) * size_t(NR), s) != cudaSuccess ||
+        cudaMemsetAsync(soff, 0, sizeof(int64_t) * size_t(S) * size_t(NR + 1), s) != cudaSuccess ||
+        cudaMemsetAsync(ints, 0, sizeof(int) * (size_t(S) * NI + 8), s) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(double), s) != cudaSuccess)
+        return fail(STC_ERR_CUDA);
+    int* dummy_novf = ints + size_t(S) * NI;
+    std::vector<int32_t*> s_cols(S, nullptr);
+    std::vector<unsigned char*> s_vals(S, nullptr);
+    int64_t scratch_total = 0;
+    stc_mark(h, s, 2);
+
+    // 1) per slab: analysis, capacities, one numeric pass into the slab's scratch
+    for (int t = 0; t < S && NR > 0; ++t) {
+        SpgRows R{};
+        R.one = sl.args[t];
+        R.nb = 1;
+        int* ti = ints + size_t(t) * NI;
+        int* bin_count = ti;
+        int* cursor = ti + NBINS_ALL;
+        int* nlist = ti + 2 * NBINS_ALL;
+        int* counters = ti + 2 * NBINS_ALL + 1;
+        int* maxcap = ti + 2 * NBINS_ALL + 4;
+        int* novf = ti + 2 * NBINS_ALL + 5;
+        int32_t* rowlist = rowlists + size_t(t) * NR;
+        int64_t* cap_t = cap + size_t(t) * NR;
+        int64_t* soff_t = soff + size_t(t) * (NR + 1);
+        int64_t blocks = (NR * 32 + 255) / 256;
+        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, nullptr);
+        k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, nullptr, cursor, rowlist);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h, 3);
+        if (weights) {
+            if ((st = stc_features_impl(h, sc, A, &sl.view[t], feat, s)) != STC_OK) return fail(st);
+            if ((st = stc_mlp_forward_impl(h, weights, feat, NR, pred, s)) != STC_OK) return fail(st);
+        }
+        int64_t cb = (NR + 255) / 256;
+        if (cb > int64_t(h->num_sms) * 8) cb = int64_t(h->num_sms) * 8;
+        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred, margin, sl.args[t].ncols, cap_t, soff_t + 1, maxcap);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+        if ((st = stc_inclusive_scan_i64(h, sc, soff_t + 1, NR, s)) != STC_OK) return fail(st);
+        int* mc = reinterpret_cast<int*>(&h->h_stage[1]);
+        *mc = 0;
+        if (cudaMemcpyAsync(&h->h_stage[0], soff_t + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(mc, maxcap, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(STC_ERR_CUDA);
+        const int64_t S_t = h->h_stage[0];
+        const int max_cap = *mc;
+        scratch_total += S_t;
+        s_cols[t] = sc.get<int32_t>(size_t(S_t) + 1);
+        s_vals[t] = sc.get<unsigned char>((size_t(S_t) + 1) * vbytes);
+        if (!s_cols[t] || !s_vals[t]) return fail(STC_ERR_OOM);
+        StcScratch sct(h, s);  // the slab's cell-offset table
+        if (max_cap >= sl.cfg[t].vcap - RK_CELL) {
+            int32_t* ctab = sct.get<int32_t>(size_t(K) * size_t(sl.ncell[t] + 1));
+            if (!ctab) return fail(STC_ERR_OOM);
+            R.one.ctab = ctab;
+            int64_t bx = (K * (sl.ncell[t] + 1) + 255) / 256;
+            if (bx > int64_t(h->num_sms) * 64) bx = int64_t(h->num_sms) * 64;
+            k_cell_offsets<<<dim3(unsigned(bx > 0 ? bx : 1), 1), 256, 0, s>>>(R);
+            if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+            stc_count(h);
+        }
+        RankOut out{};
+        out.ptr = soff_t;
+        out.cap = cap_t;
+        out.nnz = cnt + size_t(t) * NR;
+        out.ovf = ovfs + size_t(t) * NR;
+        out.novf = novf;
+        out.pred = pred;
+        out.err = err;
+        if ((st = run_numeric_any(h, alg, R, sl.ncell[t], sl.cfg[t], rowlist, nlist, counters, out, s_cols[t],
+                                  s_vals[t], NR, s)) != STC_OK)
+            return fail(st);
+    }
+    stc_mark(h, s, 3);
+
+    // 2) row pointers and per-slab offsets
+    if (NR > 0) {
+        const unsigned gb = unsigned(h->num_sms * 8);
+        k_slab_total<<<gb, 256, 0, s>>>(NR, S, cnt, c_ptr);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        if ((st = stc_inclusive_scan_i64(h, sc, c_ptr + 1, NR, s)) != STC_OK) return fail(st);
+        k_slab_offsets<<<gb, 256, 0, s>>>(NR, S, cnt, c_ptr, off);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h, 2);
+    }
+    int64_t nnz = 0;
+    std::vector<int> n_ovf(S, 0), n_rows(S, 0);
+    double err_sum = 0.0;
+    {
+        int* v = reinterpret_cast<int*>(&h->h_stage[2]);  // 2 S ints: h_stage[2 .. 2 + S)
+        for (int t = 0; t < 2 * S; ++t) v[t] = 0;
+        h->h_stage[SLAB_MAX + 8] = 0;
+        double* e = reinterpret_cast<double*>(&h->h_stage[SLAB_MAX + 9]);
+        *e = 0.0;
+        for (int t = 0; t < S && NR > 0; ++t) {
+            const int* ti = ints + size_t(t) * NI;
+            if (cudaMemcpyAsync(&v[2 * t], ti + 2 * NBINS_ALL + 5, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(&v[2 * t + 1], ti + 2 * NBINS_ALL, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess)
+                return fail(STC_ERR_CUDA);
+        }
+        if (cudaMemcpyAsync(&h->h_stage[SLAB_MAX + 8], c_ptr + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(e, err, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(STC_ERR_CUDA);
+        nnz = h->h_stage[SLAB_MAX + 8];
+        err_sum = *e;
+        for (int t = 0; t < S; ++t) {
+            n_ovf[t] = v[2 * t];
+            n_rows[t] = v[2 * t + 1];
+        }
+    }
+    if (nnz < 0) return fail(STC_ERR_CUDA);
+    c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
+    c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
+    if ((!c_col || !c_val) && nnz > 0) return fail(STC_ERR_OOM);
+    stc_mark(h, s, 4);
+
+    // 3) per slab: compaction of the rows that fit, exact recomputation of the others
+    int units = 0, overflows = 0;
+    for (int t = 0; t < S && NR > 0 && nnz > 0; ++t) {
+        const int* ti = ints + size_t(t) * NI;
+        int64_t* cnt_t = cnt + size_t(t) * NR;
+        int64_t* off_t = off + size_t(t) * NR;
+        if ((st = run_compact(h, vbytes, rowlists + size_t(t) * NR, ti + 2 * NBINS_ALL, n_rows[t],
+                              soff + size_t(t) * (NR + 1), cap + size_t(t) * NR, off_t, cnt_t, s_cols[t], s_vals[t],
+                              c_col, c_val, s)) != STC_OK)
+            return fail(st);
+        if (n_ovf[t] > 0) {
+            SpgRows R{};
+            R.one = sl.args[t];
+            R.nb = 1;
+            RankOut out{};
+            out.ptr = off_t;
+            out.cap = cnt_t;  // exact sizes
+            out.nnz = nnz_scratch;
+            out.ovf = ovf_scratch;
+            out.novf = dummy_novf;
+            if ((st = run_numeric_any(h, alg, R, sl.ncell[t], sl.cfg[t], ovfs + size_t(t) * NR,
+                                      ti + 2 * NBINS_ALL + 5, const_cast<int*>(ti) + 2 * NBINS_ALL + 2, out, c_col,
+                                      c_val, NR, s)) != STC_OK)
+                return fail(st);
+        }
+        units += n_rows[t];
+        overflows += n_ovf[t];
+    }
+    stc_mark(h, s, 5);
+    if (stats) {
+        stats->rows = units;
+        stats->overflow_rows = overflows;
+        stats->scratch_entries = scratch_total;
+        stats->nnz = nnz;
+        stats->mean_abs_log2_error = (weights && units > 0) ? err_sum / units : -1.0;
     }
     C->nrows = A->nrows;
     C->ncols = B->ncols;
@@ -2432,8 +2696,10 @@ stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, con
     C->rowptr = nullptr;
     C->col = nullptr;
     C->val = nullptr;
+    if (B->ncols > RK_MAX_COLS && (B->ncols + RK_MAX_COLS - 1) / RK_MAX_COLS <= SLAB_MAX)
+        return spgemm_learned_slab_impl(h, alg, A, B, C, weights, margin, stats, !(opts && opts->skip_validation), s);
     if (B->ncols > RK_MAX_COLS) {
-        // wider outputs: the exact two-pass path (no capacity to predict)
+        // beyond the slab path: the exact two-pass path (no capacity to predict)
         if (stats) {
             stats->rows = -1;
             stats->overflow_rows = 0;

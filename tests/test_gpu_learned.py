@@ -151,3 +151,30 @@ def test_what_the_model_gains(H, trained):
     assert excess_ml <= 0.5 * excess_ub
     assert st_ml["overflow_rows"] <= 0.05 * st_ml["rows"]
     assert 0 <= st_ml["mean_abs_log2_error"] < 0.5
+
+
+@pytest.mark.parametrize("alg", ALL)
+def test_learned_column_slabs_equal_plain(H, trained, alg):
+    """More than 2^18 output columns: every column slab is its own learned pass;
+    the result equals the plain product under any model, and the oracle's."""
+    import paper_1512_00066_b300 as stc
+    w, _ = trained
+    A = W.random_csr(500, 900, 40, seed=51, empty_frac=0.05)
+    B = W.random_csr(900, 2 * (1 << 18) + 777, 300, seed=52, empty_frac=0.05)
+    A.val = _vals(alg, A.nnz, 53)
+    B.val = _vals(alg if alg != O.MULTPATH else O.MP_I32, B.nnz, 54) if alg != O.MULTPATH else \
+        W.multpath_values(B.nnz, 20, 5, 54)
+    dA, dB = to_dev(A), to_dev(B)
+    plain = H.spgemm(alg, dA, dB)
+    under = torch.zeros(stc.MLP_NUM_WEIGHTS, dtype=torch.float32, device="cuda")
+    for weights, margin in ((w, 0.25), (None, 0.0), (under, 0.0)):
+        C, st = H.spgemm_learned(alg, dA, dB, weights, margin)
+        _same(alg, C, plain)
+        assert st["nnz"] == plain.nnz and st["rows"] > A.nrows  # (row, slab) units
+    C, st = H.spgemm_learned(alg, dA, dB, under, 0.0)
+    assert st["overflow_rows"] > 0
+    if alg == O.PT_F32:
+        rp, col, val = C.to_host()
+        ptr, rcol, rval, rabs = O.spgemm(alg, A, B, want_abs=True)
+        assert np.array_equal(rp, ptr) and np.array_equal(col, rcol)
+        compare_values(alg, val, rval, rabs)
