@@ -36,8 +36,8 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM bytes (read + write) per output entry of the fp64 numeric rank kernel, from
 # the ncu capture in profiles/k_numeric_rank_fp64_rmat16.md (R-MAT scale 16).
 # Traffic grows with the output (B stays in L2), so a full launch is scaled by its
-# nnz(C).  None until a capture of the current kernel is recorded.
-NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = None
+# nnz(C): 0.347 GB read + 1.848 GB written for 163,809,247 entries.
+NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = (0.347073e9 + 1.847521e9) / 163809247
 # FP64 peak of the B300 part: 2 FP64 operations (DADD, DMUL or DFMA) per clock per SM
 # (the nominal 1.25 TFLOP/s counting an FMA as two), 148 SMs, 2032 MHz maximum clock.
 FP64_OPS_PER_CLK_SM = 2
