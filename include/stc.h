@@ -137,7 +137,14 @@ typedef struct {
     int32_t skip_validation; /* 1: trust the CSR contents (no device checks)     */
     int32_t window_cols;     /* 0: automatic; else the column-window width of the
                                 numeric accumulator (power of two, >= 1024)      */
-    int32_t reserved[6];     /* must be zero                                     */
+    int32_t light_rows;      /* 0: the handle's tuned value (stc_autotune_spgemm),
+                                or none when untuned; -1: none; L in [1, 30]:
+                                output rows whose product count is below 2^L get
+                                their own numeric launch of 512-thread CTAs (two
+                                per SM) beside the wide one, when such a row fits
+                                the smaller value buffer (else ignored).  Applies
+                                to outputs of at most 2^18 columns.              */
+    int32_t reserved[5];     /* must be zero                                     */
 } stc_opts;
 
 /* Create a handle bound to the current CUDA device.  alloc/free may both be
@@ -375,6 +382,32 @@ typedef struct {
 STC_API stc_status stc_contract_spgemm_learned(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
                                                stc_csr* C, const float* weights, float margin,
                                                stc_learned_stats* stats, const stc_opts* opts, stc_stream stream);
+
+/*
+ * Autotuner (the single-GPU counterpart of the paper's tuning over candidate
+ * decompositions with performance models, Section 5.1, and of the
+ * automatically-adjusted performance models it names as future work, Section 7).
+ *
+ * stc_autotune_spgemm times C = A (x) B under every candidate light-row threshold
+ * (see stc_opts.light_rows: none, then each L whose rows fit the light launch's
+ * value buffer, ascending), each after one untimed run, with CUDA events on
+ * `stream`, and stores the fastest in the handle's cache for this algebra and
+ * output width (ceil(log2 B->ncols)); later calls with light_rows == 0 use it.
+ * cand_out / ms_out (host, 8 entries each, may be NULL) receive the candidates
+ * (-1 = none) and their times in milliseconds, *ncand_out their number, *best_out
+ * the chosen threshold.  Outputs of the timing runs are released.  Errors: those
+ * of stc_contract_spgemm; STC_ERR_INVALID_ARG for B->ncols > 2^18.
+ *
+ * stc_tune_save writes the handle's cache as text (a header naming the device
+ * and its SM count, then one "algebra log2-columns threshold" line per entry);
+ * stc_tune_load reads such a file into the cache, STC_ERR_INVALID_ARG when it
+ * was written for another device or is malformed (the cache is then unchanged).
+ */
+STC_API stc_status stc_autotune_spgemm(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
+                                       int32_t* best_out, int32_t* cand_out, float* ms_out, int32_t* ncand_out,
+                                       stc_stream stream);
+STC_API stc_status stc_tune_save(const stc_handle* h, const char* path);
+STC_API stc_status stc_tune_load(stc_handle* h, const char* path);
 
 /*
  * Instrumentation (no counterpart in the paper, which reports only the share of

@@ -64,7 +64,7 @@ class _Csr(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("skip_validation", ctypes.c_int32), ("window_cols", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("light_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class _LearnedStats(ctypes.Structure):
@@ -114,6 +114,13 @@ def lib():
             L.stc_bellman_ford.restype = ctypes.c_int
             L.stc_set_timing.argtypes = [p, i32]
             L.stc_set_round_driver.argtypes = [p, i32]
+            L.stc_autotune_spgemm.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, p, p, p,
+                                              p]
+            L.stc_autotune_spgemm.restype = ctypes.c_int
+            L.stc_tune_save.argtypes = [p, ctypes.c_char_p]
+            L.stc_tune_save.restype = ctypes.c_int
+            L.stc_tune_load.argtypes = [p, ctypes.c_char_p]
+            L.stc_tune_load.restype = ctypes.c_int
             L.stc_set_round_driver.restype = ctypes.c_int
             L.stc_set_timing.restype = ctypes.c_int
             L.stc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_float), i32]
@@ -251,10 +258,12 @@ class Handle:
     # -------------------------------------------------------------- calls
 
     def spgemm(self, alg: int, A: DeviceCsr, B: DeviceCsr, skip_validation: bool = False,
-               window_cols: int = 0, stream=None) -> DeviceCsr:
-        """C = A (x) B (plain two-pass SpGEMM); synchronises the stream once."""
+               window_cols: int = 0, light_rows: int = 0, stream=None) -> DeviceCsr:
+        """C = A (x) B (plain two-pass SpGEMM); synchronises the stream once.
+        light_rows: 0 tuned/default, -1 none, L > 0 light-row launch for rows with
+        fewer than 2^L products (stc_opts.light_rows)."""
         C = _Csr()
-        opts = _Opts(1 if skip_validation else 0, int(window_cols))
+        opts = _Opts(1 if skip_validation else 0, int(window_cols), int(light_rows))
         a, b = A._c(), B._c()
         st = lib().stc_contract_spgemm(self._h, alg, ctypes.byref(a), ctypes.byref(b), ctypes.byref(C),
                                        ctypes.byref(opts), _stream_ptr(stream))
@@ -270,7 +279,7 @@ class Handle:
             val = raw.view(ct)[:nnz]
         return DeviceCsr(int(C.nrows), int(C.ncols), rowptr, col, val)
 
-    def spgemm_batched(self, alg: int, As, Bs, skip_validation: bool = False, stream=None):
+    def spgemm_batched(self, alg: int, As, Bs, skip_validation: bool = False, light_rows: int = 0, stream=None):
         """C_b = A_b (x) B_b for every pair, in one batched call (one synchronisation).
 
         Returns a list of DeviceCsr whose tensors are views into three shared
@@ -281,7 +290,7 @@ class Handle:
         A = (_Csr * nb)(*[a._c() for a in As])
         B = (_Csr * nb)(*[b._c() for b in Bs])
         C = (_Csr * nb)()
-        opts = _Opts(1 if skip_validation else 0, 0)
+        opts = _Opts(1 if skip_validation else 0, 0, int(light_rows))
         st = lib().stc_contract_spgemm_batched(self._h, alg, nb, A, B, C, ctypes.byref(opts), _stream_ptr(stream))
         _check(st, "stc_contract_spgemm_batched")
         rp = self._take(C[0].rowptr).view(torch.int64)
@@ -432,6 +441,25 @@ class Handle:
                             int(batch), bc.data_ptr(), _stream_ptr(stream))
         _check(st, "stc_mfbc")
         return bc
+
+    def autotune_spgemm(self, alg: int, A: DeviceCsr, B: DeviceCsr, stream=None) -> dict:
+        """Time the candidate light-row thresholds on C = A (x) B and cache the best
+        for this algebra and output width: {"best": L, "candidates": {L: ms}}."""
+        best = ctypes.c_int32(0)
+        n = ctypes.c_int32(0)
+        cand = (ctypes.c_int32 * 8)()
+        ms = (ctypes.c_float * 8)()
+        a, b = A._c(), B._c()
+        st = lib().stc_autotune_spgemm(self._h, alg, ctypes.byref(a), ctypes.byref(b), ctypes.byref(best), cand,
+                                       ms, ctypes.byref(n), _stream_ptr(stream))
+        _check(st, "stc_autotune_spgemm")
+        return {"best": int(best.value), "candidates": {int(cand[i]): float(ms[i]) for i in range(n.value)}}
+
+    def tune_save(self, path: str):
+        _check(lib().stc_tune_save(self._h, str(path).encode()), "stc_tune_save")
+
+    def tune_load(self, path: str):
+        _check(lib().stc_tune_load(self._h, str(path).encode()), "stc_tune_load")
 
     def set_round_driver(self, driver: str = "graph"):
         """Round loops of mfbc / mfbc_sssp: "graph" (one CUDA graph launch per

@@ -199,6 +199,17 @@ __global__ void k_bin_offsets(const int* __restrict__ bin_count, int* __restrict
 
 // Scatter of row ids into their bins (order inside a bin is arbitrary: rows are
 // independent).  Block-aggregated: one global atomic per bin per block.
+// Sizes of the heavy prefix (bins above L) and the light suffix (bins 1..L) of
+// the row list.
+__global__ void k_split_counts(const int* __restrict__ bin_count, int L, int* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int heavy = 0, light = 0;
+        for (int b = 1; b < NBINS; ++b) (b > L ? heavy : light) += bin_count[b];
+        out[0] = heavy;
+        out[1] = light;
+    }
+}
+
 // single (may be null): non-zero for the rows of BIN_COPY.
 __global__ void __launch_bounds__(512) k_bin_scatter(int64_t nA, const int64_t* __restrict__ ub,
                                                      const int64_t* __restrict__ single,
@@ -1366,6 +1377,7 @@ struct RankCfg {
     bool small;
     int vcap, maxwin;
     size_t smem;
+    int nt = 0;  // threads per CTA: 256 (small), 512 (light rows), 1024 (wide)
 };
 
 template <int ALG, int NT, int MINB>
@@ -1392,6 +1404,9 @@ stc_status run_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, cons
                             int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, const int2* rec_meta, stc_stream s) {
     if (cfg.small)
         return launch_numeric_rank<ALG, 256, 4>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
+                                                NR, rec, rec_meta, s);
+    if (cfg.nt == 512)
+        return launch_numeric_rank<ALG, 512, 2>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
                                                 NR, rec, rec_meta, s);
     return launch_numeric_rank<ALG, RK_NT, 1>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val,
                                               NR, rec, rec_meta, s);
@@ -1429,13 +1444,17 @@ stc_status run_copy_any(stc_handle* h, int alg, const SpgRows& R, const int32_t*
     return STC_OK;
 }
 
-RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max) {
+// light != 0: the configuration of the light-row launch (512 threads, two CTAs
+// per SM sharing its shared memory, a value buffer of a few thousand ranks).
+RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max, bool light = false) {
     RankCfg c{};
     const size_t acc_bytes = alg == ALG_PT_F64 ? 8 : 4;
     const bool mp = alg == ALG_MULTPATH;
-    c.small = ncols_max <= 16384;
-    const int nt = c.small ? 256 : RK_NT;
-    const size_t target = c.small ? 54 * 1024 : RK_SMEM_TARGET;  // four / one CTA per SM
+    c.small = !light && ncols_max <= 16384;
+    const int nt = light ? 512 : c.small ? 256 : RK_NT;
+    c.nt = nt;
+    // four / two / one CTA(s) per SM
+    const size_t target = c.small ? 54 * 1024 : light ? 112 * 1024 : RK_SMEM_TARGET;
     const size_t static_bytes = size_t(nt) * 16 + size_t(nt) * 8 + 512 + sizeof(SpgArgs);
     for (int v = 64 * 1024; v >= 2048; v -= 1024) {
         const int mw = int(ncols_max / (v - RK_CELL)) + 2;
@@ -1456,7 +1475,7 @@ RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max) {
 stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_h, const int64_t* row_off_h,
                             bool validate, const stc_csr* Av, const stc_csr* Bv, int64_t** c_ptr_out,
                             int32_t** c_col_out, void** c_val_out, int64_t* nnz_out, int64_t* bounds_h,
-                            stc_stream s) {
+                            int light_log2, stc_stream s) {
     *c_ptr_out = nullptr;
     *c_col_out = nullptr;
     *c_val_out = nullptr;
@@ -1469,6 +1488,14 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
                               ? int((ncols_max + RK_CELL - 1) >> RK_CELL_SHIFT) : 1;
     const RankCfg cfg = rank_config(alg, ncols_max, ncell_max);
     if (!cfg.vcap) return STC_ERR_INVALID_ARG;
+    // light rows (ub < 2^light_log2) get their own launch of 512-thread CTAs, two per
+    // SM, beside the wide launch; only when their whole row fits one rank window
+    RankCfg lcfg{};
+    int L = light_log2 > 0 && light_log2 < NBINS ? light_log2 : 0;
+    if (L) {
+        lcfg = rank_config(alg, ncols_max, ncell_max, true);
+        if (!lcfg.vcap || (int64_t(1) << L) > int64_t(lcfg.vcap - RK_CELL)) L = 0;
+    }
 
     int64_t* c_ptr = static_cast<int64_t*>(stc_alloc_bytes(h, size_t(NR + 1) * 8, s));
     if (!c_ptr) return STC_ERR_OOM;
@@ -1559,16 +1586,24 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     }
     // the single synchronisation: nnz, the largest row, the validation flags (and batch bounds)
     int* stage_i = reinterpret_cast<int*>(&h->h_stage[1]);
+    int* stage_bins = reinterpret_cast<int*>(&h->h_stage[8]);  // NBINS_ALL ints
     stage_i[0] = 0;
     stage_i[1] = 0;
     if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&stage_i[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&stage_i[1], max_nnz, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        (L && cudaMemcpyAsync(stage_bins, bin_count, sizeof(int) * NBINS_ALL, cudaMemcpyDeviceToHost, s) !=
+                  cudaSuccess) ||
         (nb > 1 && cudaMemcpyAsync(bounds_h, bounds_d, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToHost, s) !=
                        cudaSuccess) ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(STC_ERR_CUDA);
+    }
+    int64_t n_heavy = 0, n_light = 0;
+    if (L) {
+        for (int b = 1; b < NBINS; ++b) (b > L ? n_heavy : n_light) += stage_bins[b];
+        if (n_light == 0) L = 0;
     }
     const int64_t nnz = h->h_stage[0];
     const int flags = stage_i[0];
@@ -1619,9 +1654,29 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     if (nnz > 0) {
         RankOut out{};
         out.ptr = c_ptr;
-        if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, nlist, counters + 1, out, c_col, c_val, NR,
-                                  s, rec, rec_meta)) != STC_OK)
+        if (L) {
+            // heavy rows (the list's prefix) on this stream, light rows (its suffix)
+            // on the auxiliary stream: their CTAs take the SMs the heavy launch frees
+            int* split = ints + 2 * NBINS_ALL + 5;  // [0] heavy rows, [1] light rows
+            k_split_counts<<<1, 32, 0, s>>>(bin_count, L, split);
+            if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+            stc_count(h);
+            if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, split, counters + 1, out, c_col, c_val,
+                                      NR, s, rec, rec_meta)) != STC_OK)
+                return fail(st);
+            cudaStream_t aux;
+            if ((st = stc_fork(h, s, &aux)) != STC_OK) return fail(st);
+            const size_t rec16 = rec_bytes / 16;
+            st = run_numeric_any(h, alg, R, ncell_max, lcfg, rowlist + n_heavy, split + 1, counters + 2, out, c_col,
+                                 c_val, NR, aux, rec ? rec + size_t(n_heavy) * rec16 : nullptr,
+                                 rec_meta ? rec_meta + n_heavy : nullptr);
+            const stc_status sj = stc_join(h, s);
+            if (st != STC_OK) return fail(st);
+            if (sj != STC_OK) return fail(sj);
+        } else if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, nlist, counters + 1, out, c_col,
+                                         c_val, NR, s, rec, rec_meta)) != STC_OK) {
             return fail(st);
+        }
         if ((st = run_copy_any(h, alg, R, rowlist, nlist, bin_count + BIN_COPY, c_ptr, c_col, c_val, s)) != STC_OK)
             return fail(st);
     }
@@ -2497,6 +2552,23 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
     C->nnz = nnz;
     return STC_OK;
 }
+// Light-row threshold of a call: the option when set, else the handle's tuned
+// value for this algebra and output width, else no light launch.
+int resolve_light(stc_handle* h, int alg, int64_t ncols_max, const stc_opts* opts) {
+    int L = opts ? opts->light_rows : 0;
+    if (L == 0) {
+        const int c = stc_log2_ceil(ncols_max > 0 ? ncols_max : 1);
+        const signed char t = (alg >= 0 && alg < 6 && c < 40) ? h->tune_light[alg][c] : -128;
+        L = t == -128 ? -1 : t;
+    }
+    return L > 0 ? L : 0;
+}
+
+int64_t ncols_max_of(const std::vector<SpgArgs>& args) {
+    int64_t m = 0;
+    for (const SpgArgs& g : args) m = g.ncols > m ? g.ncols : m;
+    return m;
+}
 }  // namespace
 
 stc_status stc_spgemm_batched_impl(stc_handle* h, int alg, int nb, const stc_csr* A, const stc_csr* B,
@@ -2519,7 +2591,8 @@ stc_status stc_spgemm_batched_impl(stc_handle* h, int alg, int nb, const stc_csr
     void* c_val = nullptr;
     int64_t nnz = 0;
     stc_status st = spgemm_rank_impl(h, alg, nb, args.data(), row_off.data(), !(opts && opts->skip_validation),
-                                     A, B, &c_ptr, &c_col, &c_val, &nnz, bounds.data(), s);
+                                     A, B, &c_ptr, &c_col, &c_val, &nnz, bounds.data(),
+                                     resolve_light(h, alg, ncols_max_of(args), opts), s);
     if (st != STC_OK) return st;
     const size_t vbytes = stc_val_bytes(alg, 'C');
     for (int b = 0; b < nb; ++b) {
@@ -2674,7 +2747,8 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
         void* c_val = nullptr;
         int64_t nnz = 0;
         stc_status st = spgemm_rank_impl(h, alg, 1, &g, row_off, !(opts && opts->skip_validation), A, B, &c_ptr,
-                                         &c_col, &c_val, &nnz, bounds, s);
+                                         &c_col, &c_val, &nnz, bounds,
+                                         resolve_light(h, alg, B->ncols, opts), s);
         if (st != STC_OK) return st;
         C->rowptr = c_ptr;
         C->col = c_col;
@@ -2685,6 +2759,64 @@ stc_status stc_spgemm_impl(stc_handle* h, int alg, const stc_csr* A, const stc_c
     if (!(opts && opts->window_cols) && (B->ncols + RK_MAX_COLS - 1) / RK_MAX_COLS <= SLAB_MAX)
         return spgemm_slab_impl(h, alg, A, B, C, !(opts && opts->skip_validation), s);
     return spgemm_window_impl(h, alg, A, B, C, opts, s);
+}
+
+// Time every candidate light-row threshold on this product; cache the fastest.
+stc_status stc_autotune_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, int32_t* best_out,
+                             int32_t* cand_out, float* ms_out, int32_t* ncand_out, stc_stream s) {
+    if (B->ncols > RK_MAX_COLS) return STC_ERR_INVALID_ARG;
+    const int ncell = B->ncols > 0 ? int((B->ncols + RK_CELL - 1) >> RK_CELL_SHIFT) : 1;
+    const RankCfg lc = rank_config(alg, B->ncols, ncell, true);
+    int lmax = 0;
+    for (int L = 1; L < 30; ++L)
+        if (lc.vcap && (int64_t(1) << L) <= int64_t(lc.vcap - RK_CELL)) lmax = L;
+    std::vector<int> cands{-1};
+    for (int L = lmax - 6 > 6 ? lmax - 6 : 6; L <= lmax; ++L) cands.push_back(L);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    STC_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return STC_ERR_CUDA;
+    }
+    stc_status st = STC_OK;
+    int best = -1;
+    float best_ms = 0.0f;
+    std::vector<float> times;
+    for (int cand : cands) {
+        stc_opts o{};
+        o.light_rows = cand;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && st == STC_OK; ++rep) {
+            stc_csr C{};
+            if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = STC_ERR_CUDA;
+            if (st == STC_OK) st = stc_spgemm_impl(h, alg, A, B, &C, &o, s);
+            if (st == STC_OK && rep == 1 && cudaEventRecord(e1, s) != cudaSuccess) st = STC_ERR_CUDA;
+            stc_free_bytes(h, C.rowptr, s);
+            stc_free_bytes(h, C.col, s);
+            stc_free_bytes(h, C.val, s);
+            if (st == STC_OK && rep == 1 &&
+                (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = STC_ERR_CUDA;
+        }
+        if (st != STC_OK) break;
+        times.push_back(ms);
+        if (times.size() == 1 || ms < best_ms) {
+            best_ms = ms;
+            best = cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != STC_OK) return st;
+    const int c = stc_log2_ceil(B->ncols > 0 ? B->ncols : 1);
+    if (c < 40) h->tune_light[alg][c] = static_cast<signed char>(best);
+    if (best_out) *best_out = best;
+    if (ncand_out) *ncand_out = int32_t(times.size());
+    for (size_t i = 0; i < times.size() && i < 8; ++i) {
+        if (cand_out) cand_out[i] = cands[i];
+        if (ms_out) ms_out[i] = times[i];
+    }
+    return STC_OK;
 }
 
 stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,

@@ -79,8 +79,38 @@ extern "C" stc_status stc_create(stc_handle** out, stc_alloc_fn alloc, stc_free_
     return STC_OK;
 }
 
+stc_status stc_fork(stc_handle* h, stc_stream s, cudaStream_t* aux) {
+    if (!h->aux) {
+        STC_CUDA_TRY(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        STC_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        STC_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
+    STC_CUDA_TRY(cudaEventRecord(h->ev_fork, s));
+    STC_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    *aux = h->aux;
+    return STC_OK;
+}
+
+stc_status stc_join(stc_handle* h, stc_stream s) {
+    STC_CUDA_TRY(cudaEventRecord(h->ev_join, h->aux));
+    STC_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    return STC_OK;
+}
+
+int stc_log2_ceil(int64_t x) {
+    int l = 0;
+    while (l < 62 && (int64_t(1) << l) < x) ++l;
+    return l;
+}
+
 extern "C" void stc_destroy(stc_handle* h) {
     if (!h) return;
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->d_flags) cudaFree(h->d_flags);
@@ -366,6 +396,7 @@ extern "C" stc_status stc_contract_spgemm(stc_handle* h, stc_algebra alg, const 
     if (opts) {
         for (int r : opts->reserved)
             if (r != 0) return STC_ERR_INVALID_ARG;
+        if (opts->light_rows < -1 || opts->light_rows > 30) return STC_ERR_INVALID_ARG;
         int w = opts->window_cols;
         if (w != 0 && (w < 1024 || (w & (w - 1)) != 0)) return STC_ERR_INVALID_ARG;
     }
@@ -390,6 +421,7 @@ extern "C" stc_status stc_contract_spgemm_batched(stc_handle* h, stc_algebra alg
     if (opts)
         for (int r : opts->reserved)
             if (r != 0) return STC_ERR_INVALID_ARG;
+        if (opts->light_rows < -1 || opts->light_rows > 30) return STC_ERR_INVALID_ARG;
     return stc_spgemm_batched_impl(h, alg, nbatch, A, B, C, opts, stream);
 }
 
@@ -448,6 +480,80 @@ extern "C" stc_status stc_mfbc_sssp(stc_handle* h, const stc_csr* G, const int32
     return stc_mfbc_sssp_impl(h, G, sources, nsources, d_out, sigma_out, rounds_out, stream);
 }
 
+extern "C" stc_status stc_autotune_spgemm(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
+                                          int32_t* best_out, int32_t* cand_out, float* ms_out, int32_t* ncand_out,
+                                          stc_stream stream) {
+    if (!h) return STC_ERR_INVALID_ARG;
+    if (!alg_valid(alg)) return STC_ERR_ALGEBRA;
+    stc_status st = stc_check_csr_host(A);
+    if (st != STC_OK) return st;
+    if ((st = stc_check_csr_host(B)) != STC_OK) return st;
+    if (A->ncols != B->nrows) return STC_ERR_SHAPE;
+    return stc_autotune_impl(h, alg, A, B, best_out, cand_out, ms_out, ncand_out, stream);
+}
+
+// Tuning files: "stc-tune 1 <SM count> <device name, blanks as '_'>" then lines
+// "<algebra> <ceil(log2 columns)> <light-row threshold>".
+static void device_tag(int device, char* name, size_t n) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        snprintf(name, n, "unknown");
+        return;
+    }
+    snprintf(name, n, "%s", prop.name);
+    for (char* c = name; *c; ++c)
+        if (*c == ' ' || *c == '\t') *c = '_';
+}
+
+extern "C" stc_status stc_tune_save(const stc_handle* h, const char* path) {
+    if (!h || !path) return STC_ERR_INVALID_ARG;
+    char name[256];
+    device_tag(h->device, name, sizeof(name));
+    FILE* f = fopen(path, "w");
+    if (!f) return STC_ERR_INVALID_ARG;
+    fprintf(f, "stc-tune 1 %d %s\n", h->num_sms, name);
+    for (int a = 0; a < 6; ++a)
+        for (int c = 0; c < 40; ++c)
+            if (h->tune_light[a][c] != -128) fprintf(f, "%d %d %d\n", a, c, int(h->tune_light[a][c]));
+    const bool ok = fclose(f) == 0;
+    return ok ? STC_OK : STC_ERR_INVALID_ARG;
+}
+
+extern "C" stc_status stc_tune_load(stc_handle* h, const char* path) {
+    if (!h || !path) return STC_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "r");
+    if (!f) return STC_ERR_INVALID_ARG;
+    char magic[32], dev[256], name[256];
+    int version = 0, sms = 0;
+    if (fscanf(f, "%31s %d %d %255s", magic, &version, &sms, dev) != 4 || strcmp(magic, "stc-tune") != 0 ||
+        version != 1) {
+        fclose(f);
+        return STC_ERR_INVALID_ARG;
+    }
+    device_tag(h->device, name, sizeof(name));
+    if (sms != h->num_sms || strcmp(dev, name) != 0) {
+        fclose(f);
+        return STC_ERR_INVALID_ARG;
+    }
+    signed char t[6][40];
+    memcpy(t, h->tune_light, sizeof(t));
+    int a, c, v;
+    int n;
+    while ((n = fscanf(f, "%d %d %d", &a, &c, &v)) == 3) {
+        if (a < 0 || a >= 6 || c < 0 || c >= 40 || v < -1 || v == 0 || v > 30) {
+            fclose(f);
+            return STC_ERR_INVALID_ARG;
+        }
+        t[a][c] = static_cast<signed char>(v);
+    }
+    const bool clean = n == EOF;
+    fclose(f);
+    if (!clean) return STC_ERR_INVALID_ARG;
+    memcpy(h->tune_light, t, sizeof(t));
+    return STC_OK;
+}
+
 extern "C" stc_status stc_set_round_driver(stc_handle* h, int32_t driver) {
     if (!h || driver < 0 || driver > 1) return STC_ERR_INVALID_ARG;
     h->round_driver = driver;
@@ -476,5 +582,6 @@ extern "C" stc_status stc_contract_spgemm_learned(stc_handle* h, stc_algebra alg
     if (opts)
         for (int r : opts->reserved)
             if (r != 0) return STC_ERR_INVALID_ARG;
+        if (opts->light_rows < -1 || opts->light_rows > 30) return STC_ERR_INVALID_ARG;
     return stc_spgemm_learned_impl(h, alg, A, B, C, weights, margin, stats, opts, stream);
 }

@@ -25,7 +25,23 @@ struct stc_handle {
     int nphases = 0;               // phases recorded by the last timed call
     int64_t launches = 0;          // kernels launched by this handle
     int round_driver = 1;          // multi-round loops: 0 host-driven, 1 CUDA graph
+    cudaStream_t aux = nullptr;    // second stream for concurrent launches (created on first use)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // tuned light-row threshold per (algebra, ceil(log2 output columns)): -128 unknown,
+    // -1 no light launch, L > 0 rows with ub < 2^L
+    signed char tune_light[6][40];
+    stc_handle() {
+        for (auto& row : tune_light)
+            for (auto& x : row) x = -128;
+    }
 };
+
+// The auxiliary stream; run work on it between stc_fork and stc_join (stream order
+// of `s` is kept: the auxiliary work starts after what is queued on `s` and `s`
+// resumes after it).
+stc_status stc_fork(stc_handle* h, stc_stream s, cudaStream_t* aux);
+stc_status stc_join(stc_handle* h, stc_stream s);
+int stc_log2_ceil(int64_t x);
 
 // Record phase boundary `idx` (0 = start of the call) when timing is enabled.
 void stc_mark(stc_handle* h, stc_stream s, int idx);
@@ -187,6 +203,8 @@ stc_status stc_mlp_grad_impl(stc_handle* h, const float* w, const float* feat, c
                              const int32_t* idx, int64_t n, float scale, float* grad, float* loss, stc_stream s);
 stc_status stc_mlp_adam_impl(stc_handle* h, float* w, float* m, float* v, float* grad, int64_t step, float lr,
                              stc_stream s);
+stc_status stc_autotune_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, int32_t* best_out,
+                             int32_t* cand_out, float* ms_out, int32_t* ncand_out, stc_stream s);
 stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
                                    const float* weights, float margin, stc_learned_stats* stats,
                                    const stc_opts* opts, stc_stream s);

@@ -95,3 +95,19 @@ def test_config_4096_pairs_sampled(H):
     pick = set(rng.choice(4096, 36, replace=False).tolist()) | set(np.argsort(sizes)[-4:].tolist())
     for b in sorted(pick):
         check_pair(O.PT_F32, As[b], Bs[b], Cs[b])
+
+
+@pytest.mark.parametrize("light", [7, 10])
+def test_batched_light_row_launch(H, light):
+    """Light rows of the whole batch in their own launch: same result as one call
+    per pair without it."""
+    sizes, As, Bs = W.powerlaw_batch(30, 64, 4096, 2.1, 4, 64, seed=7)
+    for m in As + Bs:
+        m.val = (np.abs(m.val) * 1000).astype(np.int32)
+    dA = [to_dev(a) for a in As]
+    dB = [to_dev(b) for b in Bs]
+    Cs = H.spgemm_batched(O.MP_I32, dA, dB, light_rows=light)
+    for a, b, c in zip(dA, dB, Cs):
+        ref = H.spgemm(O.MP_I32, a, b, light_rows=-1)
+        for x, y in zip(c.to_host(), ref.to_host()):
+            assert np.array_equal(x, y)

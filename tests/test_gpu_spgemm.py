@@ -41,8 +41,8 @@ def vals(alg, nnz, seed, operand):
     return W.multpath_values(nnz, 20, 5, seed)
 
 
-def check(H, alg, A, B, rows=None, window_cols=0):
-    C = H.spgemm(alg, to_dev(A), to_dev(B), window_cols=window_cols)
+def check(H, alg, A, B, rows=None, window_cols=0, light_rows=0):
+    C = H.spgemm(alg, to_dev(A), to_dev(B), window_cols=window_cols, light_rows=light_rows)
     torch.cuda.synchronize()
     H.check_device_status()
     rp, col, val = C.to_host()
@@ -105,6 +105,51 @@ def test_rmat14_square(H, alg):
     A.val = vals(alg, A.nnz, 9, "A")
     B = A.with_val(vals(alg, A.nnz, 10, "B"))
     check(H, alg, A, B)
+
+
+@pytest.mark.parametrize("alg", ALL)
+@pytest.mark.parametrize("light", [8, 10])
+def test_light_row_launch(H, alg, light):
+    """Rows with fewer than 2^light products in their own launch of smaller CTAs
+    on a second stream, beside the wide launch: R-MAT 14, all algebras."""
+    A = W.rmat(14, seed=13)
+    A.val = vals(alg, A.nnz, 19, "A")
+    B = A.with_val(vals(alg, A.nnz, 20, "B"))
+    check(H, alg, A, B, light_rows=light)
+
+
+def test_autotuner_and_tuning_file(H, tmp_path):
+    """The autotuner times its candidates, caches the fastest, and later calls
+    with the default option give the same product; the cache survives a save and
+    load, and a file for another device is refused."""
+    import paper_1512_00066_b300 as stc
+    A = W.rmat(13, seed=21)
+    A.val = W.weights_unit01(A.nnz, 2).astype(np.float32)
+    dA = to_dev(A)
+    res = H.autotune_spgemm(O.PT_F32, dA, dA)
+    assert res["best"] in res["candidates"] and -1 in res["candidates"] and len(res["candidates"]) >= 2
+    assert all(t > 0 for t in res["candidates"].values())
+    assert res["candidates"][res["best"]] == min(res["candidates"].values())
+    C = H.spgemm(O.PT_F32, dA, dA)
+    R = H.spgemm(O.PT_F32, dA, dA, light_rows=-1)
+    assert np.array_equal(C.rowptr.cpu().numpy(), R.rowptr.cpu().numpy())
+    assert np.array_equal(C.col.cpu().numpy(), R.col.cpu().numpy())
+    assert np.allclose(C.val.cpu().numpy(), R.val.cpu().numpy(), rtol=1e-5)
+    f = tmp_path / "tune.txt"
+    H.tune_save(f)
+    lines = f.read_text().splitlines()
+    assert lines[0].startswith("stc-tune 1 ") and any(l.split()[:2] == [str(O.PT_F32), "13"] for l in lines[1:])
+    H2 = stc.Handle()
+    H2.tune_load(f)
+    H2.tune_save(tmp_path / "tune2.txt")
+    assert (tmp_path / "tune2.txt").read_text() == f.read_text()
+    bad = tmp_path / "other.txt"
+    bad.write_text("stc-tune 1 3 Some_Other_GPU\n1 13 8\n")
+    with pytest.raises(stc.StcError):
+        H2.tune_load(bad)
+    bad.write_text(lines[0] + "\n1 13 0\n")
+    with pytest.raises(stc.StcError):
+        H2.tune_load(bad)
 
 
 def test_rmat14_plus_times_unit_weights_relative(H):
