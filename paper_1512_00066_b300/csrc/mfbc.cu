@@ -122,6 +122,16 @@ __device__ __forceinline__ void mf_item_edges(const MfGraph& g, int2 it, int64_t
     e1 = min(hi, e0 + MF_ITEM_EDGES);
 }
 
+// Edges of an item are taken MF_UNR at a time: the columns, lengths and the
+// targets' source slices are all loaded before any compare or atomic, so one
+// group costs one round trip to L2 instead of one per edge.
+constexpr int MF_UNR = 4;
+
+// List v as touched in round r once (stamp read first: most targets are listed).
+__device__ __forceinline__ void mf_touch(int* stamp, int32_t* touched, int* count, int32_t v, int r) {
+    if (stamp[v] != r && atomicExch(&stamp[v], r) != r) touched[atomicAdd(count, 1)] = v;
+}
+
 // Phase A of a round: dn[v][s] = min(dn[v][s], d[u][s] + w) over frontier edges
 // with pending multiplicity; every target is listed once as touched.
 __global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st) {
@@ -138,16 +148,28 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st) {
         const bool act = s < S && st.dl[int64_t(u) * S + s] > 0.0;
         const int du = act ? st.d[int64_t(u) * S + s] : 0;
         if (!__syncthreads_or(act)) continue;
-        for (int64_t p = e0; p < e1; ++p) {
-            const int32_t v = g.col[p];
-            if ((uint64_t)v >= (uint64_t)g.n) continue;
-            if (act) {
-                const int cand = du + edge_len(g, p);
-                int* dst = &st.dn[int64_t(v) * S + s];
-                if (cand < *dst) atomicMin(dst, cand);  // most candidates cannot improve
+        for (int64_t p0 = e0; p0 < e1; p0 += MF_UNR) {
+            int32_t v[MF_UNR];
+            int w[MF_UNR], cur[MF_UNR];
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) {
+                const int64_t p = p0 + k;
+                v[k] = -1;
+                if (p < e1) {
+                    const int32_t x = g.col[p];
+                    if ((uint64_t)x < (uint64_t)g.n) v[k] = x;
+                    w[k] = edge_len(g, p);
+                }
             }
-            if (s == 0 && atomicExch(&st.stamp[v], r) != r)
-                st.list[1][atomicAdd(&st.cnt[MF_C_TOUCHED], 1)] = v;
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) cur[k] = (act && v[k] >= 0) ? st.dn[int64_t(v[k]) * S + s] : 0;
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k)
+                if (act && v[k] >= 0 && du + w[k] < cur[k]) atomicMin(&st.dn[int64_t(v[k]) * S + s], du + w[k]);
+            // thread k lists target k
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k)
+                if (s == k && v[k] >= 0) mf_touch(st.stamp, st.list[1], &st.cnt[MF_C_TOUCHED], v[k], r);
         }
     }
 }
@@ -169,11 +191,24 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_add(MfGraph g, MfState st) {
         const int du = act ? st.d[int64_t(u) * S + s] : 0;
         if (!__syncthreads_or(act)) continue;
         if (!act) continue;
-        for (int64_t p = e0; p < e1; ++p) {
-            const int32_t v = g.col[p];
-            if ((uint64_t)v >= (uint64_t)g.n) continue;
-            const int64_t i = int64_t(v) * S + s;
-            if (du + edge_len(g, p) == st.dn[i]) atomicAdd(&st.dln[i], m);
+        for (int64_t p0 = e0; p0 < e1; p0 += MF_UNR) {
+            int32_t v[MF_UNR];
+            int w[MF_UNR], cur[MF_UNR];
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) {
+                const int64_t p = p0 + k;
+                v[k] = -1;
+                if (p < e1) {
+                    const int32_t x = g.col[p];
+                    if ((uint64_t)x < (uint64_t)g.n) v[k] = x;
+                    w[k] = edge_len(g, p);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) cur[k] = v[k] >= 0 ? st.dn[int64_t(v[k]) * S + s] : 0;
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k)
+                if (v[k] >= 0 && du + w[k] == cur[k]) atomicAdd(&st.dln[int64_t(v[k]) * S + s], m);
         }
     }
 }
@@ -288,11 +323,11 @@ __global__ void __launch_bounds__(MF_NT) k_mf_back(MfGraph gt, MfState st) {
     const int S = st.S;
     const int s = threadIdx.x;
     const int r = st.cnt[MF_C_BROUND];
-    const int cur = r & 1;
-    const int nR = st.cnt[MF_C_READY + cur];
-    const int32_t* __restrict__ ready = mf_pick(st.list, cur);
-    int32_t* __restrict__ next = mf_pick(st.list, cur ^ 1);
-    int* nnext = &st.cnt[MF_C_READY + (cur ^ 1)];
+    const int cur_l = r & 1;
+    const int nR = st.cnt[MF_C_READY + cur_l];
+    const int32_t* __restrict__ ready = mf_pick(st.list, cur_l);
+    int32_t* __restrict__ next = mf_pick(st.list, cur_l ^ 1);
+    int* nnext = &st.cnt[MF_C_READY + (cur_l ^ 1)];
     const int stamp = r + (1 << 30);  // disjoint from the forward rounds' stamps
     for (int b = blockIdx.x; b < nR; b += gridDim.x) {
         const int32_t w = ready[b];
@@ -310,15 +345,30 @@ __global__ void __launch_bounds__(MF_NT) k_mf_back(MfGraph gt, MfState st) {
         int64_t lo, hi;
         row_range(gt.ptr, w, gt.nnz, lo, hi);
         if (!go) continue;
-        for (int64_t p = lo; p < hi; ++p) {
-            const int32_t v = gt.col[p];
-            if ((uint64_t)v >= (uint64_t)gt.n) continue;
-            const int64_t iv = int64_t(v) * S + s;
-            if (st.d[iv] + edge_len(gt, p) == dw) {
-                atomicAdd(&st.dl[iv], st.sig[iv] * coef);
-                // the source whose count reaches zero lists v (once per round)
-                if (atomicSub(&st.dn[iv], 1) == 1 && atomicExch(&st.stamp[v], stamp) != stamp)
-                    next[atomicAdd(nnext, 1)] = v;
+        for (int64_t p0 = lo; p0 < hi; p0 += MF_UNR) {
+            int32_t v[MF_UNR];
+            int len[MF_UNR], dv[MF_UNR];
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) {
+                const int64_t p = p0 + k;
+                v[k] = -1;
+                if (p < hi) {
+                    const int32_t x = gt.col[p];
+                    if ((uint64_t)x < (uint64_t)gt.n) v[k] = x;
+                    len[k] = edge_len(gt, p);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) dv[k] = v[k] >= 0 ? st.d[int64_t(v[k]) * S + s] : 0;
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) {
+                if (v[k] >= 0 && dv[k] + len[k] == dw) {
+                    const int64_t iv = int64_t(v[k]) * S + s;
+                    atomicAdd(&st.dl[iv], st.sig[iv] * coef);
+                    // the source whose count reaches zero lists v (once per round)
+                    if (atomicSub(&st.dn[iv], 1) == 1 && atomicExch(&st.stamp[v[k]], stamp) != stamp)
+                        next[atomicAdd(nnext, 1)] = v[k];
+                }
             }
         }
     }
