@@ -410,6 +410,17 @@ STC_API stc_status stc_tune_save(const stc_handle* h, const char* path);
 STC_API stc_status stc_tune_load(stc_handle* h, const char* path);
 
 /*
+ * Failure-detection self test (no counterpart in the paper).  Runs the bounded
+ * grid barrier of the persistent solvers in a cooperative launch of two blocks
+ * that expects 2 + missing blocks (missing = 0 or 1).  With missing = 0 every
+ * block passes and the call returns STC_OK; with missing = 1 no block can pass,
+ * every block gives up after spin_limit polls of about 0.5 us (1 .. 2^24) and the
+ * call returns STC_ERR_TIMEOUT.  Either way nothing hangs and the handle stays
+ * usable.  Synchronises `stream`.
+ */
+STC_API stc_status stc_selftest_barrier(stc_handle* h, int32_t missing, int32_t spin_limit, stc_stream stream);
+
+/*
  * Instrumentation (no counterpart in the paper, which reports only the share of
  * time spent in local kernels).
  *

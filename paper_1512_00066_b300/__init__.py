@@ -117,6 +117,8 @@ def lib():
             L.stc_autotune_spgemm.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, p, p, p,
                                               p]
             L.stc_autotune_spgemm.restype = ctypes.c_int
+            L.stc_selftest_barrier.argtypes = [p, i32, i32, p]
+            L.stc_selftest_barrier.restype = ctypes.c_int
             L.stc_tune_save.argtypes = [p, ctypes.c_char_p]
             L.stc_tune_save.restype = ctypes.c_int
             L.stc_tune_load.argtypes = [p, ctypes.c_char_p]
@@ -454,6 +456,11 @@ class Handle:
                                        ms, ctypes.byref(n), _stream_ptr(stream))
         _check(st, "stc_autotune_spgemm")
         return {"best": int(best.value), "candidates": {int(cand[i]): float(ms[i]) for i in range(n.value)}}
+
+    def selftest_barrier(self, missing: int, spin_limit: int = 4096, stream=None) -> int:
+        """Status of the bounded grid barrier with `missing` blocks that never arrive
+        (0: passes; 1: gives up after spin_limit polls with STC_ERR_TIMEOUT)."""
+        return int(lib().stc_selftest_barrier(self._h, int(missing), int(spin_limit), _stream_ptr(stream)))
 
     def tune_save(self, path: str):
         _check(lib().stc_tune_save(self._h, str(path).encode()), "stc_tune_save")

@@ -109,23 +109,26 @@ __global__ void __launch_bounds__(BF_NT) k_bf_round(BfArgs a, typename BfT<ALG>:
     relax_round<ALG>(a, dist, r, a.frontier[r & 1], ncur, a.frontier[(r + 1) & 1], &a.cnt[(r + 1) % 3]);
 }
 
-// Grid-wide barrier with a bounded spin.  Returns false (and raises
-// STC_FLAG_TIMEOUT) if the other blocks did not arrive in time.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* flags, int* s_ok) {
+// Grid-wide barrier of `expected` blocks (gridDim.x in the solvers) with a
+// bounded spin: after spin_limit polls of ~0.5 us it gives up, raises
+// STC_FLAG_TIMEOUT and returns false, so a block that never arrives ends the
+// kernel with a status instead of a hang.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned expected, long long spin_limit, int* flags,
+                             int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         unsigned g0 = *(volatile unsigned*)gen;
         __threadfence();
         unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == expected - 1) {
             *(volatile unsigned*)count = 0u;
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
             long long spins = 0;
             while (*(volatile unsigned*)gen == g0) {
-                if (++spins > BARRIER_SPIN_LIMIT) {
+                if (++spins > spin_limit) {
                     ok = 0;
                     atomicOr(flags, STC_FLAG_TIMEOUT);
                     break;
@@ -140,6 +143,16 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int* flags, int* s_
     return *s_ok != 0;
 }
 
+// Failure-detection self test: every block of a cooperative launch enters a grid
+// barrier that expects `expected` blocks; passed counts the blocks that got
+// through.
+__global__ void k_barrier_selftest(unsigned* bar, unsigned expected, long long spin_limit, int* flags,
+                                   int* passed) {
+    __shared__ int s_ok;
+    if (grid_barrier(&bar[0], &bar[1], expected, spin_limit, flags, &s_ok) && threadIdx.x == 0)
+        atomicAdd(passed, 1);
+}
+
 template <int ALG>
 __global__ void __launch_bounds__(BF_NT) k_bf_persistent(BfArgs a, typename BfT<ALG>::D* dist,
                                                          unsigned* bar, int* flags, int* rounds_out) {
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(BF_NT) k_bf_persistent(BfArgs a, typename BfT<
         if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt[(r + 2) % 3] = 0;
         relax_round<ALG>(a, dist, r, a.frontier[r & 1], ncur, a.frontier[(r + 1) & 1],
                          &a.cnt[(r + 1) % 3]);
-        if (!grid_barrier(&bar[0], &bar[1], flags, &s_ok)) return;
+        if (!grid_barrier(&bar[0], &bar[1], gridDim.x, BARRIER_SPIN_LIMIT, flags, &s_ok)) return;
         const int nnext = *(volatile int*)&a.cnt[(r + 1) % 3];
         if (nnext == 0) break;
         ++changed_rounds;
@@ -355,6 +368,34 @@ stc_status stc_bellman_ford_impl(stc_handle* h, int alg, const stc_csr* G, int32
                                  int32_t* rounds, int64_t* relax, int32_t persistent, stc_stream s) {
     if (alg == ALG_MP_I32) return run_bf<ALG_MP_I32>(h, G, source, dist, rounds, relax, persistent, s);
     return run_bf<ALG_MP_F32>(h, G, source, dist, rounds, relax, persistent, s);
+}
+
+extern "C" stc_status stc_selftest_barrier(stc_handle* h, int32_t missing, int32_t spin_limit,
+                                           stc_stream s) {
+    if (!h || missing < 0 || missing > 1 || spin_limit < 1 || spin_limit > (1 << 24)) return STC_ERR_INVALID_ARG;
+    StcScratch sc(h, s);
+    int* ints = sc.get<int>(4);  // [0..1] barrier, [2] passed
+    if (!ints) return STC_ERR_OOM;
+    STC_CUDA_TRY(cudaMemsetAsync(ints, 0, 4 * sizeof(int), s));
+    unsigned* bar = reinterpret_cast<unsigned*>(ints);
+    unsigned expected = 2u + unsigned(missing);
+    long long limit = spin_limit;
+    int* flags = h->d_flags;
+    int* passed = ints + 2;
+    void* args[] = {&bar, &expected, &limit, &flags, &passed};
+    STC_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(2), dim3(32), args, 0, s));
+    stc_count(h);
+    int* st = reinterpret_cast<int*>(&h->h_stage[0]);
+    st[0] = st[1] = 0;
+    STC_CUDA_TRY(cudaMemcpyAsync(&st[0], passed, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaMemcpyAsync(&st[1], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st[1]) {
+        const int f = st[1];
+        STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+        return stc_flags_to_status(f);
+    }
+    return st[0] == 2 ? STC_OK : STC_ERR_CUDA;
 }
 
 // ----------------------------------------------------------------- allocation-free variant

@@ -166,3 +166,17 @@ def test_bellman_ford_drivers_are_distinct(H):
         assert np.array_equal(d.cpu().numpy(), 7 * np.arange(n)) and r == n - 1
     assert launches["graph"] == launches[True] + 1
     assert launches[False] >= launches[True] + n - 2
+
+
+def test_bounded_barrier_times_out_with_a_status(H):
+    """A grid barrier waiting for a block that never arrives gives up after its
+    poll limit: the call returns STC_ERR_TIMEOUT (8), no kernel hangs, and the
+    handle keeps working."""
+    assert H.selftest_barrier(0) == 0
+    assert H.selftest_barrier(1, spin_limit=4096) == 8
+    assert H.selftest_barrier(0) == 0
+    n = 500
+    L = W.csr_from_coo(np.arange(n - 1), np.arange(1, n), n, n)
+    L.val = np.full(n - 1, 3, np.int32)
+    d, r = H.bellman_ford(O.MP_I32, to_dev(L), 0, persistent=True)
+    assert np.array_equal(d.cpu().numpy(), 3 * np.arange(n)) and r == n - 1
