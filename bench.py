@@ -313,10 +313,15 @@ def run_stc(args):
     forms = {}
     if not args.no_forms and wl["scale"] is not None and rank == 0:
         H.set_timing(False)
-        forms["bellman_ford_drivers"] = measure_bf_drivers(stc, H, wl)
-        forms["learned_vs_plain"] = measure_learned(stc, H, wl, dev)
-        forms["batched_vs_per_call"] = measure_batched(stc, H)
-        forms["mfbc"] = measure_mfbc(stc, H)
+        want = set(args.forms.split(","))
+        if "bf" in want:
+            forms["bellman_ford_drivers"] = measure_bf_drivers(stc, H, wl)
+        if "learned" in want:
+            forms["learned_vs_plain"] = measure_learned(stc, H, wl, dev)
+        if "batched" in want:
+            forms["batched_vs_per_call"] = measure_batched(stc, H)
+        if "mfbc" in want:
+            forms["mfbc"] = measure_mfbc(stc, H)
 
     if rank == 0:
         out = {
@@ -582,6 +587,8 @@ def main():
                     help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the light-row autotuning before the warm-up")
+    ap.add_argument("--forms", default="bf,learned,batched,mfbc",
+                    help="comma-separated subset of the comparison forms to run after the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned / batched / centrality measurements")
