@@ -174,6 +174,56 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st) {
     }
 }
 
+// Phases A and B in one pass for unit lengths (g.w == null): every source's
+// frontier in round r is its BFS level r (all sources start together), so every
+// candidate of the round is r + 1 and none can lower a target below a tie; the
+// multiplicity of a candidate that ties the minimum (atomicMin's old value
+// >= r + 1) is added here and k_mf_relax_add is not run.
+__global__ void __launch_bounds__(MF_NT, 8) k_mf_relax_unit(MfGraph g, MfState st) {
+    const int S = st.S;
+    const int s = threadIdx.x;
+    const int r = st.cnt[MF_C_FROUND];
+    const int nitems = st.cnt[MF_C_ITEMS + (r & 1)];
+    const int2* __restrict__ F = mf_pick(st.items, r);
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        const int2 it = F[t];
+        const int32_t u = it.x;
+        int64_t e0, e1;
+        mf_item_edges(g, it, e0, e1);
+        const double m = s < S ? st.dl[int64_t(u) * S + s] : 0.0;
+        const bool act = m > 0.0;
+        const int cand = act ? st.d[int64_t(u) * S + s] + 1 : 0;
+        if (!__syncthreads_or(act)) continue;
+        for (int64_t p0 = e0; p0 < e1; p0 += MF_UNR) {
+            int32_t v[MF_UNR];
+            int cur[MF_UNR];
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) {
+                const int64_t p = p0 + k;
+                v[k] = -1;
+                if (p < e1) {
+                    const int32_t x = g.col[p];
+                    if ((uint64_t)x < (uint64_t)g.n) v[k] = x;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) cur[k] = (act && v[k] >= 0) ? st.dn[int64_t(v[k]) * S + s] : 0;
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) {
+                if (act && v[k] >= 0 && cand <= cur[k]) {
+                    const int64_t i = int64_t(v[k]) * S + s;
+                    const int old = cand < cur[k] ? atomicMin(&st.dn[i], cand) : cand;
+                    if (old >= cand) atomicAdd(&st.dln[i], m);
+                }
+            }
+            // thread k lists target k
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k)
+                if (s == k && v[k] >= 0) mf_touch(st.stamp, st.list[1], &st.cnt[MF_C_TOUCHED], v[k], r);
+        }
+    }
+}
+
 // Phase B: add the pending multiplicity of every candidate that reached the minimum.
 __global__ void __launch_bounds__(MF_NT) k_mf_relax_add(MfGraph g, MfState st) {
     const int S = st.S;
@@ -488,13 +538,17 @@ stc_status mf_run_host(stc_handle* h, const MfBatch& b, stc_stream s) {
     STC_LAUNCH_CHECK();
     stc_count(h, 2);
     for (;;) {
-        k_mf_relax_min<<<rg, MF_NT, 0, s>>>(g, st);
-        k_mf_relax_add<<<rg, MF_NT, 0, s>>>(g, st);
+        if (g.w) {
+            k_mf_relax_min<<<rg, MF_NT, 0, s>>>(g, st);
+            k_mf_relax_add<<<rg, MF_NT, 0, s>>>(g, st);
+        } else {
+            k_mf_relax_unit<<<rg, MF_NT, 0, s>>>(g, st);
+        }
         k_mf_clear_frontier<<<rg, MF_NT, 0, s>>>(st);
         k_mf_update<<<rg, MF_NT, 0, s>>>(g, st);
         k_mf_fwd_check<<<1, 1, 0, s>>>(st, g.n, h->d_flags, 0, none);
         STC_LAUNCH_CHECK();
-        stc_count(h, 5);
+        stc_count(h, g.w ? 5 : 4);
         STC_CUDA_TRY(cudaMemcpyAsync(go, &st.cnt[MF_C_GO], sizeof(int), cudaMemcpyDeviceToHost, s));
         STC_CUDA_TRY(cudaStreamSynchronize(s));
         if (!*go) break;
@@ -519,7 +573,7 @@ stc_status mf_run_host(stc_handle* h, const MfBatch& b, stc_stream s) {
 }
 
 // Graph driver: one CUDA graph per batch shape,
-//   init -> seed -> WHILE{relax_min -> relax_add -> clear -> update -> check}
+//   init -> seed -> WHILE{relax_min -> relax_add (unit lengths: relax_unit) -> clear -> update -> check}
 //        [-> successors -> WHILE{back -> check} -> bc],
 // each WHILE condition set on the device by its check kernel, so a batch is one
 // graph launch with no host round trip.  Kernel arguments (state pointers, S) are
@@ -595,13 +649,16 @@ cudaError_t mf_build_graph(stc_handle* h, MfBatch b, MfGraphExec& x) {
         void* a_gs[] = {&b.g, &b.st};
         void* a_st[] = {&b.st};
         void* a_chk[] = {&b.st, &n, &flags, &in_graph, &hf};
-        MF_G(mf_add_kernel(fb, &k1, nullptr, (const void*)k_mf_relax_min, rg, MF_NT, a_gs));
-        MF_G(mf_add_kernel(fb, &k2, &k1, (const void*)k_mf_relax_add, rg, MF_NT, a_gs));
+        MF_G(mf_add_kernel(fb, &k1, nullptr,
+                           b.g.w ? (const void*)k_mf_relax_min : (const void*)k_mf_relax_unit, rg,
+                           MF_NT, a_gs));
+        k2 = k1;
+        if (b.g.w) MF_G(mf_add_kernel(fb, &k2, &k1, (const void*)k_mf_relax_add, rg, MF_NT, a_gs));
         MF_G(mf_add_kernel(fb, &k3, &k2, (const void*)k_mf_clear_frontier, rg, MF_NT, a_st));
         MF_G(mf_add_kernel(fb, &k4, &k3, (const void*)k_mf_update, rg, MF_NT, a_gs));
         MF_G(mf_add_kernel(fb, &k5, &k4, (const void*)k_mf_fwd_check, 1, 1, a_chk));
     }
-    x.nodes = 7;
+    x.nodes = b.g.w ? 7 : 6;
     if (b.bc) {
         cudaGraphNode_t n_succ, n_bw, n_bc;
         void* a_succ[] = {&b.g, &b.st};
@@ -616,7 +673,7 @@ cudaError_t mf_build_graph(stc_handle* h, MfBatch b, MfGraphExec& x) {
         MF_G(mf_add_kernel(bb, &k2, &k1, (const void*)k_mf_back_check, 1, 1, a_chk));
         void* a_bc[] = {&b.st, &n, &b.src, &b.bc};
         MF_G(mf_add_kernel(x.graph, &n_bc, &n_bw, (const void*)k_mf_bc, grid_for(h, n, 32), MF_NT, a_bc));
-        x.nodes = 11;
+        x.nodes += 4;
     }
     MF_G(cudaGraphInstantiate(&x.exec, x.graph, 0));
     x.S = b.st.S;
