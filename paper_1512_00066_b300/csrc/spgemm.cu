@@ -1707,14 +1707,15 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
 // upper-bound single pass), else (1 + margin) * (2^pred - 1) + 8, clipped to
 // [1, min(ub, ncols)].  Also the scan input of the scratch offsets and the largest
 // capacity.
+// single (may be null): non-zero for rows written by the copy kernel (no scratch).
 __global__ void k_capacity(int64_t NR, const int64_t* __restrict__ ub, const float* __restrict__ pred, float margin,
-                           int64_t ncols, int64_t* __restrict__ cap, int64_t* __restrict__ cap_scan,
-                           int* __restrict__ maxcap) {
+                           int64_t ncols, const int64_t* __restrict__ single, int64_t* __restrict__ cap,
+                           int64_t* __restrict__ cap_scan, int* __restrict__ maxcap) {
     int m = 0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NR; i += int64_t(gridDim.x) * blockDim.x) {
         const int64_t u = ub[i];
         int64_t c = 0;
-        if (u > 0) {
+        if (u > 0 && !(single && single[i] > 0)) {
             const int64_t lim = u < ncols ? u : ncols;
             if (pred) {
                 const float p = fmaxf(exp2f(pred[i]) - 1.0f, 0.0f);
@@ -2222,9 +2223,10 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
     if (NR > 0) {
         int64_t blocks = (NR * 32 + 255) / 256;
         if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, nullptr);
+        // rows with one stored entry: exact size ub into c_ptr + 1, written by the copy kernel
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, c_ptr + 1);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
-        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, nullptr, cursor, rowlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, c_ptr + 1, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h, 3);
         if (weights) {
@@ -2233,7 +2235,7 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
         }
         int64_t cb = (NR + 255) / 256;
         if (cb > int64_t(h->num_sms) * 8) cb = int64_t(h->num_sms) * 8;
-        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred, margin, B->ncols, cap, soff + 1, maxcap);
+        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred, margin, B->ncols, c_ptr + 1, cap, soff + 1, maxcap);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h);
         if ((st = stc_inclusive_scan_i64(h, sc, soff + 1, NR, s)) != STC_OK) return fail(st);
@@ -2307,6 +2309,8 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
     if (NR > 0 && nnz > 0) {
         if ((st = run_compact(h, vbytes, rowlist, nlist, n_rows, soff, cap, c_ptr, nullptr, scol, sval, c_col, c_val,
                               s)) != STC_OK)
+            return fail(st);
+        if ((st = run_copy_any(h, alg, R, rowlist, nlist, bin_count + BIN_COPY, c_ptr, c_col, c_val, s)) != STC_OK)
             return fail(st);
         if (n_ovf > 0) {
             RankOut out{};
@@ -2422,7 +2426,8 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         }
         int64_t cb = (NR + 255) / 256;
         if (cb > int64_t(h->num_sms) * 8) cb = int64_t(h->num_sms) * 8;
-        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred, margin, sl.args[t].ncols, cap_t, soff_t + 1, maxcap);
+        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred, margin, sl.args[t].ncols, nullptr, cap_t, soff_t + 1,
+                                                 maxcap);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h);
         if ((st = stc_inclusive_scan_i64(h, sc, soff_t + 1, NR, s)) != STC_OK) return fail(st);
