@@ -318,6 +318,8 @@ def run_stc(args):
             forms["bellman_ford_drivers"] = measure_bf_drivers(stc, H, wl)
         if "learned" in want:
             forms["learned_vs_plain"] = measure_learned(stc, H, wl, dev)
+        if "masked" in want:
+            forms["masked_vs_plain"] = measure_masked(stc, H, wl)
         if "batched" in want:
             forms["batched_vs_per_call"] = measure_batched(stc, H)
         if "mfbc" in want:
@@ -444,6 +446,24 @@ def measure_learned(stc, H, wl, dev):
         del d32
         torch.cuda.empty_cache()
     return out
+
+
+def measure_masked(stc, H, wl):
+    """Masked product C<A> = A.A (the output structure given: A's own, the
+    triangle-counting shape) against the plain A.A, (+,x) fp64 on the workload's
+    graph."""
+    import torch
+    A = wl["A"]
+    d64 = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, wl["w64"])
+    M = stc.DeviceCsr(A.nrows, A.ncols, d64.rowptr, d64.col, None)
+    nprod = products(A)
+    t_plain = _timed(lambda: H.spgemm(stc.PLUS_TIMES_F64, d64, d64), 3)
+    t_mask = _timed(lambda: H.spgemm_masked(stc.PLUS_TIMES_F64, d64, d64, M), 3)
+    torch.cuda.empty_cache()
+    return {"unit": UNIT, "workload": f"rmat{wl['scale']} (+,x) fp64: C<A> = A.A vs A.A",
+            "products": nprod, "mask_entries": A.nnz,
+            "masked": nprod / t_mask, "plain": nprod / t_plain,
+            "ms": {"masked": 1e3 * t_mask, "plain": 1e3 * t_plain}}
 
 
 def measure_batched(stc, H):
@@ -593,7 +613,7 @@ def main():
                     help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the light-row autotuning before the warm-up")
-    ap.add_argument("--forms", default="bf,learned,batched,mfbc",
+    ap.add_argument("--forms", default="bf,learned,masked,batched,mfbc",
                     help="comma-separated subset of the comparison forms to run after the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",

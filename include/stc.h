@@ -189,6 +189,29 @@ STC_API stc_status stc_contract_spgemm(stc_handle* h, stc_algebra alg, const stc
                                stc_csr* C, const stc_opts* opts, stc_stream stream);
 
 /*
+ * Masked SpGEMM: the contraction with a prescribed output structure (the paper
+ * lists output sparsity in contractions as future work, Section 7).  C has
+ * exactly the structure of M:
+ *   C_ij = (+) over k of f(A_ik, B_kj)   for every stored (i, j) of M,
+ * and the algebra's additive identity where no product reaches (i, j) (0 for
+ * (+,x) and bool, INT_MAX/2 for (min,+) int32, +inf for (min,+) fp32, and
+ * (INT_MAX/2, 0) for the multiplicity monoid).  Products outside M are not
+ * accumulated; rows whose M row is empty are not computed.
+ *
+ * M: CSR with nrows = A->nrows, ncols = B->ncols, sorted unique columns; its val
+ * is ignored (may be NULL).  c_val: device array of M->nnz values of the
+ * algebra's C type, in M's entry order (overwritten); C's row pointers and
+ * columns are M's.  At most 2^18 output columns, and M->nrows times the per-row
+ * rank record (8 B per 32 columns plus 8 B per 1024 columns) within 24 GB
+ * (STC_ERR_INVALID_ARG otherwise).  Synchronises `stream` once (validation and
+ * the longest mask row); the values are complete when the stream reaches them.
+ * Errors: as stc_contract_spgemm, and STC_ERR_SHAPE when M's shape differs.
+ */
+STC_API stc_status stc_contract_spgemm_masked(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
+                                              const stc_csr* M, void* c_val, const stc_opts* opts,
+                                              stc_stream stream);
+
+/*
  * Batched SpGEMM: C_b = A_b (x) B_b for b < nbatch independent pairs (Section
  * 3.3.1: an index shared by all three operands names independent problems), all
  * rows of all pairs handled by the same persistent launches (one row work queue

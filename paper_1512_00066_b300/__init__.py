@@ -117,6 +117,9 @@ def lib():
             L.stc_autotune_spgemm.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, p, p, p,
                                               p]
             L.stc_autotune_spgemm.restype = ctypes.c_int
+            L.stc_contract_spgemm_masked.argtypes = [p, ctypes.c_int, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr),
+                                                     ctypes.POINTER(_Csr), p, p, p]
+            L.stc_contract_spgemm_masked.restype = ctypes.c_int
             L.stc_selftest_barrier.argtypes = [p, i32, i32, p]
             L.stc_selftest_barrier.restype = ctypes.c_int
             L.stc_tune_save.argtypes = [p, ctypes.c_char_p]
@@ -280,6 +283,24 @@ class Handle:
         else:
             val = raw.view(ct)[:nnz]
         return DeviceCsr(int(C.nrows), int(C.ncols), rowptr, col, val)
+
+    def spgemm_masked(self, alg: int, A: DeviceCsr, B: DeviceCsr, M: DeviceCsr, skip_validation: bool = False,
+                      stream=None) -> DeviceCsr:
+        """C<M> = A (x) B with the structure of M (identity where no product lands)."""
+        ct = _DT[alg][2]
+        dev = M.col.device
+        if ct == "dsig":
+            val = torch.empty((M.nnz, DSIG_BYTES), dtype=torch.uint8, device=dev)
+        else:
+            val = torch.empty(M.nnz, dtype=ct, device=dev)
+        m = _Csr(M.nrows, M.ncols, M.nnz, M.rowptr.data_ptr(), M.col.data_ptr() if M.nnz else None, None)
+        opts = _Opts(1 if skip_validation else 0, 0, 0)
+        a, b = A._c(), B._c()
+        st = lib().stc_contract_spgemm_masked(self._h, alg, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m),
+                                              val.data_ptr() if M.nnz else None, ctypes.byref(opts),
+                                              _stream_ptr(stream))
+        _check(st, "stc_contract_spgemm_masked")
+        return DeviceCsr(M.nrows, M.ncols, M.rowptr, M.col, val)
 
     def spgemm_batched(self, alg: int, As, Bs, skip_validation: bool = False, light_rows: int = 0, stream=None):
         """C_b = A_b (x) B_b for every pair, in one batched call (one synchronisation).

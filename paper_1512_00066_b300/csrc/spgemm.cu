@@ -94,6 +94,7 @@ template <> struct Tr<ALG_PT_F32> {
     static __device__ __forceinline__ C out(Acc v) { return v; }
     // the output of an entry with exactly one product (added to an empty accumulator)
     static __device__ __forceinline__ C one(A a, B b) { return __fadd_rn(0.0f, __fmul_rn(a, b)); }
+    static __device__ __forceinline__ C identity() { return 0.0f; }  // of (+)
 };
 template <> struct Tr<ALG_PT_F64> {
     using A = double; using B = double; using C = double; using Acc = double;
@@ -103,6 +104,7 @@ template <> struct Tr<ALG_PT_F64> {
     }
     static __device__ __forceinline__ C out(Acc v) { return v; }
     static __device__ __forceinline__ C one(A a, B b) { return __dadd_rn(0.0, __dmul_rn(a, b)); }
+    static __device__ __forceinline__ C identity() { return 0.0; }
 };
 template <> struct Tr<ALG_MP_I32> {
     using A = int; using B = int; using C = int; using Acc = int;
@@ -114,6 +116,7 @@ template <> struct Tr<ALG_MP_I32> {
     }
     static __device__ __forceinline__ C out(Acc v) { return v; }
     static __device__ __forceinline__ C one(A a, B b) { return a + b; }
+    static __device__ __forceinline__ C identity() { return STC_MIN_PLUS_I32_IDENTITY; }
 };
 template <> struct Tr<ALG_MP_F32> {
     using A = float; using B = float; using C = float; using Acc = unsigned;
@@ -123,6 +126,7 @@ template <> struct Tr<ALG_MP_F32> {
     }
     static __device__ __forceinline__ C out(Acc v) { return ordered_to_f32(v); }
     static __device__ __forceinline__ C one(A a, B b) { return ordered_to_f32(f32_to_ordered(__fadd_rn(a, b))); }
+    static __device__ __forceinline__ C identity() { return __int_as_float(0x7f800000); }  // +inf
 };
 template <> struct Tr<ALG_BOOL> {
     using A = uint8_t; using B = uint8_t; using C = uint8_t; using Acc = unsigned;
@@ -132,6 +136,7 @@ template <> struct Tr<ALG_BOOL> {
     }
     static __device__ __forceinline__ C out(Acc v) { return uint8_t(v != 0u); }
     static __device__ __forceinline__ C one(A a, B b) { return uint8_t(a != 0 && b != 0); }
+    static __device__ __forceinline__ C identity() { return 0; }
 };
 template <> struct Tr<ALG_MULTPATH> {
     using A = int; using B = DSig; using C = DSig; using Acc = int;  // distance part
@@ -1106,7 +1111,10 @@ __global__ void k_batch_bounds(SpgRows R, const int64_t* __restrict__ c_ptr, int
         out[b] = c_ptr[R.row_off[b]];
 }
 
-template <int ALG, int NT, int MINB>
+// MASKED: the rank records describe a given output structure (a mask M): products
+// whose column is not in the row's structure are skipped, entries that no product
+// reaches get the additive identity, and no columns are written (c_col unused).
+template <int ALG, int NT, int MINB, bool MASKED = false>
 __global__ void __launch_bounds__(NT, MINB)
 k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
@@ -1266,6 +1274,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             const int32_t* tab = nwin > 1 ? g.ctab : nullptr;
             auto rank_of = [&](int col) -> int {
                 const uint2 e = wb[col >> 5];
+                if constexpr (MASKED)
+                    if (!((e.x >> (col & 31)) & 1u)) return -1;  // not in the mask
                 return int(e.y) + __popc(e.x & ((1u << (col & 31)) - 1u)) - rb;
             };
             for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
@@ -1290,14 +1300,16 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             }
             for (int r = threadIdx.x; r < rcount; r += NT) {
                 if (fits) {
-                    c_col[o0 + rb + r] = scol[r] + g.col_base;
+                    if constexpr (!MASKED) c_col[o0 + rb + r] = scol[r] + g.col_base;
                     if constexpr (ALG == ALG_MULTPATH) {
                         DSig o;
-                        o.d = vals[r];
+                        o.d = (MASKED && vals[r] == T::empty()) ? STC_MIN_PLUS_I32_IDENTITY : vals[r];
                         o.pad = 0;
                         o.s = sig[r];
                         cval[o0 + rb + r] = o;
                         sig[r] = 0.0;
+                    } else if constexpr (MASKED) {
+                        cval[o0 + rb + r] = vals[r] == T::empty() ? T::identity() : T::out(vals[r]);
                     } else {
                         cval[o0 + rb + r] = T::out(vals[r]);
                     }
@@ -1380,11 +1392,11 @@ struct RankCfg {
     int nt = 0;  // threads per CTA: 256 (small), 512 (light rows), 1024 (wide)
 };
 
-template <int ALG, int NT, int MINB>
+template <int ALG, int NT, int MINB, bool MASKED = false>
 stc_status launch_numeric_rank(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
                                const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
                                int32_t* c_col, void* c_val, int64_t NR, const uint4* rec, const int2* rec_meta, stc_stream s) {
-    auto kern = k_numeric_rank<ALG, NT, MINB>;
+    auto kern = k_numeric_rank<ALG, NT, MINB, MASKED>;
     STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cfg.smem)));
     int per_sm = 0;
     STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, cfg.smem));
@@ -1423,6 +1435,31 @@ stc_status run_numeric_any(stc_handle* h, int alg, const SpgRows& R, int ncell_m
     case ALG_MP_F32: return run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
     case ALG_BOOL: return run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
     case ALG_MULTPATH: return run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
+    default: return STC_ERR_ALGEBRA;
+    }
+}
+
+template <int ALG>
+stc_status run_numeric_masked_alg(stc_handle* h, const SpgRows& R, int ncell_max, const RankCfg& cfg,
+                                  const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
+                                  void* c_val, int64_t NR, const uint4* rec, const int2* rec_meta, stc_stream s) {
+    if (cfg.small)
+        return launch_numeric_rank<ALG, 256, 4, true>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, nullptr,
+                                                      c_val, NR, rec, rec_meta, s);
+    return launch_numeric_rank<ALG, RK_NT, 1, true>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, nullptr,
+                                                    c_val, NR, rec, rec_meta, s);
+}
+
+stc_status run_numeric_masked(stc_handle* h, int alg, const SpgRows& R, int ncell_max, const RankCfg& cfg,
+                              const int32_t* rowlist, const int* nlist, int* counter, const RankOut& out,
+                              void* c_val, int64_t NR, const uint4* rec, const int2* rec_meta, stc_stream s) {
+    switch (alg) {
+    case ALG_PT_F32: return run_numeric_masked_alg<ALG_PT_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_val, NR, rec, rec_meta, s);
+    case ALG_PT_F64: return run_numeric_masked_alg<ALG_PT_F64>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_val, NR, rec, rec_meta, s);
+    case ALG_MP_I32: return run_numeric_masked_alg<ALG_MP_I32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_val, NR, rec, rec_meta, s);
+    case ALG_MP_F32: return run_numeric_masked_alg<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_val, NR, rec, rec_meta, s);
+    case ALG_BOOL: return run_numeric_masked_alg<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_val, NR, rec, rec_meta, s);
+    case ALG_MULTPATH: return run_numeric_masked_alg<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_val, NR, rec, rec_meta, s);
     default: return STC_ERR_ALGEBRA;
     }
 }
@@ -2557,6 +2594,152 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
     C->nnz = nnz;
     return STC_OK;
 }
+// ----------------------------------------------------------------- masked product
+//
+// C<M> = A (x) B with the structure of M given: rows whose mask row is empty are
+// not computed; the others are listed heaviest first by their product count.  The
+// symbolic kernel run on (I, M) -- the identity pattern times the mask -- writes
+// every listed row's rank record from the mask row itself; the numeric kernel in
+// masked form then accumulates the products that land in the mask.
+
+// ubm[i] = 0 for an empty mask row, else max(ub[i], 1) (listed even without
+// products: its entries get the identity); bins counted by ubm.
+__global__ void k_mask_ub(int64_t NR, const int64_t* __restrict__ ub, const int64_t* __restrict__ m_ptr,
+                          int64_t nnzM, int64_t* __restrict__ ubm, int* __restrict__ bin_count) {
+    __shared__ int s_bins[NBINS];
+    for (int t = threadIdx.x; t < NBINS; t += blockDim.x) s_bins[t] = 0;
+    __syncthreads();
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NR; i += int64_t(gridDim.x) * blockDim.x) {
+        int64_t lo, hi;
+        row_range(m_ptr, i, nnzM, lo, hi);
+        const int64_t u = hi > lo ? (ub[i] > 0 ? ub[i] : 1) : 0;
+        ubm[i] = u;
+        atomicAdd(&s_bins[bin_of(u)], 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NBINS; t += blockDim.x)
+        if (s_bins[t]) atomicAdd(&bin_count[t], s_bins[t]);
+}
+
+// The identity pattern: ptr[i] = i, col[i] = i.
+__global__ void k_iota(int64_t n, int64_t* __restrict__ ptr, int32_t* __restrict__ col) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= n; i += int64_t(gridDim.x) * blockDim.x) {
+        ptr[i] = i;
+        if (i < n) col[i] = int32_t(i);
+    }
+}
+
+stc_status spgemm_masked_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, const stc_csr* M,
+                              void* c_val, bool validate, stc_stream s) {
+    const int64_t NR = A->nrows;
+    if (B->ncols > RK_MAX_COLS) return STC_ERR_INVALID_ARG;
+    SpgArgs g = make_args(A, B);
+    const int ncell_max = g.ncell > 0 ? g.ncell : 1;
+    const RankCfg cfg = rank_config(alg, B->ncols, ncell_max);
+    if (!cfg.vcap) return STC_ERR_INVALID_ARG;
+    const size_t rec_bytes = rank_layout(ncell_max, 0, 0, 4, false).winfirst;
+    if (double(NR) * double(rec_bytes) > RK_RECORD_BUDGET) return STC_ERR_INVALID_ARG;
+    StcScratch sc(h, s);
+    stc_mark(h, s, 0);
+    stc_status st;
+    if (validate) {
+        if ((st = stc_validate_csr_async(h, A, s)) != STC_OK) return st;
+        if ((st = stc_validate_csr_async(h, B, s)) != STC_OK) return st;
+        if ((st = stc_validate_csr_async(h, M, s)) != STC_OK) return st;
+    }
+    stc_mark(h, s, 1);
+    if (NR == 0 || M->nnz == 0) return STC_OK;
+    int64_t* ub = sc.get<int64_t>(size_t(NR));
+    int64_t* ubm = sc.get<int64_t>(size_t(NR));
+    int64_t* cnt = sc.get<int64_t>(size_t(NR));
+    int32_t* rowlist = sc.get<int32_t>(size_t(NR));
+    int64_t* iota_ptr = sc.get<int64_t>(size_t(NR) + 1);
+    int32_t* iota_col = sc.get<int32_t>(size_t(NR));
+    int* ints = sc.get<int>(3 * NBINS_ALL + 8);
+    uint4* rec = sc.get<uint4>(size_t(NR) * (rec_bytes / 16));
+    int2* rec_meta = sc.get<int2>(size_t(NR));
+    if (sc.failed) return STC_ERR_OOM;
+    STC_CUDA_TRY(cudaMemsetAsync(ints, 0, sizeof(int) * (3 * NBINS_ALL + 8), s));
+    int* bin_count = ints;
+    int* cursor = ints + NBINS_ALL;
+    int* nlist = ints + 2 * NBINS_ALL;
+    int* counters = ints + 2 * NBINS_ALL + 1;  // [0] symbolic, [1] numeric
+    int* max_nnz = ints + 2 * NBINS_ALL + 4;
+    int* product_bins = ints + 2 * NBINS_ALL + 8;  // unused counts of k_row_ub_b
+    SpgRows R{};
+    R.one = g;
+    R.nb = 1;
+    int64_t blocks = (NR * 32 + 255) / 256;
+    if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+    const unsigned gb = unsigned(h->num_sms * 8);
+    k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, product_bins, nullptr);
+    k_mask_ub<<<gb, 256, 0, s>>>(NR, ub, M->rowptr, M->nnz, ubm, bin_count);
+    k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
+    k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ubm, nullptr, cursor, rowlist);
+    k_iota<<<gb, 256, 0, s>>>(NR, iota_ptr, iota_col);
+    STC_LAUNCH_CHECK();
+    stc_count(h, 5);
+    stc_mark(h, s, 2);
+    // rank records of the mask rows: the symbolic pass over I (x) M
+    SpgArgs gm = make_args(A, B);
+    gm.K = NR;
+    gm.nnzA = NR;
+    gm.a_ptr = iota_ptr;
+    gm.a_col = iota_col;
+    gm.a_val = nullptr;
+    gm.nnzB = M->nnz;
+    gm.b_ptr = M->rowptr;
+    gm.b_col = M->col;
+    gm.b_val = nullptr;
+    SpgRows RM{};
+    RM.one = gm;
+    RM.nb = 1;
+    {
+        const size_t smem = sym_layout(ncell_max).total;
+        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        int per_sm = 0;
+        STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
+        if (per_sm < 1) return STC_ERR_CUDA;
+        int64_t grid = int64_t(per_sm) * h->num_sms;
+        if (grid > NR) grid = NR;
+        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(RM, ncell_max, rowlist, nlist, counters, cnt, max_nnz, rec,
+                                                     rec_meta, cfg.vcap - RK_CELL);
+        STC_LAUNCH_CHECK();
+        stc_count(h);
+    }
+    stc_mark(h, s, 3);
+    // the one synchronisation: validation flags and the longest mask row
+    int* stage = reinterpret_cast<int*>(&h->h_stage[0]);
+    stage[0] = stage[1] = 0;
+    STC_CUDA_TRY(cudaMemcpyAsync(&stage[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaMemcpyAsync(&stage[1], max_nnz, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (stage[0]) {
+        const int f = stage[0];
+        STC_CUDA_TRY(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
+        return stc_flags_to_status(f);
+    }
+    if (stage[1] >= cfg.vcap - RK_CELL) {
+        int32_t* ctab = sc.get<int32_t>(size_t(g.K) * size_t(g.ncell + 1));
+        if (!ctab) return STC_ERR_OOM;
+        R.one.ctab = ctab;
+        int64_t bx = (g.K * (g.ncell + 1) + 255) / 256;
+        if (bx > int64_t(h->num_sms) * 64) bx = int64_t(h->num_sms) * 64;
+        k_cell_offsets<<<dim3(unsigned(bx > 0 ? bx : 1), 1), 256, 0, s>>>(R);
+        STC_LAUNCH_CHECK();
+        stc_count(h);
+    }
+    stc_mark(h, s, 4);
+    RankOut out{};
+    out.ptr = M->rowptr;
+    if ((st = run_numeric_masked(h, alg, R, ncell_max, cfg, rowlist, nlist, counters + 1, out, c_val, NR, rec,
+                                 rec_meta, s)) != STC_OK)
+        return st;
+    stc_mark(h, s, 5);
+    return STC_OK;
+}
+
 // Light-row threshold of a call: the option when set, else the handle's tuned
 // value for this algebra and output width, else no light launch.
 int resolve_light(stc_handle* h, int alg, int64_t ncols_max, const stc_opts* opts) {
@@ -2822,6 +3005,11 @@ stc_status stc_autotune_impl(stc_handle* h, int alg, const stc_csr* A, const stc
         if (ms_out) ms_out[i] = times[i];
     }
     return STC_OK;
+}
+
+stc_status stc_spgemm_masked_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, const stc_csr* M,
+                                  void* c_val, const stc_opts* opts, stc_stream s) {
+    return spgemm_masked_impl(h, alg, A, B, M, c_val, !(opts && opts->skip_validation), s);
 }
 
 stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,

@@ -480,6 +480,27 @@ extern "C" stc_status stc_mfbc_sssp(stc_handle* h, const stc_csr* G, const int32
     return stc_mfbc_sssp_impl(h, G, sources, nsources, d_out, sigma_out, rounds_out, stream);
 }
 
+extern "C" stc_status stc_contract_spgemm_masked(stc_handle* h, stc_algebra alg, const stc_csr* A,
+                                                 const stc_csr* B, const stc_csr* M, void* c_val,
+                                                 const stc_opts* opts, stc_stream stream) {
+    if (!h || !M) return STC_ERR_INVALID_ARG;
+    if (!alg_valid(alg)) return STC_ERR_ALGEBRA;
+    stc_status st = stc_check_csr_host(A);
+    if (st != STC_OK) return st;
+    if ((st = stc_check_csr_host(B)) != STC_OK) return st;
+    stc_csr mstruct = *M;  // the mask's values are not read
+    if (!mstruct.val) mstruct.val = mstruct.col;
+    if ((st = stc_check_csr_host(&mstruct)) != STC_OK) return st;
+    if (A->ncols != B->nrows || M->nrows != A->nrows || M->ncols != B->ncols) return STC_ERR_SHAPE;
+    if (M->nnz > 0 && !c_val) return STC_ERR_INVALID_ARG;
+    if (opts) {
+        for (int r : opts->reserved)
+            if (r != 0) return STC_ERR_INVALID_ARG;
+        if (opts->window_cols != 0 || opts->light_rows < -1 || opts->light_rows > 30) return STC_ERR_INVALID_ARG;
+    }
+    return stc_spgemm_masked_impl(h, alg, A, B, M, c_val, opts, stream);
+}
+
 extern "C" stc_status stc_autotune_spgemm(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
                                           int32_t* best_out, int32_t* cand_out, float* ms_out, int32_t* ncand_out,
                                           stc_stream stream) {

@@ -203,6 +203,8 @@ stc_status stc_mlp_grad_impl(stc_handle* h, const float* w, const float* feat, c
                              const int32_t* idx, int64_t n, float scale, float* grad, float* loss, stc_stream s);
 stc_status stc_mlp_adam_impl(stc_handle* h, float* w, float* m, float* v, float* grad, int64_t step, float lr,
                              stc_stream s);
+stc_status stc_spgemm_masked_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, const stc_csr* M,
+                                  void* c_val, const stc_opts* opts, stc_stream s);
 stc_status stc_autotune_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, int32_t* best_out,
                              int32_t* cand_out, float* ms_out, int32_t* ncand_out, stc_stream s);
 stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,

@@ -302,3 +302,113 @@ def test_rmat20_column_slabs_full_size_sampled(H):
     ptr, rcol, rval, rabs = O.spgemm(O.PT_F32, A, A, rows=rows, want_abs=True)
     assert np.array_equal(col, rcol)
     compare_values(O.PT_F32, val, rval, rabs, where="rmat20 sampled")
+
+
+# ----------------------------------------------------------------- masked product
+
+def masked_expected(alg, A, B, M):
+    """C<M> from the oracle's full product: its entries at M's positions, the
+    additive identity where the product has none."""
+    ptr, col, val, absv = O.spgemm(alg, A, B, want_abs=True)
+    rows = np.repeat(np.arange(A.nrows, dtype=np.int64), np.diff(ptr))
+    keys = rows * B.ncols + col.astype(np.int64)
+    mrows = np.repeat(np.arange(M.nrows, dtype=np.int64), np.diff(M.rowptr))
+    mkeys = mrows * B.ncols + M.col.astype(np.int64)
+    if len(keys):
+        pos = np.minimum(np.searchsorted(keys, mkeys), len(keys) - 1)
+        hit = keys[pos] == mkeys
+    else:
+        pos = np.zeros(len(mkeys), np.int64)
+        hit = np.zeros(len(mkeys), bool)
+    out = np.zeros(len(mkeys), dtype=val.dtype)
+    if alg == O.MULTPATH:
+        out["d"] = O.TROP_I32_ID
+    elif alg == O.MP_I32:
+        out[:] = O.TROP_I32_ID
+    elif alg == O.MP_F32:
+        out[:] = np.inf
+    out[hit] = val[pos[hit]]
+    ab = np.zeros(len(mkeys))
+    if absv is not None:
+        ab[hit] = absv[pos[hit]]
+    return out, ab, hit
+
+
+def mask_from(A, B, keep, extra_per_row, seed, empty_frac=0.1):
+    """Part of the product's structure (fraction `keep`) plus random columns."""
+    rng = np.random.default_rng(seed)
+    ptr, col, _, _ = O.spgemm(O.BOOL, A.with_val(np.ones(A.nnz, np.uint8)), B.with_val(np.ones(B.nnz, np.uint8)))
+    rows = np.repeat(np.arange(A.nrows), np.diff(ptr))
+    sel = rng.random(len(col)) < keep
+    er = rng.integers(0, A.nrows, extra_per_row * A.nrows)
+    ec = rng.integers(0, B.ncols, extra_per_row * A.nrows)
+    r = np.r_[rows[sel], er]
+    c = np.r_[col[sel], ec]
+    drop = rng.random(A.nrows) < empty_frac
+    k = ~drop[r]
+    return W.csr_from_coo(r[k], c[k], A.nrows, B.ncols)
+
+
+def check_masked(H, alg, A, B, M, where=""):
+    C = H.spgemm_masked(alg, to_dev(A), to_dev(B), to_dev(M))
+    torch.cuda.synchronize()
+    H.check_device_status()
+    assert np.array_equal(C.rowptr.cpu().numpy(), M.rowptr) and np.array_equal(C.col.cpu().numpy(), M.col)
+    exp, ab, hit = masked_expected(alg, A, B, M)
+    got = C.val.cpu().numpy()
+    compare_values(alg, got, exp, ab, where=where or f"masked alg {alg}")
+    return hit
+
+
+@pytest.mark.parametrize("alg", ALL)
+def test_masked_all_algebras(H, alg):
+    """A mask holding half of the product's entries, foreign entries (identity) and
+    empty rows, over rows of A that are empty or not."""
+    A = W.random_csr(400, 500, 30, seed=61, empty_frac=0.15)
+    B = W.random_csr(500, 3000, 40, seed=62, empty_frac=0.1)
+    A.val = vals(alg, A.nnz, 63, "A")
+    B.val = vals(alg, B.nnz, 64, "B")
+    M = mask_from(A, B, 0.5, 5, seed=65)
+    hit = check_masked(H, alg, A, B, M)
+    assert hit.any() and not hit.all()
+
+
+@pytest.mark.parametrize("alg", [O.PT_F64, O.MP_I32, O.MULTPATH])
+def test_masked_by_own_structure_rmat14(H, alg):
+    """C<A> = A (x) A masked by A (the triangle-counting shape), R-MAT scale 14."""
+    A = W.rmat(14, seed=31)
+    A.val = vals(alg, A.nnz, 32, "A")
+    B = A.with_val(vals(alg, A.nnz, 33, "B"))
+    M = W.Csr(A.nrows, A.ncols, A.rowptr, A.col, None)
+    check_masked(H, alg, A, B, M)
+
+
+@pytest.mark.parametrize("alg", [O.PT_F32, O.MP_F32, O.BOOL])
+def test_masked_rows_over_several_rank_windows(H, alg):
+    """Mask rows with tens of thousands of entries (several rank windows each)."""
+    A = W.random_csr(120, 300, 300, seed=71, empty_frac=0.05)
+    B = W.random_csr(300, 60000, 400, seed=72)
+    A.val = vals(alg, A.nnz, 73, "A")
+    B.val = vals(alg, B.nnz, 74, "B")
+    M = mask_from(A, B, 0.8, 2000, seed=75, empty_frac=0.05)
+    assert np.diff(M.rowptr).max() > 30000
+    check_masked(H, alg, A, B, M)
+
+
+def test_masked_errors(H):
+    import paper_1512_00066_b300 as stc
+    A = W.random_csr(10, 8, 3, seed=1)
+    A.val = np.ones(A.nnz, np.int32)
+    B = W.random_csr(8, 9, 3, seed=2)
+    B.val = np.ones(B.nnz, np.int32)
+    Mbad = W.random_csr(10, 10, 3, seed=3)  # 10 columns, the product has 9
+    with pytest.raises(stc.StcError) as e:
+        H.spgemm_masked(O.MP_I32, to_dev(A), to_dev(B), to_dev(Mbad))
+    assert e.value.status == 2
+    U = W.Csr(10, 9, np.r_[0, 2, np.full(9, 2)].astype(np.int64), np.array([5, 1], np.int32), None)
+    with pytest.raises(stc.StcError) as e:
+        H.spgemm_masked(O.MP_I32, to_dev(A), to_dev(B), to_dev(U))
+    assert e.value.status == 3
+    E = W.Csr(10, 9, np.zeros(11, np.int64), np.zeros(0, np.int32), None)
+    C = H.spgemm_masked(O.MP_I32, to_dev(A), to_dev(B), to_dev(E))
+    assert C.nnz == 0
