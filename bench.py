@@ -320,6 +320,8 @@ def run_stc(args):
             forms["learned_vs_plain"] = measure_learned(stc, H, wl, dev)
         if "masked" in want:
             forms["masked_vs_plain"] = measure_masked(stc, H, wl)
+        if "apsp" in want:
+            forms["apsp_path_doubling"] = measure_apsp(stc, H)
         if "batched" in want:
             forms["batched_vs_per_call"] = measure_batched(stc, H)
         if "mfbc" in want:
@@ -464,6 +466,33 @@ def measure_masked(stc, H, wl):
             "products": nprod, "mask_entries": A.nnz,
             "masked": nprod / t_mask, "plain": nprod / t_plain,
             "ms": {"masked": 1e3 * t_mask, "plain": 1e3 * t_plain}}
+
+
+def measure_apsp(stc, H, n=2048):
+    """All-pairs shortest paths by path doubling on the paper's APSP workload:
+    a dense graph on n = 2048 vertices with int32 lengths U[1, n^2].  Ops = the
+    (min,+) products of all squarings."""
+    import torch
+    rng = np.random.default_rng(0)
+    rows = np.repeat(np.arange(n), n)
+    cols = np.tile(np.arange(n), n)
+    keep = rows != cols
+    G = W.csr_from_coo(rows[keep], cols[keep], n, n)
+    G.val = rng.integers(1, n * n + 1, G.nnz).astype(np.int32)
+    d = stc.DeviceCsr.from_host(G.nrows, G.ncols, G.rowptr, G.col, G.val)
+    res = {}
+
+    def run():
+        P, sq = H.apsp(d)
+        res["squarings"] = sq
+        res["nnz"] = P.nnz
+        return P
+
+    t = _timed(run, 3)
+    ops = res["squarings"] * n ** 3  # every squaring of a full matrix: n^3 products
+    torch.cuda.empty_cache()
+    return {"unit": UNIT, "workload": f"dense n={n}, int32 lengths U[1, n^2], (min,+) path doubling",
+            "ms": 1e3 * t, "squarings": res["squarings"], "value": ops / t, "closure_nnz": res["nnz"]}
 
 
 def measure_batched(stc, H):
@@ -613,7 +642,7 @@ def main():
                     help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the light-row autotuning before the warm-up")
-    ap.add_argument("--forms", default="bf,learned,masked,batched,mfbc",
+    ap.add_argument("--forms", default="bf,learned,masked,apsp,batched,mfbc",
                     help="comma-separated subset of the comparison forms to run after the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",

@@ -284,6 +284,26 @@ STC_API stc_status stc_bellman_ford(stc_handle* h, stc_algebra alg, const stc_cs
                             int32_t persistent, stc_stream stream);
 
 /*
+ * All-pairs shortest paths by path doubling (Section 4.2): the closure of
+ * I + G over (min,+) int32 by repeated squaring, P <- P (x) P, until a squaring
+ * changes nothing (at most ceil(log2 n) + 1 squarings).  Work is O(n^3 log n)
+ * for a dense graph (Floyd-Warshall's O(n^3) is sequential in n; this is
+ * logarithmic in depth).
+ *
+ * G: square CSR, row u lists the edges u -> v with int32 lengths (val required;
+ * negative lengths allowed).  *P_out receives the distance matrix as a CSR
+ * allocated through the handle (release rowptr, col, val with stc_free): entry
+ * (u, v) is the shortest u -> v distance, stored for every reachable pair
+ * (the diagonal is 0); unreachable pairs are not stored.  Path sums must fit
+ * int32 (no overflow check, as for the semiring itself).  *squarings_out (host,
+ * may be NULL): squarings performed.  Synchronises `stream`.  Errors: CSR and
+ * argument errors, STC_ERR_SHAPE for a non-square G, STC_ERR_NEG_CYCLE when a
+ * diagonal entry ends negative (a negative cycle).
+ */
+STC_API stc_status stc_apsp_path_doubling(stc_handle* h, const stc_csr* G, stc_csr* P_out, int32_t* squarings_out,
+                                          stc_stream stream);
+
+/*
  * Shortest distances and path counts from up to 256 sources at once: Bellman-Ford
  * over the (distance, multiplicity) monoid of STC_MULTPATH_I32_F64 (the geodetic
  * semiring that Section 4.2 names for betweenness centrality), with each vertex

@@ -501,6 +501,15 @@ extern "C" stc_status stc_contract_spgemm_masked(stc_handle* h, stc_algebra alg,
     return stc_spgemm_masked_impl(h, alg, A, B, M, c_val, opts, stream);
 }
 
+extern "C" stc_status stc_apsp_path_doubling(stc_handle* h, const stc_csr* G, stc_csr* P_out,
+                                             int32_t* squarings_out, stc_stream stream) {
+    if (!h || !P_out) return STC_ERR_INVALID_ARG;
+    stc_status st = stc_check_csr_host(G);
+    if (st != STC_OK) return st;
+    if (G->nrows != G->ncols) return STC_ERR_SHAPE;
+    return stc_apsp_impl(h, G, P_out, squarings_out, stream);
+}
+
 extern "C" stc_status stc_autotune_spgemm(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
                                           int32_t* best_out, int32_t* cand_out, float* ms_out, int32_t* ncand_out,
                                           stc_stream stream) {

@@ -186,6 +186,7 @@ stc_status stc_spgemm_batched_impl(stc_handle* h, int alg, int nb, const stc_csr
                                    stc_csr* C, const stc_opts* opts, stc_stream s);
 stc_status stc_spmm_impl(stc_handle* h, int alg, const stc_csr* A, const void* X, int64_t ldx,
                          int32_t ncol, void* Y, int64_t ldy, int32_t accumulate, stc_stream s);
+stc_status stc_apsp_impl(stc_handle* h, const stc_csr* G, stc_csr* P_out, int32_t* squarings_out, stc_stream s);
 stc_status stc_bellman_ford_impl(stc_handle* h, int alg, const stc_csr* G, int32_t source,
                                  void* dist, int32_t* rounds, int64_t* relaxations,
                                  int32_t persistent, stc_stream s);
