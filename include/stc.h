@@ -304,6 +304,25 @@ STC_API stc_status stc_apsp_path_doubling(stc_handle* h, const stc_csr* G, stc_c
                                           stc_stream stream);
 
 /*
+ * All-pairs shortest paths by Tiskin's path doubling (Section 4.2, the paper's
+ * simplified form: the paths of exactly l hops at every step).  Paths carry
+ * (weight, hops); P starts as the edges (w, 1) and, for l = 1, 2, 4, ... < n,
+ * P <- P (+) Pl (x) P where Pl holds the entries of P with exactly l hops and
+ * (+) takes the lexicographic minimum of (weight, hops) -- the paper keeps the
+ * second operand on a weight tie, which depends on the order of reduction; the
+ * hop count breaks the tie here, so the result is the same whatever the order.
+ * The loop ends early when Pl is empty.  Pl shrinks as l grows, so the product
+ * count is well below that of stc_apsp_path_doubling on most graphs.
+ *
+ * G, *P_out and the errors as for stc_apsp_path_doubling (the same distance
+ * matrix, zero diagonal included).  *rounds_out (host, may be NULL): doubling
+ * steps performed; *products_out (host, may be NULL): path products evaluated,
+ * the sum over the steps of the entries (i, k) of Pl times nnz(P_k).
+ */
+STC_API stc_status stc_apsp_tiskin(stc_handle* h, const stc_csr* G, stc_csr* P_out, int32_t* rounds_out,
+                                   int64_t* products_out, stc_stream stream);
+
+/*
  * Shortest distances and path counts from up to 256 sources at once: Bellman-Ford
  * over the (distance, multiplicity) monoid of STC_MULTPATH_I32_F64 (the geodetic
  * semiring that Section 4.2 names for betweenness centrality), with each vertex

@@ -122,6 +122,8 @@ def lib():
             L.stc_contract_spgemm_masked.restype = ctypes.c_int
             L.stc_apsp_path_doubling.argtypes = [p, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, p]
             L.stc_apsp_path_doubling.restype = ctypes.c_int
+            L.stc_apsp_tiskin.argtypes = [p, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, p, p]
+            L.stc_apsp_tiskin.restype = ctypes.c_int
             L.stc_selftest_barrier.argtypes = [p, i32, i32, p]
             L.stc_selftest_barrier.restype = ctypes.c_int
             L.stc_tune_save.argtypes = [p, ctypes.c_char_p]
@@ -299,6 +301,22 @@ class Handle:
         col = self._take(P.col).view(torch.int32)[:nnz]
         val = self._take(P.val).view(torch.int32)[:nnz]
         return DeviceCsr(int(P.nrows), int(P.ncols), rowptr, col, val), int(sq.value)
+
+    def apsp_tiskin(self, G: DeviceCsr, stream=None):
+        """All-pairs shortest distances by Tiskin's path doubling:
+        (P as DeviceCsr, rounds, path products evaluated)."""
+        P = _Csr()
+        rounds = ctypes.c_int32(0)
+        prods = ctypes.c_int64(0)
+        g = G._c()
+        st = lib().stc_apsp_tiskin(self._h, ctypes.byref(g), ctypes.byref(P), ctypes.byref(rounds),
+                                   ctypes.byref(prods), _stream_ptr(stream))
+        _check(st, "stc_apsp_tiskin")
+        nnz = int(P.nnz)
+        rowptr = self._take(P.rowptr).view(torch.int64)[: P.nrows + 1]
+        col = self._take(P.col).view(torch.int32)[:nnz]
+        val = self._take(P.val).view(torch.int32)[:nnz]
+        return DeviceCsr(int(P.nrows), int(P.ncols), rowptr, col, val), int(rounds.value), int(prods.value)
 
     def spgemm_masked(self, alg: int, A: DeviceCsr, B: DeviceCsr, M: DeviceCsr, skip_validation: bool = False,
                       stream=None) -> DeviceCsr:

@@ -138,6 +138,30 @@ template <> struct Tr<ALG_BOOL> {
     static __device__ __forceinline__ C one(A a, B b) { return uint8_t(a != 0 && b != 0); }
     static __device__ __forceinline__ C identity() { return 0; }
 };
+template <> struct Tr<ALG_PATH> {
+    // lexicographic (w, h) as one 64-bit key: w with its sign bit flipped, then h
+    using A = PathVal; using B = PathVal; using C = PathVal; using Acc = unsigned long long;
+    static __device__ __forceinline__ Acc key(int32_t w, int32_t h) {
+        return (Acc(uint32_t(w) ^ 0x80000000u) << 32) | uint32_t(h);
+    }
+    static __device__ __forceinline__ Acc empty() { return ~0ull; }
+    static __device__ __forceinline__ void combine(Acc* acc, int c, A a, B b) {
+        const Acc k = key(a.w + b.w, a.h + b.h);
+        if (k < acc[c]) atomicMin(&acc[c], k);
+    }
+    static __device__ __forceinline__ C out(Acc v) {
+        C o;
+        o.w = int32_t(uint32_t(v >> 32) ^ 0x80000000u);
+        o.h = int32_t(uint32_t(v));
+        return o;
+    }
+    static __device__ __forceinline__ C one(A a, B b) {
+        C o;
+        o.w = a.w + b.w;
+        o.h = a.h + b.h;
+        return o;
+    }
+};
 template <> struct Tr<ALG_MULTPATH> {
     using A = int; using B = DSig; using C = DSig; using Acc = int;  // distance part
     static __device__ __forceinline__ Acc empty() { return INT_MAX; }
@@ -1435,6 +1459,7 @@ stc_status run_numeric_any(stc_handle* h, int alg, const SpgRows& R, int ncell_m
     case ALG_MP_F32: return run_numeric_rank<ALG_MP_F32>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
     case ALG_BOOL: return run_numeric_rank<ALG_BOOL>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
     case ALG_MULTPATH: return run_numeric_rank<ALG_MULTPATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
+    case ALG_PATH: return run_numeric_rank<ALG_PATH>(h, R, ncell_max, cfg, rowlist, nlist, counter, out, c_col, c_val, NR, rec, rec_meta, s);
     default: return STC_ERR_ALGEBRA;
     }
 }
@@ -1474,6 +1499,7 @@ stc_status run_copy_any(stc_handle* h, int alg, const SpgRows& R, const int32_t*
     case ALG_MP_F32: k_copy_rows<ALG_MP_F32><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
     case ALG_BOOL: k_copy_rows<ALG_BOOL><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
     case ALG_MULTPATH: k_copy_rows<ALG_MULTPATH><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
+    case ALG_PATH: k_copy_rows<ALG_PATH><<<grid, 256, 0, s>>>(R, rowlist, nlist, ncopy, c_ptr, c_col, c_val); break;
     default: return STC_ERR_ALGEBRA;
     }
     STC_LAUNCH_CHECK();
@@ -1485,7 +1511,7 @@ stc_status run_copy_any(stc_handle* h, int alg, const SpgRows& R, const int32_t*
 // per SM sharing its shared memory, a value buffer of a few thousand ranks).
 RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max, bool light = false) {
     RankCfg c{};
-    const size_t acc_bytes = alg == ALG_PT_F64 ? 8 : 4;
+    const size_t acc_bytes = (alg == ALG_PT_F64 || alg == ALG_PATH) ? 8 : 4;
     const bool mp = alg == ALG_MULTPATH;
     c.small = !light && ncols_max <= 16384;
     const int nt = light ? 512 : c.small ? 256 : RK_NT;

@@ -48,6 +48,7 @@ size_t stc_val_bytes(int alg, char operand) {
     case ALG_MP_F32: return 4;
     case ALG_BOOL: return 1;
     case ALG_MULTPATH: return operand == 'A' ? 4 : 16;
+    case ALG_PATH: return 8;
     default: return 0;
     }
 }
@@ -508,6 +509,15 @@ extern "C" stc_status stc_apsp_path_doubling(stc_handle* h, const stc_csr* G, st
     if (st != STC_OK) return st;
     if (G->nrows != G->ncols) return STC_ERR_SHAPE;
     return stc_apsp_impl(h, G, P_out, squarings_out, stream);
+}
+
+extern "C" stc_status stc_apsp_tiskin(stc_handle* h, const stc_csr* G, stc_csr* P_out, int32_t* rounds_out,
+                                      int64_t* products_out, stc_stream stream) {
+    if (!h || !P_out) return STC_ERR_INVALID_ARG;
+    stc_status st = stc_check_csr_host(G);
+    if (st != STC_OK) return st;
+    if (G->nrows != G->ncols) return STC_ERR_SHAPE;
+    return stc_apsp_tiskin_impl(h, G, P_out, rounds_out, products_out, stream);
 }
 
 extern "C" stc_status stc_autotune_spgemm(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,

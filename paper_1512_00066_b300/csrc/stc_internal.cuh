@@ -111,6 +111,12 @@ constexpr int ALG_MP_I32 = STC_MIN_PLUS_I32;
 constexpr int ALG_MP_F32 = STC_MIN_PLUS_F32;
 constexpr int ALG_BOOL = STC_OR_AND_BOOL;
 constexpr int ALG_MULTPATH = STC_MULTPATH_I32_F64;
+// Internal algebra (not in stc_algebra): paths (w, h) of Tiskin's path doubling,
+// (+) = lexicographic minimum of (w, h), (x) = (w1 + w2, h1 + h2).
+constexpr int ALG_PATH = 6;
+struct PathVal {
+    int32_t w, h;
+};
 
 size_t stc_val_bytes(int alg, char operand);  // 'A', 'B' or 'C'
 
@@ -186,6 +192,8 @@ stc_status stc_spgemm_batched_impl(stc_handle* h, int alg, int nb, const stc_csr
                                    stc_csr* C, const stc_opts* opts, stc_stream s);
 stc_status stc_spmm_impl(stc_handle* h, int alg, const stc_csr* A, const void* X, int64_t ldx,
                          int32_t ncol, void* Y, int64_t ldy, int32_t accumulate, stc_stream s);
+stc_status stc_apsp_tiskin_impl(stc_handle* h, const stc_csr* G, stc_csr* P_out, int32_t* rounds_out,
+                                int64_t* products_out, stc_stream s);
 stc_status stc_apsp_impl(stc_handle* h, const stc_csr* G, stc_csr* P_out, int32_t* squarings_out, stc_stream s);
 stc_status stc_bellman_ford_impl(stc_handle* h, int alg, const stc_csr* G, int32_t source,
                                  void* dist, int32_t* rounds, int64_t* relaxations,
