@@ -38,8 +38,9 @@ L2_BYTES = 126 * 1024 * 1024
 # Traffic grows with the output (B stays in L2), so a full launch is scaled by its
 # nnz(C): 0.347 GB read + 1.848 GB written for 163,809,247 entries.
 NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = (0.347073e9 + 1.847521e9) / 163809247
-# FP64 peak of the B300 part: 2 FP64 operations (DADD, DMUL or DFMA) per clock per SM
-# (the nominal 1.25 TFLOP/s counting an FMA as two), 148 SMs, 2032 MHz maximum clock.
+# FP64 peak of the B300 part: 2 FP64 instructions (DADD, DMUL or DFMA) per clock per SM
+# (the nominal 1.25 TFLOP/s counting an FMA as two flops), 148 SMs, 2032 MHz maximum
+# clock.  In flops this is the peak of DADD/DMUL code; DFMA code does twice the flops.
 FP64_OPS_PER_CLK_SM = 2
 NUM_SMS = 148
 SM_MAX_MHZ = 2032
@@ -322,6 +323,8 @@ def run_stc(args):
             forms["masked_vs_plain"] = measure_masked(stc, H, wl)
         if "apsp" in want:
             forms["apsp_path_doubling"] = measure_apsp(stc, H)
+        if "spmm" in want:
+            forms["spmm_e1"] = measure_spmm_e1(stc, H)
         if "batched" in want:
             forms["batched_vs_per_call"] = measure_batched(stc, H)
         if "mfbc" in want:
@@ -507,6 +510,30 @@ def measure_apsp(stc, H, n=2048):
                        "value": tk["products"] / t_tk}}
 
 
+def measure_spmm_e1(stc, H, n=16384, k=8192, densities=(0.01, 0.16)):
+    """The paper's SpMM experiment shape: an n x n sparse matrix with independent
+    density d times a dense n x k block (n = 16384, k = 8192), fp64.  Each product
+    is one DFMA instruction (2 flops); the fraction is of the FP64 instruction
+    peak (2 per clock per SM, the same unit as the numeric kernel's roofline)."""
+    import torch
+    X = torch.rand((n, k), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    Y = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    out = {"workload": f"A {n}x{n} sparse (independent density), X {n}x{k} dense, fp64", "unit": "TFLOP/s"}
+    for dens in densities:
+        rng = np.random.default_rng(0)
+        A = W.distinct_columns(rng, rng.binomial(n, dens, size=n), n)
+        A.val = W.weights_unit01(A.nnz, 1)
+        d = stc.DeviceCsr.from_host(n, n, A.rowptr, A.col, A.val)
+        t = _timed(lambda: H.spmm(stc.PLUS_TIMES_F64, d, X, Y), 3)
+        fma_t = A.nnz * k / t / 1e12  # DFMA instructions, in units of 1e12 per second
+        out[f"density_{dens}"] = {"nnz": A.nnz, "ms": 1e3 * t, "tflops": 2.0 * fma_t,
+                                  "fp64_frac": fma_t / FP64_PEAK_TFLOPS}
+        del d
+    del X, Y
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_batched(stc, H):
     """4096 independent (+,x) fp32 pairs: one batched call vs one call per pair."""
     import torch
@@ -654,7 +681,7 @@ def main():
                     help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the light-row autotuning before the warm-up")
-    ap.add_argument("--forms", default="bf,learned,masked,apsp,batched,mfbc",
+    ap.add_argument("--forms", default="bf,learned,masked,apsp,spmm,batched,mfbc",
                     help="comma-separated subset of the comparison forms to run after the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",

@@ -146,6 +146,64 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t nrows, int64_t ncols, int6
     }
 }
 
+// Wide dense operands (ncol >= MM_TILE): warp units (row, tile of MM_TILE columns)
+// taken tile-major, so the warps running at one time share one column tile of X
+// (nrows x MM_TILE values, resident in L2); each lane holds MM_U accumulators
+// (independent chains) and the row's entries are read once per tile.
+constexpr int MM_U = 4;
+constexpr int MM_TILE = 32 * MM_U;
+
+template <int ALG>
+__global__ void __launch_bounds__(256) k_spmm_tiled(int64_t nrows, int64_t ncols, int64_t nnz,
+                                                    const int64_t* __restrict__ ptr,
+                                                    const int32_t* __restrict__ col,
+                                                    const void* __restrict__ aval, const void* __restrict__ x,
+                                                    int64_t ldx, int ncol, void* __restrict__ y, int64_t ldy,
+                                                    int accumulate) {
+    using T = MM<ALG>;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int ntiles = (ncol + MM_TILE - 1) / MM_TILE;
+    const int64_t nunits = nrows * ntiles;
+    const auto* A = static_cast<const typename T::A*>(aval);
+    const auto* X = static_cast<const typename T::X*>(x);
+    auto* Y = static_cast<typename T::Y*>(y);
+    for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < nunits; q += nwarps) {
+        const int64_t tile = q / nrows;
+        const int64_t i = q - tile * nrows;
+        const int c0 = int(tile) * MM_TILE + lane;
+        int64_t lo, hi;
+        row_range(ptr, i, nnz, lo, hi);
+        typename T::Acc acc[MM_U];
+#pragma unroll
+        for (int u = 0; u < MM_U; ++u) acc[u] = T::id();
+        for (int64_t p = lo; p < hi; ++p) {
+            const int32_t k = col[p];
+            if ((uint64_t)k >= (uint64_t)ncols) continue;
+            const typename T::A a = A[p];
+            const auto* xr = X + int64_t(k) * ldx;
+            typename T::X xv[MM_U];
+#pragma unroll
+            for (int u = 0; u < MM_U; ++u) {
+                const int c = c0 + 32 * u;
+                if (c < ncol) xv[u] = xr[c];
+            }
+#pragma unroll
+            for (int u = 0; u < MM_U; ++u)
+                if (c0 + 32 * u < ncol) acc[u] = T::add(acc[u], T::f(a, xv[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < MM_U; ++u) {
+            const int c = c0 + 32 * u;
+            if (c < ncol) {
+                typename T::Acc v = acc[u];
+                if (accumulate) v = T::add(T::load(Y[i * ldy + c]), v);
+                Y[i * ldy + c] = T::out(v);
+            }
+        }
+    }
+}
+
 template <int ALG>
 stc_status launch_mm(stc_handle* h, const stc_csr* A, const void* X, int64_t ldx, int32_t ncol, void* Y,
                      int64_t ldy, int32_t accumulate, stc_stream s) {
@@ -156,6 +214,9 @@ stc_status launch_mm(stc_handle* h, const stc_csr* A, const void* X, int64_t ldx
     if (ncol == 1)
         k_spmv<ALG><<<unsigned(blocks), 256, 0, s>>>(A->nrows, A->ncols, A->nnz, A->rowptr, A->col, A->val,
                                                     X, Y, accumulate);
+    else if (ncol >= MM_TILE)
+        k_spmm_tiled<ALG><<<unsigned(h->num_sms * 16), 256, 0, s>>>(A->nrows, A->ncols, A->nnz, A->rowptr, A->col,
+                                                                     A->val, X, ldx, ncol, Y, ldy, accumulate);
     else
         k_spmm<ALG><<<unsigned(blocks), 256, 0, s>>>(A->nrows, A->ncols, A->nnz, A->rowptr, A->col, A->val,
                                                     X, ldx, ncol, Y, ldy, accumulate);

@@ -63,7 +63,7 @@ def host_out(alg, Y):
 
 
 @pytest.mark.parametrize("alg", ALL)
-@pytest.mark.parametrize("ncol", [1, 5, 37])
+@pytest.mark.parametrize("ncol", [1, 5, 37, 300])
 @pytest.mark.parametrize("accumulate", [False, True])
 def test_spmm_all_algebras(H, alg, ncol, accumulate):
     A = W.random_csr(2049, 1500, 70, seed=11, empty_frac=0.1)
@@ -180,3 +180,22 @@ def test_bounded_barrier_times_out_with_a_status(H):
     L.val = np.full(n - 1, 3, np.int32)
     d, r = H.bellman_ford(O.MP_I32, to_dev(L), 0, persistent=True)
     assert np.array_equal(d.cpu().numpy(), 3 * np.arange(n)) and r == n - 1
+
+
+def test_spmm_paper_e1_shape_sampled(H):
+    """The paper's SpMM shape: a 16384 x 16384 sparse matrix with independent 1%
+    density times a dense 16384 x 8192 block, fp64, at full size: 64 sampled rows
+    element by element against the oracle (run on those rows of A)."""
+    n, k = 16384, 8192
+    rng = np.random.default_rng(101)
+    A = W.distinct_columns(rng, rng.binomial(n, 0.01, size=n), n)
+    A.val = W.weights_unit01(A.nnz, 102)
+    X = np.random.default_rng(103).random((n, k))
+    Y = H.spmm(O.PT_F64, to_dev(A), torch.from_numpy(X).cuda())
+    rows = np.unique(np.r_[np.random.default_rng(104).choice(n, 62, replace=False), 0, n - 1])
+    sub_ptr = np.r_[0, np.cumsum(np.diff(A.rowptr)[rows])].astype(np.int64)
+    sel = np.concatenate([np.arange(A.rowptr[i], A.rowptr[i + 1]) for i in rows])
+    S = W.Csr(len(rows), n, sub_ptr, A.col[sel], A.val[sel])
+    ref = O.spmm(O.PT_F64, S, X, None)
+    got = Y[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref))
