@@ -99,8 +99,19 @@ template <> struct Tr<ALG_PT_F32> {
 template <> struct Tr<ALG_PT_F64> {
     using A = double; using B = double; using C = double; using Acc = double;
     static __device__ __forceinline__ Acc empty() { return 0.0; }
+    // acc[c] = fma(a, b, acc[c]) by compare-and-swap: one FP64 instruction per
+    // product (B300 issues about two FP64 operations per clock per SM) instead of a
+    // multiply plus the add of an atomicAdd; the bits are compared, so a NaN ends
+    // the loop like any other value
     static __device__ __forceinline__ void combine(Acc* acc, int c, A a, B b) {
-        atomicAdd(&acc[c], a * b);
+        unsigned long long* p = reinterpret_cast<unsigned long long*>(&acc[c]);
+        unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(p);
+        for (;;) {
+            const unsigned long long want = __double_as_longlong(__fma_rn(a, b, __longlong_as_double(old)));
+            const unsigned long long seen = atomicCAS(p, old, want);
+            if (seen == old) break;
+            old = seen;
+        }
     }
     static __device__ __forceinline__ C out(Acc v) { return v; }
     static __device__ __forceinline__ C one(A a, B b) { return __dadd_rn(0.0, __dmul_rn(a, b)); }
@@ -705,13 +716,15 @@ __device__ __forceinline__ void walk_tasks_bits(const SpgArgs& g, TaskSmem<NT>& 
     }
 }
 
-// Numeric walk: load the task's columns and B values up front, then for every
-// valid column map it to its rank in the current window with rank_of and apply
-// upd(r, col, b, a) when the rank is in [0, rcount).
-template <int NT, class AT, class BT, class RankF, class UpdF>
+// Numeric walk: load the task's columns and B values up front, map every valid
+// column to its rank in the current window with rank_of, calling on_rank(r, col)
+// for the ranks in [0, rcount), then apply upd(r, col, b, a) to those.  All the
+// rank lookups of a task are issued before its first accumulator update: the
+// compiler cannot move a bitmap read past an atomic on the same shared memory.
+template <int NT, class AT, class BT, class RankF, class OnRankF, class UpdF>
 __device__ __forceinline__ void walk_tasks_rank(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
                                                 const AT* s_aval, const BT* __restrict__ bval, int rcount,
-                                                RankF rank_of, UpdF upd) {
+                                                RankF rank_of, OnRankF on_rank, UpdF upd) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int U = RK_SUB / 32;
     for (int t = wid; t < ntasks;) {
@@ -734,13 +747,15 @@ __device__ __forceinline__ void walk_tasks_rank(const SpgArgs& g, TaskSmem<NT>& 
                 }
             }
         }
+        int rk[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) {
-                const int r = rank_of(col[u]);
-                if ((unsigned)r < (unsigned)rcount) upd(r, col[u], val[u], a);
-            }
+            rk[u] = (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) ? rank_of(col[u]) : -1;
+            if ((unsigned)rk[u] < (unsigned)rcount) on_rank(rk[u], col[u]);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if ((unsigned)rk[u] < (unsigned)rcount) upd(rk[u], col[u], val[u], a);
         int nt = 0;
         if (lane == 0) nt = atomicAdd(&ts.next, 1);
         t = __shfl_sync(0xffffffffu, nt, 0);
@@ -1305,8 +1320,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
                 const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
                 walk_tasks_rank<NT, AT, BT>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
+                                            [&](int r, int col) { scol[r] = col; },
                                             [&](int r, int col, const BT& b, const AT a) {
-                                                scol[r] = col;
                                                 if constexpr (ALG == ALG_MULTPATH) atomicMin(&vals[r], a + b.d);
                                                 else T::combine(vals, r, a, b);
                                             });
@@ -1316,6 +1331,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                 for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
                     const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
                     walk_tasks_rank<NT, AT, BT>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
+                                                [&](int, int) {},
                                                 [&](int r, int, const BT& b, const AT a) {
                                                     if (a + b.d == vals[r]) atomicAdd(&sig[r], b.s);
                                                 });
