@@ -327,6 +327,8 @@ def run_stc(args):
             forms["apsp_path_doubling"] = measure_apsp(stc, H)
         if "spmm" in want:
             forms["spmm_e1"] = measure_spmm_e1(stc, H)
+        if "mlp" in want:
+            forms["mlp_forward"] = measure_mlp(stc, H)
         if "batched" in want:
             forms["batched_vs_per_call"] = measure_batched(stc, H)
         if "mfbc" in want:
@@ -512,6 +514,50 @@ def measure_apsp(stc, H, n=2048):
                        "value": tk["products"] / t_tk}}
 
 
+def measure_mlp(stc, H, scale=20):
+    """Row-size perceptron forward over the features of every row of A.A (R-MAT
+    scale 20, 2^20 rows): the CUDA-core kernel against the tcgen05 one, timed with
+    CUDA events on the launching stream (the 285 MB feature matrix is larger than
+    L2).  Algorithmic bytes per row: 272 of features read, 4 of prediction written."""
+    import torch
+    A = W.rmat(scale, seed=0)
+    dA = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, np.ones(A.nnz, np.float32))
+    feat = H.row_features(dA, dA)
+    n = feat.shape[0]
+    w = stc.mlp_init(seed=1)
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    hbm, peak_kind = peaks()
+    L = stc.lib()
+    s = torch.cuda.current_stream()
+    out = {"workload": f"features of R-MAT {scale} A.A rows ({n} rows x 68 fp32)", "rows": n,
+           "bytes_per_row": 276}
+    for name, fn in (("cuda_cores", L.stc_mlp_forward), ("tcgen05", L.stc_mlp_forward_tc)):
+        def run():
+            st = fn(H._h, w.data_ptr(), feat.data_ptr(), n, y.data_ptr(), s.cuda_stream)
+            if st != 0:
+                raise stc.StcError(st, name)
+        for _ in range(3):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(10):
+            run()
+        e1.record(s)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 10 / 1e3
+        gbs = n * 276 / t / 1e9
+        out[name] = {"us": 1e6 * t, "GB/s": gbs, "hbm_frac": gbs / hbm, "peak_source": peak_kind}
+        out[name]["y"] = y.clone()
+    H.check_device_status()
+    yc, yt = out["cuda_cores"].pop("y"), out["tcgen05"].pop("y")
+    out["max_rel_diff"] = float(((yc - yt).abs() / (1 + yc.abs())).max())
+    out["speedup"] = out["cuda_cores"]["us"] / out["tcgen05"]["us"]
+    del feat, dA, y, yc, yt
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_spmm_e1(stc, H, n=16384, k=8192, densities=(0.01, 0.16)):
     """The paper's SpMM experiment shape: an n x n sparse matrix with independent
     density d times a dense n x k block (n = 16384, k = 8192), fp64.  Each product
@@ -683,7 +729,7 @@ def main():
                     help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the light-row autotuning before the warm-up")
-    ap.add_argument("--forms", default="bf,learned,masked,apsp,spmm,batched,mfbc",
+    ap.add_argument("--forms", default="bf,learned,masked,apsp,spmm,mlp,batched,mfbc",
                     help="comma-separated subset of the comparison forms to run after the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",

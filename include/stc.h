@@ -400,6 +400,16 @@ STC_API stc_status stc_row_features(stc_handle* h, const stc_csr* A, const stc_c
 STC_API stc_status stc_mlp_forward(stc_handle* h, const float* weights, const float* feat, int64_t n, float* y,
                                    stc_stream stream);
 
+/* The same model on the tensor cores (tcgen05 MMAs, fp32 accumulators in tensor
+ * memory): each fp32 activation enters as the sum of two bf16 halves (hi, lo), so
+ * inputs keep about 16 significant bits; results agree with stc_mlp_forward to
+ * about 1e-5 relative.  feat must be 16-byte aligned (STC_ERR_INVALID_ARG
+ * otherwise).  A tensor-core completion that does not arrive within about a
+ * quarter of a second raises STC_FLAG_TIMEOUT (read by stc_check_device_status);
+ * the kernel then releases its tensor memory and returns. */
+STC_API stc_status stc_mlp_forward_tc(stc_handle* h, const float* weights, const float* feat, int64_t n, float* y,
+                                      stc_stream stream);
+
 /* grad (device float [STC_MLP_NUM_WEIGHTS]) += gradient of
  * (1/scale) * sum over the n rows r = idx[0..n) (idx NULL: rows 0..n) of
  * (y_r - target_r)^2; *loss (device float) += that sum of squares. */

@@ -144,6 +144,8 @@ def lib():
             L.stc_row_features.restype = ctypes.c_int
             L.stc_mlp_forward.argtypes = [p, p, p, i64, p, p]
             L.stc_mlp_forward.restype = ctypes.c_int
+            L.stc_mlp_forward_tc.argtypes = [p, p, p, i64, p, p]
+            L.stc_mlp_forward_tc.restype = ctypes.c_int
             L.stc_mlp_grad.argtypes = [p, p, p, p, p, i64, ctypes.c_float, p, p, p]
             L.stc_mlp_grad.restype = ctypes.c_int
             L.stc_mlp_adam.argtypes = [p, p, p, p, p, i64, ctypes.c_float, p]
@@ -434,6 +436,15 @@ class Handle:
         y = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
         _check(lib().stc_mlp_forward(self._h, weights.data_ptr(), feat.data_ptr(), feat.shape[0], y.data_ptr(),
                                      _stream_ptr(stream)), "stc_mlp_forward")
+        return y
+
+    def mlp_forward_tc(self, weights: torch.Tensor, feat: torch.Tensor, stream=None) -> torch.Tensor:
+        """The model on the tensor cores (tcgen05); raises StcError on a device
+        timeout (synchronises the stream)."""
+        y = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        _check(lib().stc_mlp_forward_tc(self._h, weights.data_ptr(), feat.data_ptr(), feat.shape[0], y.data_ptr(),
+                                        _stream_ptr(stream)), "stc_mlp_forward_tc")
+        self.check_device_status(stream)
         return y
 
     def mlp_grad(self, weights, feat, target, idx=None, scale=None, stream=None):

@@ -2310,7 +2310,7 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
         stc_count(h, 3);
         if (weights) {
             if ((st = stc_features_impl(h, sc, A, B, feat, s)) != STC_OK) return fail(st);
-            if ((st = stc_mlp_forward_impl(h, weights, feat, NR, pred, s)) != STC_OK) return fail(st);
+            if ((st = stc_mlp_forward_tc_impl(h, weights, feat, NR, pred, s)) != STC_OK) return fail(st);
         }
         int64_t cb = (NR + 255) / 256;
         if (cb > int64_t(h->num_sms) * 8) cb = int64_t(h->num_sms) * 8;
@@ -2501,7 +2501,7 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         stc_count(h, 3);
         if (weights) {
             if ((st = stc_features_impl(h, sc, A, &sl.view[t], feat, s)) != STC_OK) return fail(st);
-            if ((st = stc_mlp_forward_impl(h, weights, feat, NR, pred, s)) != STC_OK) return fail(st);
+            if ((st = stc_mlp_forward_tc_impl(h, weights, feat, NR, pred, s)) != STC_OK) return fail(st);
         }
         int64_t cb = (NR + 255) / 256;
         if (cb > int64_t(h->num_sms) * 8) cb = int64_t(h->num_sms) * 8;

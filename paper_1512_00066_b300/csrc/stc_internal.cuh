@@ -206,6 +206,8 @@ stc_status stc_mfbc_impl(stc_handle* h, const stc_csr* G, const int32_t* sources
 
 stc_status stc_features_impl(stc_handle* h, StcScratch& sc, const stc_csr* A, const stc_csr* B, float* feat,
                              stc_stream s);
+stc_status stc_mlp_forward_tc_impl(stc_handle* h, const float* w, const float* feat, int64_t n, float* y,
+                                   stc_stream s);
 stc_status stc_mlp_forward_impl(stc_handle* h, const float* w, const float* feat, int64_t n, float* y,
                                 stc_stream s);
 stc_status stc_mlp_grad_impl(stc_handle* h, const float* w, const float* feat, const float* target,

@@ -54,6 +54,35 @@ def test_mlp_forward_and_gradient_match_oracle(H):
     assert abs(float(loss) / n - Lr) <= 1e-4 * Lr
 
 
+@pytest.mark.parametrize("n", [1, 129, 1024, 131072 - 37])
+def test_mlp_forward_tensor_cores(H, n):
+    """tcgen05 forward against the fp64 oracle and the CUDA-core kernel: one row,
+    a tile plus one row, whole tiles, and more tiles than resident CTAs with a
+    ragged last tile."""
+    import paper_1512_00066_b300 as stc
+    w = stc.mlp_init(seed=6)
+    A = W.rmat(17, seed=8)
+    feat = H.row_features(to_dev(A), to_dev(A))[:n]
+    y = H.mlp_forward_tc(w, feat).cpu().numpy()
+    yr = O.mlp_forward(bf16_weights(w), feat[:, :67].double().cpu().numpy())
+    assert np.all(np.abs(y - yr) <= 1e-4 * (1 + np.abs(yr)))
+    yc = H.mlp_forward(w, feat).cpu().numpy()
+    assert np.all(np.abs(y - yc) <= 1e-4 * (1 + np.abs(yc)))
+
+
+def test_mlp_forward_tensor_cores_signed_inputs(H):
+    """Inputs of both signs and wide range (the hi/lo split of negative values),
+    a non-zero padding column (ignored), and an empty batch."""
+    import paper_1512_00066_b300 as stc
+    w = stc.mlp_init(seed=7)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    feat = torch.randn(5000, 68, device="cuda", generator=g) * 8.0
+    y = H.mlp_forward_tc(w, feat).cpu().numpy()
+    yr = O.mlp_forward(bf16_weights(w), feat[:, :67].double().cpu().numpy())
+    assert np.all(np.abs(y - yr) <= 1e-4 * (1 + np.abs(yr)))
+    assert H.mlp_forward_tc(w, feat[:0]).numel() == 0
+
+
 def _pairs(stc, seeds):
     """Training matrices: R-MAT scales 11-14 (seeds >= 1; the evaluation graph is
     seed 0), ER and banded matrices."""
