@@ -9,8 +9,8 @@
 //
 // Precision.  An fp32 activation x is split into hi = bf16(x) and lo = bf16(x - hi)
 // and both halves are multiplied by the (exactly bf16) weights, so x is carried to
-// about 16 significant bits (|x - hi - lo| <= 2^-17 |x|), close to the CUDA-core
-// kernel that multiplies fp32 features by bf16 weights.
+// about 16 significant bits (bf16 rounds to 8 bits, so |x - hi - lo| <= 2^-16 |x|),
+// close to the CUDA-core kernel that multiplies fp32 features by bf16 weights.
 //
 // Shared-memory operand layout (no swizzle, K-major): an operand of R rows and K
 // columns is stored as 8-row x 8-element core matrices of 128 contiguous bytes
