@@ -332,7 +332,7 @@ def run_stc(args):
         if "batched" in want:
             forms["batched_vs_per_call"] = measure_batched(stc, H)
         if "mfbc" in want:
-            forms["mfbc"] = measure_mfbc(stc, H)
+            forms["mfbc"] = measure_mfbc(stc, H, scale=args.mfbc_scale, nsrc=args.mfbc_sources)
 
     if rank == 0:
         out = {
@@ -616,9 +616,10 @@ def measure_bf_drivers(stc, H, wl):
 
 def measure_mfbc(stc, H, scale=22, nsrc=4096, batch=256):
     """Betweenness centrality on R-MAT scale 22 over a 4096-source sample (16
-    batches of 256): GTEPS = sources * edges / time (forward + backward +
-    reduction), with unit and int32 [1, 255] lengths; the host-driven round loop is
-    timed on one batch beside the graph driver."""
+    batches of 256; other sizes through --mfbc-scale / --mfbc-sources):
+    GTEPS = sources * edges / time (forward + backward + reduction), with unit and
+    int32 [1, 255] lengths; the host-driven round loop is timed on one batch beside
+    the graph driver."""
     import torch
     G = W.rmat(scale, seed=0)
     src = W.sample_sources(G, nsrc, seed=0)
@@ -732,6 +733,8 @@ def main():
     ap.add_argument("--forms", default="bf,learned,masked,apsp,spmm,mlp,batched,mfbc",
                     help="comma-separated subset of the comparison forms to run after the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mfbc-scale", type=int, default=22, help="R-MAT scale of the mfbc form")
+    ap.add_argument("--mfbc-sources", type=int, default=4096, help="sampled sources of the mfbc form")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned / batched / centrality measurements")
     args = ap.parse_args()
