@@ -583,6 +583,13 @@ k_numeric(SpgArgs g, const int32_t* __restrict__ rowlist, const int* __restrict_
 //            each window's walk to that window's columns.
 
 constexpr int RK_SUB = 256;                 // B entries per warp task
+// B entries per warp task of the numeric pass's value walk.  A row's products are a
+// few dozen tasks for the CTA's 32 warps, so shorter tasks balance the warps better
+// where products are expensive: fp64 (+,x) (a compare-and-swap of a DFMA each) takes
+// 64, fp32 (+,x) 128, the other algebras RK_SUB (each the fastest measured at R-MAT 18)
+constexpr int value_task_entries(int alg) {
+    return alg == ALG_PT_F64 ? 64 : alg == ALG_PT_F32 ? 128 : RK_SUB;
+}
 constexpr int RK_CELL_SHIFT = 10;           // 1024-column cells (32 bitmap words)
 constexpr int RK_CELL = 1 << RK_CELL_SHIFT;
 constexpr int RK_MAX_COLS = 1 << 18;        // 32 KB bitmap
@@ -604,7 +611,7 @@ struct TaskSmem {
 
 // Segments of the chunk [p0, p0+NT) of A_i: whole B rows, or (ctab != null) the
 // part of each B row inside cells [cl, ch).  Returns the number of warp tasks.
-template <int NT, class AT, bool WITH_VAL>
+template <int NT, class AT, bool WITH_VAL, int SUB = RK_SUB>
 __device__ __forceinline__ int load_tasks(const SpgArgs& g, const int32_t* __restrict__ ctab, int ncell,
                                           int64_t p0, int64_t ahi, int cl, int ch, TaskSmem<NT>& ts,
                                           AT* s_aval) {
@@ -631,7 +638,7 @@ __device__ __forceinline__ int load_tasks(const SpgArgs& g, const int32_t* __res
         }
     }
     int total;
-    int ex = block_exclusive_scan<NT, int>((len + RK_SUB - 1) / RK_SUB, ts.warp, total);
+    int ex = block_exclusive_scan<NT, int>((len + SUB - 1) / SUB, ts.warp, total);
     ts.pre[threadIdx.x] = ex;
     if ((threadIdx.x & 31) == 0) ts.coarse[threadIdx.x >> 5] = ex;
     ts.len[threadIdx.x] = len;
@@ -643,18 +650,18 @@ __device__ __forceinline__ int load_tasks(const SpgArgs& g, const int32_t* __res
 }
 
 // Run op(p, col, j) for every product of the loaded chunk (p: B position,
-// j: index of the A entry in the chunk).  Columns are loaded RK_SUB/32 at a time.
-template <int NT, class Op>
+// j: index of the A entry in the chunk).  Columns are loaded SUB/32 at a time.
+template <int NT, int SUB = RK_SUB, class Op>
 __device__ __forceinline__ void walk_tasks(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks, Op op) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int U = RK_SUB / 32;
+    constexpr int U = SUB / 32;
     for (int t = wid; t < ntasks;) {
         const int j = find_seg_warp<NT>(ts.pre, ts.coarse, t, lane);
-        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
+        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * SUB;
         const int64_t end = ts.lo[j] + ts.len[j];
         // warp-uniform number of 32-entry steps of this task (short B rows stop early)
         const int64_t span = end - start;
-        const int nu = span >= RK_SUB ? U : int((span + 31) >> 5);
+        const int nu = span >= SUB ? U : int((span + 31) >> 5);
         int col[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -679,17 +686,17 @@ __device__ __forceinline__ void walk_tasks(const SpgArgs& g, TaskSmem<NT>& ts, i
 // Symbolic walk: set the bitmap bit of every product's column.  All the task's
 // bitmap reads are issued before its atomics (a read after an atomic would wait
 // for it), and the summary bits are derived from the bitmap afterwards.
-template <int NT>
+template <int NT, int SUB = RK_SUB>
 __device__ __forceinline__ void walk_tasks_bits(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
                                                 uint32_t* bits) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int U = RK_SUB / 32;
+    constexpr int U = SUB / 32;
     for (int t = wid; t < ntasks;) {
         const int j = find_seg_warp<NT>(ts.pre, ts.coarse, t, lane);
-        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
+        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * SUB;
         const int64_t end = ts.lo[j] + ts.len[j];
         const int64_t span = end - start;
-        const int nu = span >= RK_SUB ? U : int((span + 31) >> 5);
+        const int nu = span >= SUB ? U : int((span + 31) >> 5);
         int col[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -721,18 +728,18 @@ __device__ __forceinline__ void walk_tasks_bits(const SpgArgs& g, TaskSmem<NT>& 
 // for the ranks in [0, rcount), then apply upd(r, col, b, a) to those.  All the
 // rank lookups of a task are issued before its first accumulator update: the
 // compiler cannot move a bitmap read past an atomic on the same shared memory.
-template <int NT, class AT, class BT, class RankF, class OnRankF, class UpdF>
+template <int NT, class AT, class BT, int SUB = RK_SUB, class RankF, class OnRankF, class UpdF>
 __device__ __forceinline__ void walk_tasks_rank(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
                                                 const AT* s_aval, const BT* __restrict__ bval, int rcount,
                                                 RankF rank_of, OnRankF on_rank, UpdF upd) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int U = RK_SUB / 32;
+    constexpr int U = SUB / 32;
     for (int t = wid; t < ntasks;) {
         const int j = find_seg_warp<NT>(ts.pre, ts.coarse, t, lane);
-        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * RK_SUB;
+        const int64_t start = ts.lo[j] + int64_t(t - ts.pre[j]) * SUB;
         const int64_t end = ts.lo[j] + ts.len[j];
         const int64_t span = end - start;
-        const int nu = span >= RK_SUB ? U : int((span + 31) >> 5);
+        const int nu = span >= SUB ? U : int((span + 31) >> 5);
         const AT a = s_aval[j];
         int col[U];
         BT val[U];
@@ -1164,6 +1171,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
     using AT = typename T::A;
     using BT = typename T::B;
     using Acc = typename T::Acc;
+    constexpr int VSUB = value_task_entries(ALG);
     extern __shared__ uint4 smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
     const RankLayout L = rank_layout(ncell_max, vcap, maxwin, sizeof(Acc), ALG == ALG_MULTPATH);
@@ -1318,8 +1326,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                 return int(e.y) + __popc(e.x & ((1u << (col & 31)) - 1u)) - rb;
             };
             for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
-                const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
-                walk_tasks_rank<NT, AT, BT>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
+                const int ntasks = load_tasks<NT, AT, true, VSUB>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
+                walk_tasks_rank<NT, AT, BT, VSUB>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
                                             [&](int r, int col) { scol[r] = col; },
                                             [&](int r, int col, const BT& b, const AT a) {
                                                 if constexpr (ALG == ALG_MULTPATH) atomicMin(&vals[r], a + b.d);
@@ -1329,8 +1337,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             }
             if constexpr (ALG == ALG_MULTPATH) {
                 for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
-                    const int ntasks = load_tasks<NT, AT, true>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
-                    walk_tasks_rank<NT, AT, BT>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
+                    const int ntasks = load_tasks<NT, AT, true, VSUB>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
+                    walk_tasks_rank<NT, AT, BT, VSUB>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
                                                 [&](int, int) {},
                                                 [&](int r, int, const BT& b, const AT a) {
                                                     if (a + b.d == vals[r]) atomicAdd(&sig[r], b.s);
