@@ -402,9 +402,10 @@ STC_API stc_status stc_mlp_forward(stc_handle* h, const float* weights, const fl
 
 /* The same model on the tensor cores (tcgen05 MMAs, fp32 accumulators in tensor
  * memory): each fp32 activation enters as the sum of two bf16 halves (hi, lo), so
- * inputs keep about 16 significant bits; results agree with stc_mlp_forward to
- * about 1e-5 relative.  feat must be 16-byte aligned (STC_ERR_INVALID_ARG
- * otherwise).  A tensor-core completion that does not arrive within about a
+ * inputs keep about 16 significant bits (error <= 2^-16 of each value).  The error
+ * of y is that rounding carried through the weights: about 1e-5 of |y| on feature
+ * rows, more where y cancels larger intermediate sums.  feat must be 16-byte
+ * aligned (STC_ERR_INVALID_ARG otherwise).  A tensor-core completion that does not arrive within about a
  * quarter of a second raises STC_FLAG_TIMEOUT (read by stc_check_device_status);
  * the kernel then releases its tensor memory and returns. */
 STC_API stc_status stc_mlp_forward_tc(stc_handle* h, const float* weights, const float* feat, int64_t n, float* y,
