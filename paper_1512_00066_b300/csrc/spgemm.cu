@@ -1171,7 +1171,9 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
     using AT = typename T::A;
     using BT = typename T::B;
     using Acc = typename T::Acc;
-    constexpr int VSUB = value_task_entries(ALG);
+    // masked products skip most products at the rank lookup, so per-task overhead
+    // dominates there: long tasks
+    constexpr int VSUB = MASKED ? RK_SUB : value_task_entries(ALG);
     extern __shared__ uint4 smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
     const RankLayout L = rank_layout(ncell_max, vcap, maxwin, sizeof(Acc), ALG == ALG_MULTPATH);
