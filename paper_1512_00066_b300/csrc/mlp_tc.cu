@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_forward_tc(const float* __rest
         bool got = warp_bar_wait(bar, phase);
         phase ^= 1;
         fence_after_sync();
-        // 3) epilogue 1: H1 = relu(D1 + b1), split, into the layer-2 A operand
+        // 3) epilogue 1: H1 = relu(D1) (D1 includes b1), split, into the layer-2 A operand
         if (got) {
 #pragma unroll
             for (int c = 0; c < NH / 16; ++c) {
