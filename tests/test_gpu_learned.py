@@ -74,6 +74,22 @@ def test_mlp_forward_tensor_cores(H, n):
     assert np.all(np.abs(y - yc) <= mlp_tc_tolerance(wd, x, yc) + 1e-5 * (1 + np.abs(yc)))
 
 
+def test_mlp_forward_tensor_cores_full_size(H):
+    """The workload the benchmark times: features of every row of A.A for R-MAT
+    scale 20 (2^20 rows), every row against the fp64 oracle."""
+    import paper_1512_00066_b300 as stc
+    w = stc.mlp_init(seed=1)
+    A = W.rmat(20, seed=0)
+    dA = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, np.ones(A.nnz, np.float32))
+    feat = H.row_features(dA, dA)
+    assert feat.shape[0] == 1 << 20
+    y = H.mlp_forward_tc(w, feat).cpu().numpy()
+    wd = bf16_weights(w)
+    x = feat[:, :67].double().cpu().numpy()
+    yr = O.mlp_forward(wd, x)
+    assert np.all(np.abs(y - yr) <= mlp_tc_tolerance(wd, x, yr))
+
+
 def test_mlp_forward_tensor_cores_signed_inputs(H):
     """Inputs of both signs and wide range (the hi/lo split of negative values),
     a non-zero padding column (ignored), and an empty batch."""
