@@ -395,6 +395,36 @@ def test_masked_rows_over_several_rank_windows(H, alg):
     check_masked(H, alg, A, B, M)
 
 
+def test_masked_rmat18_full_size_sampled(H):
+    """The benchmark's masked product, C<A> = A.A in fp64 at R-MAT scale 18: C has
+    exactly A's structure, and every 64th row plus the 256 heaviest rows hold the
+    oracle's product read at the mask's positions (0 where no product lands)."""
+    A = W.rmat(18, seed=0)
+    A.val = W.weights_unit01(A.nnz, seed=0)
+    M = W.Csr(A.nrows, A.ncols, A.rowptr, A.col, None)
+    d = to_dev(A)
+    C = H.spgemm_masked(O.PT_F64, d, d, to_dev(M))
+    torch.cuda.synchronize()
+    H.check_device_status()
+    assert np.array_equal(C.rowptr.cpu().numpy(), M.rowptr) and np.array_equal(C.col.cpu().numpy(), M.col)
+    lens = np.diff(A.rowptr)
+    ub = np.zeros(A.nrows, np.int64)
+    np.add.at(ub, np.repeat(np.arange(A.nrows), lens), lens[A.col])
+    rows = np.unique(np.r_[np.arange(0, A.nrows, 64), np.argsort(ub)[-256:]])
+    sel = np.concatenate([np.arange(M.rowptr[i], M.rowptr[i + 1]) for i in rows])
+    got = C.val.cpu().numpy()[sel]
+    ptr, col, val, absv = O.spgemm(O.PT_F64, A, A, rows=rows, want_abs=True)
+    mrow = np.repeat(np.arange(len(rows), dtype=np.int64), lens[rows])
+    pkeys = np.repeat(np.arange(len(rows), dtype=np.int64), np.diff(ptr)) * A.ncols + col.astype(np.int64)
+    mkeys = mrow * A.ncols + M.col[sel].astype(np.int64)
+    pos = np.minimum(np.searchsorted(pkeys, mkeys), max(len(pkeys) - 1, 0))
+    hit = pkeys[pos] == mkeys
+    exp = np.where(hit, val[pos], 0.0)
+    ab = np.where(hit, absv[pos], 0.0)
+    assert hit.any() and not hit.all()
+    compare_values(O.PT_F64, got, exp, ab, where="masked rmat18 sampled")
+
+
 def test_masked_errors(H):
     import paper_1512_00066_b300 as stc
     A = W.random_csr(10, 8, 3, seed=1)
