@@ -58,3 +58,24 @@ def test_null_arguments_are_rejected_before_any_device_work(libstc):
     assert f(None, 0, None, None, None, None, None) == 1  # STC_ERR_INVALID_ARG
     libstc.stc_bellman_ford.restype = ctypes.c_int
     assert libstc.stc_bellman_ford(None, 2, None, 0, None, None, 1, None) == 1
+
+
+def test_learned_and_tensor_core_entry_points_check_arguments_first(libstc):
+    """Null handles, weights, buffers and negative sizes are rejected with
+    STC_ERR_INVALID_ARG before any device work, for the perceptron entry points
+    (CUDA-core and tensor-core forward) and the masked product."""
+    p, i64 = ctypes.c_void_p, ctypes.c_int64
+    for name in ("stc_mlp_forward", "stc_mlp_forward_tc"):
+        f = getattr(libstc, name)
+        f.restype = ctypes.c_int
+        f.argtypes = [p, p, p, i64, p, p]
+        assert f(None, None, None, 0, None, None) == 1
+        dummy = ctypes.c_float(0.0)
+        ptr = ctypes.addressof(dummy)
+        assert f(None, ptr, ptr, 1, ptr, None) == 1      # no handle
+        assert f(ptr, None, ptr, 1, ptr, None) == 1      # no weights
+        assert f(ptr, ptr, None, 1, ptr, None) == 1      # rows without features
+        assert f(ptr, ptr, ptr, -1, ptr, None) == 1      # negative row count
+    g = libstc.stc_contract_spgemm_masked
+    g.restype = ctypes.c_int
+    assert g(None, 0, None, None, None, None, None, None) == 1
