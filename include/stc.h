@@ -434,6 +434,40 @@ STC_API stc_status stc_mlp_train(stc_handle* h, float* weights, const float* fea
                                  int32_t batch, int32_t epochs, float lr, uint64_t seed, float* loss_out,
                                  stc_stream stream);
 
+/*
+ * Exact row sizes: counts[i] = nnz(C_i) for C = A B (device int64 [A->nrows]),
+ * the symbolic phase of the plain path alone (the size of the union of the
+ * column sets of the B rows that row i of A selects, Section 3.3.1).  Values of
+ * A and B are not read and may be NULL.  Outputs wider than 2^18 columns are
+ * counted slab by slab (at most 32 slabs of 2^18 columns; STC_ERR_SHAPE above).
+ * opts may be NULL (validation on).  Synchronises `stream` once (the
+ * validation flags).
+ */
+STC_API stc_status stc_row_counts(stc_handle* h, const stc_csr* A, const stc_csr* B, int64_t* counts,
+                                  const stc_opts* opts, stc_stream stream);
+
+/*
+ * Training examples of the row-size model from the product A B: feat (device,
+ * float [A->nrows][STC_MLP_FEAT_STRIDE]) as stc_row_features, and the exact
+ * targets target[i] = log2(1 + nnz(C_i)) (device float [A->nrows]) from the
+ * symbolic phase (stc_row_counts).  Values of A and B are not read.
+ * Synchronises `stream` once.
+ */
+STC_API stc_status stc_training_rows(stc_handle* h, const stc_csr* A, const stc_csr* B, float* feat,
+                                     float* target, stc_stream stream);
+
+/*
+ * Model files.  stc_model_save writes the STC_MLP_NUM_WEIGHTS fp32 weights
+ * (device) to `path`: a 32-byte header (magic "STCMLP1", inputs 67, hidden 64,
+ * number of weights, the 64-bit FNV-1a checksum of the weight bytes) followed by
+ * the weights as little-endian fp32.  stc_model_load reads such a file into
+ * `weights` (device); a missing or unreadable file, another layout, trailing
+ * bytes or a checksum mismatch give STC_ERR_INVALID_ARG and leave `weights`
+ * unchanged.  Both synchronise `stream`.
+ */
+STC_API stc_status stc_model_save(const char* path, const float* weights, stc_stream stream);
+STC_API stc_status stc_model_load(const char* path, float* weights, stc_stream stream);
+
 typedef struct {
     int64_t rows;              /* output rows with at least one product (-1: exact path used) */
     int64_t overflow_rows;     /* rows whose predicted capacity was too small */
@@ -449,7 +483,10 @@ typedef struct {
  * the model `weights`, clipped to [1, min(ub_i, ncols)], or min(ub_i, ncols) when
  * weights is NULL -- and one numeric pass writes it into scratch of that size
  * while counting it exactly; rows that fit are compacted into C, rows that did
- * not are recomputed exactly.  B->ncols above 2^18 uses the exact two-pass path.
+ * not are recomputed exactly.  Outputs wider than 2^18 columns (at most 32
+ * column slabs of 2^18) run the same single pass slab by slab: every slab B_s
+ * is its own learned product A B_s, and stats count (row, slab) units; wider
+ * outputs than that use the exact two-pass path (stats->rows = -1).
  * Synchronises `stream` twice.  stats (host, may be NULL) as above.
  */
 STC_API stc_status stc_contract_spgemm_learned(stc_handle* h, stc_algebra alg, const stc_csr* A, const stc_csr* B,
@@ -525,14 +562,16 @@ STC_API int64_t stc_kernel_launches(const stc_handle* h);
  *  - G->nrows may not exceed STC_NOALLOC_BF_MAX_VERTICES; larger graphs get
  *    STC_ERR_CAPACITY before any work is enqueued.
  *  - The first call on each device looks up that array's device address
- *    (cudaGetSymbolAddress) with the device current; make that first call
- *    before any stream capture on that device.
+ *    (cudaGetSymbolAddress) with the device current.
+ *  - Every call synchronises `stream` and reads its result back into host
+ *    memory, so no call may be made while a stream on the device is being
+ *    captured into a CUDA graph.
  *  - Every call on a device shares the same array and leaves its contents
  *    behind; each call clears what must start at zero.  Calls whose work
  *    overlaps on the GPU (different streams or threads without ordering) race
  *    on the array and give wrong results: serialise them.
  * Arguments, results and the other errors are those of stc_bellman_ford;
- * *rounds_out (host, may be NULL).  Synchronises `stream`.
+ * *rounds_out (host, may be NULL).
  */
 #define STC_NOALLOC_BF_MAX_VERTICES (1 << 20)
 STC_API stc_status stc_bellman_ford_noalloc(stc_algebra alg, const stc_csr* G, int32_t source,

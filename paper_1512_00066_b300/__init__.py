@@ -159,6 +159,14 @@ def lib():
                                                       ctypes.POINTER(_Csr), p, ctypes.c_float,
                                                       ctypes.POINTER(_LearnedStats), ctypes.POINTER(_Opts), p]
             L.stc_contract_spgemm_learned.restype = ctypes.c_int
+            L.stc_row_counts.argtypes = [p, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, ctypes.POINTER(_Opts), p]
+            L.stc_row_counts.restype = ctypes.c_int
+            L.stc_training_rows.argtypes = [p, ctypes.POINTER(_Csr), ctypes.POINTER(_Csr), p, p, p]
+            L.stc_training_rows.restype = ctypes.c_int
+            L.stc_model_save.argtypes = [ctypes.c_char_p, p, p]
+            L.stc_model_save.restype = ctypes.c_int
+            L.stc_model_load.argtypes = [ctypes.c_char_p, p, p]
+            L.stc_model_load.restype = ctypes.c_int
             L.stc_bellman_ford_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(_Csr), i32, p,
                                                    ctypes.POINTER(i32), p]
             L.stc_bellman_ford_noalloc.restype = ctypes.c_int
@@ -176,6 +184,28 @@ def _status_text(s: int) -> str:
 def _check(st: int, where: str):
     if st != 0:
         raise StcError(st, where)
+
+
+def _check_dist(alg: int, G: "DeviceCsr", dist: torch.Tensor, where: str) -> None:
+    """Reject a distance buffer the library would write out of bounds or misread.
+
+    The Bellman-Ford kernels write G.nrows elements of the algebra's type (int32
+    for MIN_PLUS_I32, fp32 for MIN_PLUS_F32) at dist's first element, so the
+    buffer must be a contiguous tensor of that dtype with at least G.nrows
+    elements on the device that holds G.  Raised before any device work."""
+    want = {MIN_PLUS_I32: torch.int32, MIN_PLUS_F32: torch.float32}.get(alg)
+    if want is None:
+        raise ValueError(f"{where}: algebra {alg} has no Bellman-Ford (MIN_PLUS_I32 or MIN_PLUS_F32)")
+    if not isinstance(dist, torch.Tensor):
+        raise ValueError(f"{where}: dist must be a torch tensor")
+    if dist.dtype != want:
+        raise ValueError(f"{where}: dist has dtype {dist.dtype}, the algebra needs {want}")
+    if not dist.is_contiguous():
+        raise ValueError(f"{where}: dist must be contiguous")
+    if dist.numel() < G.nrows:
+        raise ValueError(f"{where}: dist holds {dist.numel()} elements, the graph has {G.nrows} vertices")
+    if not dist.is_cuda or dist.device != G.col.device:
+        raise ValueError(f"{where}: dist is on {dist.device}, the graph on {G.col.device}")
 
 
 def _stream_ptr(stream=None) -> int:
@@ -412,6 +442,8 @@ class Handle:
         if dist is None:
             dist = torch.empty(G.nrows, dtype=torch.int32 if alg == MIN_PLUS_I32 else torch.float32,
                                device=G.col.device)
+        else:
+            _check_dist(alg, G, dist, "bellman_ford")
         rounds = ctypes.c_int32(0)
         relax = ctypes.c_int64(0)
         g = G._c()
@@ -431,6 +463,24 @@ class Handle:
         _check(lib().stc_row_features(self._h, ctypes.byref(a), ctypes.byref(b), f.data_ptr(), _stream_ptr(stream)),
                "stc_row_features")
         return f
+
+    def row_counts(self, A: DeviceCsr, B: DeviceCsr, skip_validation: bool = False, stream=None) -> torch.Tensor:
+        """Exact nnz of every row of A B (the symbolic phase alone): int64 [A.nrows]."""
+        c = torch.empty(A.nrows, dtype=torch.int64, device=A.col.device)
+        opts = _Opts(1 if skip_validation else 0, 0, 0)
+        a, b = A._c(), B._c()
+        _check(lib().stc_row_counts(self._h, ctypes.byref(a), ctypes.byref(b), c.data_ptr(), ctypes.byref(opts),
+                                    _stream_ptr(stream)), "stc_row_counts")
+        return c
+
+    def training_rows_of(self, A: DeviceCsr, B: DeviceCsr, stream=None):
+        """(feat [A.nrows, 68], target [A.nrows]) of the product A B, from stc_training_rows."""
+        f = torch.empty((A.nrows, MLP_FEAT_STRIDE), dtype=torch.float32, device=A.col.device)
+        t = torch.empty(A.nrows, dtype=torch.float32, device=A.col.device)
+        a, b = A._c(), B._c()
+        _check(lib().stc_training_rows(self._h, ctypes.byref(a), ctypes.byref(b), f.data_ptr(), t.data_ptr(),
+                                       _stream_ptr(stream)), "stc_training_rows")
+        return f, t
 
     def mlp_forward(self, weights: torch.Tensor, feat: torch.Tensor, stream=None) -> torch.Tensor:
         y = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
@@ -561,8 +611,11 @@ def bellman_ford_noalloc(alg: int, G: DeviceCsr, source: int, dist: torch.Tensor
     For callers that must not allocate device memory during the call: the
     library's working memory is a fixed array compiled into it.  Returns the
     number of rounds; raises StcError (STC_ERR_CAPACITY) above
-    NOALLOC_BF_MAX_VERTICES vertices.
+    NOALLOC_BF_MAX_VERTICES vertices.  `dist` must be a contiguous tensor of the
+    algebra's type with at least G.nrows elements on G's device (ValueError
+    otherwise, before any device work).
     """
+    _check_dist(alg, G, dist, "bellman_ford_noalloc")
     rounds = ctypes.c_int32(0)
     g = G._c()
     st = lib().stc_bellman_ford_noalloc(alg, ctypes.byref(g), int(source), dist.data_ptr(),
@@ -580,16 +633,28 @@ def mlp_init(seed: int = 0, device="cuda", stream=None) -> torch.Tensor:
 
 def training_rows(H: "Handle", pairs):
     """Features and exact targets log2(1 + nnz(C_i)) for every row of every (A, B)
-    pair (DeviceCsr), computed on the device: (feat [N, 68], target [N])."""
+    pair (DeviceCsr), both computed by the library (stc_training_rows):
+    (feat [N, 68], target [N])."""
     feats, targets = [], []
     for A, B in pairs:
-        feats.append(H.row_features(A, B))
-        C = H.spgemm(OR_AND_BOOL, A.__class__(A.nrows, A.ncols, A.rowptr, A.col,
-                                              torch.ones(A.nnz, dtype=torch.uint8, device=A.col.device)),
-                     B.__class__(B.nrows, B.ncols, B.rowptr, B.col,
-                                 torch.ones(B.nnz, dtype=torch.uint8, device=B.col.device)))
-        targets.append(torch.log2(1.0 + (C.rowptr[1:] - C.rowptr[:-1]).to(torch.float32)))
+        f, t = H.training_rows_of(A, B)
+        feats.append(f)
+        targets.append(t)
     return torch.cat(feats), torch.cat(targets)
+
+
+def model_save(path: str, weights: torch.Tensor, stream=None) -> None:
+    """Write the model's weights (device fp32 [MLP_NUM_WEIGHTS]) to a file (stc_model_save)."""
+    if weights.dtype != torch.float32 or weights.numel() != MLP_NUM_WEIGHTS or not weights.is_contiguous():
+        raise ValueError(f"weights must be a contiguous float32 tensor of {MLP_NUM_WEIGHTS} values")
+    _check(lib().stc_model_save(str(path).encode(), weights.data_ptr(), _stream_ptr(stream)), "stc_model_save")
+
+
+def model_load(path: str, device="cuda", stream=None) -> torch.Tensor:
+    """Read a model file written by model_save into a new device tensor (stc_model_load)."""
+    w = torch.empty(MLP_NUM_WEIGHTS, dtype=torch.float32, device=device)
+    _check(lib().stc_model_load(str(path).encode(), w.data_ptr(), _stream_ptr(stream)), "stc_model_load")
+    return w
 
 
 _default = {}

@@ -408,7 +408,18 @@ extern "C" stc_status stc_selftest_barrier(stc_handle* h, int32_t missing, int32
 
 namespace {
 
-constexpr size_t NOALLOC_HEADER = 256;  // counters, barrier, rounds, flags, relaxations
+// Header of the scratch array (bytes):
+//   [0, 12)   int[0..2]   frontier and work counters
+//   [16, 24)  int[4..5]   grid-barrier state
+//   [24, 28)  int[6]      round count
+//   [28, 32)  int[7]      device flags
+//   [64, 72)  u64         relaxation counter (written by every round, not read back)
+// then, per vertex, the two frontier slots, the round stamp and the fp32 distance key.
+constexpr size_t NOALLOC_HEADER = 256;
+constexpr size_t NOALLOC_RELAX_OFFSET = 64;
+static_assert(NOALLOC_RELAX_OFFSET + sizeof(unsigned long long) <= NOALLOC_HEADER,
+              "the relaxation counter must sit inside the cleared header");
+static_assert(8 * sizeof(int) <= NOALLOC_RELAX_OFFSET, "the counters and flags must end before the relaxation counter");
 // per vertex: two frontier slots, a round stamp and an fp32 distance key
 constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + size_t(STC_NOALLOC_BF_MAX_VERTICES) * 16;
 
@@ -457,7 +468,7 @@ stc_status run_bf_noalloc(const stc_csr* G, int32_t source, void* dist_out, int3
     a.col = G->col;
     a.w = G->val;
     a.cnt = ints;
-    a.relax = reinterpret_cast<unsigned long long*>(base + 64);
+    a.relax = reinterpret_cast<unsigned long long*>(base + NOALLOC_RELAX_OFFSET);
     a.frontier[0] = reinterpret_cast<int32_t*>(base + NOALLOC_HEADER);
     a.frontier[1] = a.frontier[0] + n;
     a.stamp = a.frontier[1] + n;

@@ -21,6 +21,9 @@
 
 #include <algorithm>
 
+#include <cstdio>
+#include <cstring>
+
 #include "stc_internal.cuh"
 
 namespace {
@@ -249,6 +252,31 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __re
     }
 }
 
+// target[i] = log2(1 + cnt[i]): the quantity the model predicts, from the exact
+// row counts of the symbolic phase.
+__global__ void k_log2_targets(int64_t n, const int64_t* __restrict__ cnt, float* __restrict__ target) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        target[i] = float(log2(1.0 + double(cnt[i])));
+}
+
+// 64-bit FNV-1a over a byte string (Fowler, Noll and Vo's published constants):
+// the integrity check of a saved model file.
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+    uint64_t x = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        x ^= p[i];
+        x *= 0x100000001b3ull;
+    }
+    return x;
+}
+
+struct ModelHeader {
+    char magic[8];        // "STCMLP1" and a terminating zero
+    int32_t inputs, hidden, nweights, reserved;
+    uint64_t checksum;    // FNV-1a of the nweights little-endian fp32 values
+};
+static_assert(sizeof(ModelHeader) == 32, "model file header layout");
+
 size_t grad_smem() { return sizeof(float) * (size_t(NW) + 3 + size_t(GR) * NF + 3 * size_t(GR) * NH + GR); }
 
 }  // namespace
@@ -400,5 +428,79 @@ extern "C" stc_status stc_mlp_train(stc_handle* h, float* weights, const float* 
         if (loss_out) loss_out[e] = lh / float(n);
     }
     STC_CUDA_TRY(cudaStreamSynchronize(s));
+    return STC_OK;
+}
+
+extern "C" stc_status stc_row_counts(stc_handle* h, const stc_csr* A, const stc_csr* B, int64_t* counts,
+                                     const stc_opts* opts, stc_stream stream) {
+    if (!h || !A || !B || (A->nrows > 0 && !counts)) return STC_ERR_INVALID_ARG;
+    stc_csr a = *A, b = *B;
+    if (!a.val) a.val = a.col;  // values are not read
+    if (!b.val) b.val = b.col;
+    stc_status st = stc_check_csr_host(&a);
+    if (st != STC_OK) return st;
+    if ((st = stc_check_csr_host(&b)) != STC_OK) return st;
+    if (A->ncols != B->nrows) return STC_ERR_SHAPE;
+    if ((st = stc_row_counts_impl(h, &a, &b, counts, opts, stream)) != STC_OK) return st;
+    return stc_check_device_status(h, stream);
+}
+
+extern "C" stc_status stc_training_rows(stc_handle* h, const stc_csr* A, const stc_csr* B, float* feat,
+                                        float* target, stc_stream stream) {
+    if (!h || !A || !B || (A->nrows > 0 && (!feat || !target))) return STC_ERR_INVALID_ARG;
+    stc_csr a = *A, b = *B;
+    if (!a.val) a.val = a.col;
+    if (!b.val) b.val = b.col;
+    stc_status st = stc_check_csr_host(&a);
+    if (st != STC_OK) return st;
+    if ((st = stc_check_csr_host(&b)) != STC_OK) return st;
+    if (A->ncols != B->nrows) return STC_ERR_SHAPE;
+    if (A->nrows == 0) return STC_OK;
+    StcScratch sc(h, stream);
+    int64_t* cnt = sc.get<int64_t>(size_t(A->nrows));
+    if (!cnt) return STC_ERR_OOM;
+    if ((st = stc_row_counts_impl(h, &a, &b, cnt, nullptr, stream)) != STC_OK) return st;
+    if ((st = stc_features_impl(h, sc, &a, &b, feat, stream)) != STC_OK) return st;
+    int64_t blocks = (A->nrows + 255) / 256;
+    if (blocks > int64_t(h->num_sms) * 8) blocks = int64_t(h->num_sms) * 8;
+    k_log2_targets<<<unsigned(blocks), 256, 0, stream>>>(A->nrows, cnt, target);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return stc_check_device_status(h, stream);
+}
+
+extern "C" stc_status stc_model_save(const char* path, const float* weights, stc_stream stream) {
+    if (!path || !weights) return STC_ERR_INVALID_ARG;
+    std::vector<float> w(NW);
+    STC_CUDA_TRY(cudaMemcpyAsync(w.data(), weights, sizeof(float) * NW, cudaMemcpyDeviceToHost, stream));
+    STC_CUDA_TRY(cudaStreamSynchronize(stream));
+    ModelHeader hd{};
+    memcpy(hd.magic, "STCMLP1", 8);
+    hd.inputs = NF;
+    hd.hidden = NH;
+    hd.nweights = NW;
+    hd.checksum = fnv1a64(reinterpret_cast<const unsigned char*>(w.data()), sizeof(float) * NW);
+    FILE* f = fopen(path, "wb");
+    if (!f) return STC_ERR_INVALID_ARG;
+    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(w.data(), sizeof(float), NW, f) == size_t(NW);
+    ok = (fclose(f) == 0) && ok;
+    return ok ? STC_OK : STC_ERR_INVALID_ARG;
+}
+
+extern "C" stc_status stc_model_load(const char* path, float* weights, stc_stream stream) {
+    if (!path || !weights) return STC_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) return STC_ERR_INVALID_ARG;
+    ModelHeader hd{};
+    std::vector<float> w(NW);
+    bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "STCMLP1", 8) == 0 && hd.inputs == NF &&
+              hd.hidden == NH && hd.nweights == NW && fread(w.data(), sizeof(float), NW, f) == size_t(NW);
+    unsigned char extra;
+    ok = ok && fread(&extra, 1, 1, f) == 0;  // nothing after the weights
+    fclose(f);
+    if (!ok || fnv1a64(reinterpret_cast<const unsigned char*>(w.data()), sizeof(float) * NW) != hd.checksum)
+        return STC_ERR_INVALID_ARG;
+    STC_CUDA_TRY(cudaMemcpyAsync(weights, w.data(), sizeof(float) * NW, cudaMemcpyHostToDevice, stream));
+    STC_CUDA_TRY(cudaStreamSynchronize(stream));
     return STC_OK;
 }

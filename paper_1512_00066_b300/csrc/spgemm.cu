@@ -1953,10 +1953,16 @@ __global__ void k_slab_scatter(const int64_t* __restrict__ b_ptr, const int32_t*
             const int32_t shift = int32_t(int64_t(t) * RK_MAX_COLS);
             for (int64_t e = lane; e < n; e += 32) {
                 s_col[dst + e] = b_col[src + e] - shift;
-                s_val[dst + e] = b_val[src + e];
+                if (s_val) s_val[dst + e] = b_val[src + e];
             }
         }
     }
+}
+
+// dst[i] += src[i].
+__global__ void k_add_i64(int64_t n, const int64_t* __restrict__ src, int64_t* __restrict__ dst) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] += src[i];
 }
 
 // c_ptr[i + 1] = sum over slabs of cnt[s NR + i].
@@ -1991,14 +1997,15 @@ struct Slabs {
     std::vector<int> ncell;
 };
 
+// values == false: only the structure of the slabs (B->val may be NULL).
 stc_status build_slabs(stc_handle* h, StcScratch& sc, int alg, const stc_csr* A, const stc_csr* B, int S,
-                       Slabs& out, stc_stream s) {
+                       Slabs& out, stc_stream s, bool values = true) {
     const int64_t K = A->ncols;
     const size_t vbB = stc_val_bytes(alg, 'B');
     int32_t* bnd = sc.get<int32_t>(size_t(K) * size_t(S + 1) + 1);
     int64_t* bsptr = sc.get<int64_t>(size_t(S) * size_t(K + 1));
     int32_t* s_col = sc.get<int32_t>(size_t(B->nnz) + 1);
-    unsigned char* s_val = sc.get<unsigned char>((size_t(B->nnz) + 1) * vbB);
+    unsigned char* s_val = values ? sc.get<unsigned char>((size_t(B->nnz) + 1) * vbB) : nullptr;
     if (sc.failed) return STC_ERR_OOM;
     STC_CUDA_TRY(cudaMemsetAsync(bsptr, 0, sizeof(int64_t) * size_t(S) * size_t(K + 1), s));
     const unsigned gw = unsigned(h->num_sms * 16);
@@ -2054,7 +2061,7 @@ stc_status build_slabs(stc_handle* h, StcScratch& sc, int alg, const stc_csr* A,
         g.ncell = int((g.ncols + RK_CELL - 1) >> RK_CELL_SHIFT);
         g.b_ptr = bsptr + size_t(t) * (K + 1);
         g.b_col = s_col + sb.base[t];
-        g.b_val = s_val + size_t(sb.base[t]) * vbB;
+        g.b_val = s_val ? s_val + size_t(sb.base[t]) * vbB : nullptr;
         g.nnzB = (t + 1 < S ? sb.base[t + 1] : B->nnz) - sb.base[t];
         g.col_base = int(int64_t(t) * RK_MAX_COLS);
         out.args[t] = g;
@@ -2069,6 +2076,75 @@ stc_status build_slabs(stc_handle* h, StcScratch& sc, int alg, const stc_csr* A,
         out.ncell[t] = g.ncell > 0 ? g.ncell : 1;
         out.cfg[t] = rank_config(alg, g.ncols, out.ncell[t]);
         if (!out.cfg[t].vcap) return STC_ERR_INVALID_ARG;
+    }
+    return STC_OK;
+}
+
+// Exact nnz(C_i) of every row of C = A B (the symbolic phase alone): row
+// analysis, binning and the symbolic rank kernel without stored records, slab by
+// slab (summed) for outputs wider than RK_MAX_COLS.  counts: device int64[nrows].
+stc_status row_counts_impl(stc_handle* h, const stc_csr* A, const stc_csr* B, int64_t* counts, bool validate,
+                           stc_stream s) {
+    const int64_t NR = A->nrows;
+    if (NR == 0) return STC_OK;
+    STC_CUDA_TRY(cudaMemsetAsync(counts, 0, size_t(NR) * 8, s));
+    StcScratch sc(h, s);
+    stc_status st;
+    if (validate) {
+        if ((st = stc_validate_csr_async(h, A, s)) != STC_OK) return st;
+        if ((st = stc_validate_csr_async(h, B, s)) != STC_OK) return st;
+    }
+    const int S = B->ncols > RK_MAX_COLS ? int((B->ncols + RK_MAX_COLS - 1) / RK_MAX_COLS) : 1;
+    if (S > SLAB_MAX) return STC_ERR_SHAPE;
+    std::vector<SpgArgs> args;
+    if (S == 1) {
+        args.push_back(make_args(A, B));
+    } else {
+        Slabs sl;
+        if ((st = build_slabs(h, sc, ALG_BOOL, A, B, S, sl, s, false)) != STC_OK) return st;
+        args = sl.args;
+    }
+    int64_t* ub = sc.get<int64_t>(size_t(NR));
+    int32_t* rowlist = sc.get<int32_t>(size_t(NR));
+    int64_t* part = S > 1 ? sc.get<int64_t>(size_t(NR)) : counts;
+    int* ints = sc.get<int>(2 * NBINS_ALL + 8);
+    if (sc.failed) return STC_ERR_OOM;
+    int64_t blocks = (NR * 32 + 255) / 256;
+    if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
+    for (int t = 0; t < S; ++t) {
+        SpgRows R{};
+        R.one = args[t];
+        R.nb = 1;
+        const int ncell = args[t].ncell > 0 ? args[t].ncell : 1;
+        STC_CUDA_TRY(cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS_ALL + 8), s));
+        if (S > 1) STC_CUDA_TRY(cudaMemsetAsync(part, 0, size_t(NR) * 8, s));
+        int* bin_count = ints;
+        int* cursor = ints + NBINS_ALL;
+        int* nlist = ints + 2 * NBINS_ALL;
+        int* counter = ints + 2 * NBINS_ALL + 1;
+        int* max_nnz = ints + 2 * NBINS_ALL + 4;
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, part);
+        k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
+        k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, part, cursor, rowlist);
+        STC_LAUNCH_CHECK();
+        stc_count(h, 3);
+        const size_t smem = sym_layout(ncell).total;
+        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        int per_sm = 0;
+        STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
+        if (per_sm < 1) return STC_ERR_CUDA;
+        int64_t grid = int64_t(per_sm) * h->num_sms;
+        if (grid > NR) grid = NR;
+        kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell, rowlist, nlist, counter, part, max_nnz, nullptr,
+                                                     nullptr, 0);
+        STC_LAUNCH_CHECK();
+        stc_count(h);
+        if (S > 1) {
+            k_add_i64<<<unsigned(h->num_sms * 8), 256, 0, s>>>(NR, part, counts);
+            STC_LAUNCH_CHECK();
+            stc_count(h);
+        }
     }
     return STC_OK;
 }
@@ -3088,4 +3164,9 @@ stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, con
         return st;
     }
     return spgemm_learned_impl(h, alg, A, B, C, weights, margin, stats, !(opts && opts->skip_validation), s);
+}
+
+stc_status stc_row_counts_impl(stc_handle* h, const stc_csr* A, const stc_csr* B, int64_t* counts,
+                               const stc_opts* opts, stc_stream s) {
+    return row_counts_impl(h, A, B, counts, !(opts && opts->skip_validation), s);
 }
