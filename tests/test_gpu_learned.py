@@ -229,3 +229,91 @@ def test_learned_column_slabs_equal_plain(H, trained, alg):
         ptr, rcol, rval, rabs = O.spgemm(alg, A, B, want_abs=True)
         assert np.array_equal(rp, ptr) and np.array_equal(col, rcol)
         compare_values(alg, val, rval, rabs)
+
+
+def test_training_rows_are_features_and_exact_log_counts(H):
+    """stc_training_rows: the features of stc_row_features and targets
+    log2(1 + nnz(C_i)) from the symbolic phase; stc_row_counts equals the oracle's
+    row counts, also past 2^18 output columns (counted slab by slab)."""
+    import paper_1512_00066_b300 as stc
+    for A, B in ((W.rmat(12, seed=21), None),
+                 (W.random_csr(300, 700, 30, seed=22, empty_frac=0.1),
+                  W.random_csr(700, 3 * (1 << 18) + 5, 200, seed=23, empty_frac=0.1))):
+        B = A if B is None else B
+        dA = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, None)
+        dB = stc.DeviceCsr.from_host(B.nrows, B.ncols, B.rowptr, B.col, None)
+        cnt = O.spgemm_count(A, B)
+        assert np.array_equal(H.row_counts(dA, dB).cpu().numpy(), cnt)
+        f, t = H.training_rows_of(dA, dB)
+        assert torch.equal(f, H.row_features(dA, dB))
+        assert np.array_equal(t.cpu().numpy(), np.log2(1.0 + cnt).astype(np.float32))
+
+
+def test_model_file_round_trip_and_rejections(H, trained, tmp_path):
+    import paper_1512_00066_b300 as stc
+    w, _ = trained
+    p = tmp_path / "model.stc"
+    stc.model_save(p, w)
+    assert torch.equal(stc.model_load(p), w)
+    raw = bytearray(p.read_bytes())
+    assert len(raw) == 32 + 4 * stc.MLP_NUM_WEIGHTS and raw[:8] == b"STCMLP1\0"
+    for bad in (raw[:-4], raw + b"\0", raw[:40] + bytes([raw[40] ^ 1]) + raw[41:], b"XXXXXXX\0" + raw[8:]):
+        q = tmp_path / "bad.stc"
+        q.write_bytes(bytes(bad))
+        with pytest.raises(stc.StcError):
+            stc.model_load(q)
+    with pytest.raises(stc.StcError):
+        stc.model_load(tmp_path / "missing.stc")
+
+
+def _block_hashes(col: torch.Tensor, block: int = 1 << 27):
+    """64-bit hash of every block of `block` consecutive entries: sum of col * w
+    with fixed odd random weights w, in wrapping int64 arithmetic."""
+    g = torch.Generator(device="cuda").manual_seed(12345)
+    w = torch.randint(-(1 << 62), 1 << 62, (block,), dtype=torch.int64, device="cuda", generator=g) | 1
+    out = []
+    for s in range(0, col.numel(), block):
+        c = col[s:s + block].to(torch.int64)
+        out.append(int((c * w[:c.numel()]).sum()))
+    return out
+
+
+def _rows_of(C, rows):
+    """(row pointers, columns, values) of the listed rows of device CSR C, on the host."""
+    r = torch.from_numpy(rows).cuda()
+    start = C.rowptr[r]
+    lens = C.rowptr[r + 1] - start
+    ptr = torch.zeros(rows.size + 1, dtype=torch.int64, device="cuda")
+    ptr[1:] = torch.cumsum(lens, 0)
+    idx = torch.repeat_interleave(start - ptr[:-1], lens) + torch.arange(int(ptr[-1]), device="cuda")
+    return ptr.cpu().numpy(), C.col[idx].cpu().numpy(), C.val[idx].cpu().numpy()
+
+
+def test_rmat20_learned_full_size_structure_and_sampled_values(H, trained):
+    """The learned-sizing workload at full size: (+,x) fp32 A.A on R-MAT scale 20
+    (2^20 output columns, four slabs).  The learned result has the plain result's
+    row pointers exactly and the same column array (64-bit hash of every block of
+    2^27 entries); values of every 64th row and of the 1024 longest rows against
+    the fp64 oracle within relative 1e-5."""
+    import paper_1512_00066_b300 as stc
+    w, _ = trained
+    A = W.rmat(20, seed=0)
+    A.val = W.weights_unit01(A.nnz, seed=0).astype(np.float32)
+    dA = to_dev(A)
+    plain = H.spgemm(O.PT_F32, dA, dA)
+    p_ptr = plain.rowptr.cpu().numpy()
+    p_hash = _block_hashes(plain.col)
+    lens = np.diff(p_ptr)
+    rows = np.unique(np.r_[np.arange(0, A.nrows, 64), np.argsort(lens)[-1024:]]).astype(np.int64)
+    del plain
+    torch.cuda.empty_cache()
+    C, st = H.spgemm_learned(O.PT_F32, dA, dA, w, 0.5)
+    assert st["nnz"] == int(p_ptr[-1]) and st["rows"] > A.nrows
+    assert np.array_equal(C.rowptr.cpu().numpy(), p_ptr)
+    assert _block_hashes(C.col) == p_hash
+    gptr, gcol, gval = _rows_of(C, rows)
+    del C
+    torch.cuda.empty_cache()
+    ptr, rcol, rval, rabs = O.spgemm(O.PT_F32, A, A, rows=rows, want_abs=True)
+    assert np.array_equal(gptr, ptr) and np.array_equal(gcol, rcol)
+    compare_values(O.PT_F32, gval, rval, rabs, "rmat20 learned rows")

@@ -5,6 +5,8 @@ Forward distances and path counts are exact integers (fp64 counts below 2^53) an
 must match bit for bit; centrality is held to relative 1e-12 (absolute 1e-9 on
 entries the oracle gives as exactly zero).
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -25,8 +27,14 @@ def H():
     return stc.Handle()
 
 
+@functools.lru_cache(maxsize=2)
+def _structure(scale, seed):
+    return W.rmat(scale, seed=seed)
+
+
 def graph(scale, seed, weighted):
-    G = W.rmat(scale, seed=seed)
+    S = _structure(scale, seed)
+    G = W.Csr(S.nrows, S.ncols, S.rowptr, S.col)
     G.val = W.weights_int(G.nnz, 1, 255, seed + 1) if weighted else None
     return G
 
@@ -118,6 +126,19 @@ def test_rmat22_full_size_forward_sampled(H):
         sj = sig[:, j].cpu().numpy()
         assert np.array_equal(dj, np.where(rd < 0, INF, rd))
         assert np.array_equal(sj, rs)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_rmat22_centrality_on_a_source_sample(H, weighted):
+    """The centrality workload at full size: R-MAT scale 22 with unit lengths and
+    with int32 lengths U[1,255], over 64 sources (every 64th of the seeded
+    4096-source sample, in one batch of 64): every vertex's centrality against
+    Brandes' algorithm (Section 4.2, geodetic semiring) within relative 1e-12."""
+    G = graph(22, 0, weighted)
+    src = W.sample_sources(G, 4096, seed=0)[::64]
+    assert src.size == 64
+    bc = H.mfbc(to_dev(G), src, batch=64).cpu().numpy()
+    bc_close(bc, O.brandes(G, src, weighted))
 
 
 @pytest.mark.parametrize("weighted", [False, True])

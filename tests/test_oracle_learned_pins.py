@@ -70,3 +70,40 @@ def test_mlp_closed_form_bias_only():
     g, L = O.mlp_grad(w, x, t)
     assert abs(g[-1] - 2 * np.mean(2.5 - t)) < 1e-12 and np.all(g[:-1] == 0)
     assert abs(L - np.mean((2.5 - t) ** 2)) < 1e-12
+
+
+def test_min_hash_key_of_a_single_column_from_the_published_output():
+    """A row whose column union is {0}: SplitMix64's first published output for
+    seed 0 is 0xE220A8397B1DCDAF, so the column lands in bucket 0xE220... >> 59 = 28
+    with key 0x7B1DCDAF (the low word), normalised by 2^32; every other bucket is
+    empty (1, 1).  Taking the high word or dropping the normalisation fails here."""
+    B = W.Csr(1, 4, np.array([0, 1], np.int64), np.array([0], np.int32))
+    F = O.row_features(_single_row(0, 1), B)[0]
+    assert (0xE220A8397B1DCDAF >> 59) == 28
+    for b in range(32):
+        if b == 28:
+            assert F[3 + 2 * b] == 0x7B1DCDAF / 2.0 ** 32 and F[4 + 2 * b] == 0.0
+        else:
+            assert F[3 + 2 * b] == 1.0 and F[4 + 2 * b] == 1.0
+
+
+def test_min_hash_keys_restated_on_random_rows():
+    """Bucket-wise minimum of (low 32 bits of SplitMix64(j)) / 2^32 over the union
+    of the B rows' columns, written out with Python integers."""
+    A = W.random_csr(12, 40, 6, seed=7, empty_frac=0.0)
+    B = W.random_csr(40, 3000, 50, seed=8, empty_frac=0.0)
+    F = O.row_features(A, B)
+    for i in range(A.nrows):
+        cols = set()
+        for k in A.col[A.rowptr[i]:A.rowptr[i + 1]]:
+            cols |= set(B.col[B.rowptr[k]:B.rowptr[k + 1]].tolist())
+        mins = [None] * 32
+        for j in cols:
+            h = O.splitmix64(int(j))
+            b, key = h >> 59, h & 0xFFFFFFFF
+            mins[b] = key if mins[b] is None else min(mins[b], key)
+        for b in range(32):
+            if mins[b] is None:
+                assert F[i, 3 + 2 * b] == 1.0 and F[i, 4 + 2 * b] == 1.0
+            else:
+                assert F[i, 3 + 2 * b] == mins[b] / 2.0 ** 32 and F[i, 4 + 2 * b] == 0.0
