@@ -34,7 +34,7 @@ METRIC = "SpGEMM semiring-ops/s & MFBC GTEPS, learned+batched vs plain form on o
 UNIT = "semiring-ops/s"
 L2_BYTES = 126 * 1024 * 1024
 # DRAM bytes (read + write) per output entry of the fp64 numeric rank kernel, from
-# the ncu capture in profiles/k_numeric_rank_fp64_rmat16.md (R-MAT scale 16).
+# one ncu capture of that kernel at R-MAT scale 16.
 # Traffic grows with the output (B stays in L2), so a full launch is scaled by its
 # nnz(C): 0.349 GB read + 1.848 GB written for 163,809,247 entries.
 NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = (0.348871e9 + 1.848168e9) / 163809247
@@ -89,6 +89,22 @@ def nprod_of(A: W.Csr) -> int:
 
 def csr_bytes(n, nnz, s):
     return 8 * (n + 1) + (4 + s) * nnz
+
+
+# Betweenness centrality: algorithmic bytes per (edge, source) traversal in each
+# direction -- the target's 4-byte distance read and its 8-byte multiplicity (forward)
+# or dependency (backward) updated; the edge's column and length are shared by the
+# batch's sources and not counted.
+MFBC_BYTES_PER_TRAVERSAL = 12
+
+
+def gustavson_bytes(A: W.Csr, B: W.Csr, nnzC: int, s: int) -> int:
+    """Algorithmic bytes of C = A B in the row-wise (Gustavson) model: read A, for
+    every stored A_ik the pointer pair of B_k (8 B) and B_k's columns and values,
+    write C; s = bytes per value."""
+    lens = np.diff(B.rowptr)
+    gathered = int(lens[A.col].sum())
+    return csr_bytes(A.nrows, A.nnz, s) + 8 * A.nnz + (4 + s) * gathered + csr_bytes(A.nrows, nnzC, s)
 
 
 class Clocks:
@@ -231,7 +247,7 @@ def run_stc(args):
         def step():
             C = H.spgemm(stc.MIN_PLUS_I32, dA, dA)
             t = H.phase_times()
-            return ops_step, {"numeric_ms": t[4], "nnzC": C.nnz, "s": 4}
+            return ops_step, {"numeric_ms": t[4], "spgemm_ms": sum(t[:5]), "nnzC": C.nnz, "s": 4}
         dom_val_bytes = 4
     else:
         nprod = products(A)
@@ -293,8 +309,11 @@ def run_stc(args):
         t_total = float(tt.item())
     value = world * ops_total / t_total
 
-    # roofline of the dominant kernel (numeric pass of the first SpGEMM): compulsory
-    # DRAM bytes = read A and B once, the cell-offset table, C.rowptr; write C
+    # roofline of the dominant kernel: the numeric phase of the first SpGEMM of the
+    # step.  Algorithmic bytes follow the row-wise (Gustavson) traffic model: read A,
+    # for every stored A_ik its B row's pointer pair (8 B) and the row's columns and
+    # values, write C (gustavson_bytes).  The compulsory bytes (A, B and C once, plus
+    # the cell table and C.rowptr read back) are reported beside them.
     n, nnzA = A.nrows, A.nnz
     nnzC = infos[0]["nnzC"]
     s = dom_val_bytes
@@ -303,11 +322,14 @@ def run_stc(args):
                   + 8 * (n + 1) + (4 + s) * nnzC)
     num_ms = statistics.mean(i["numeric_ms"] for i in infos)
     hbm, peak_kind = peaks()
-    achieved = compulsory / (num_ms / 1e3) / 1e9
-    # the fp64 numeric phase is bound by the FP64 pipe: one DMUL and one DADD (the
-    # shared-memory atomic add) per product
-    fp64_tflops = 2 * nprod_of(A) / (num_ms / 1e3) / 1e12
-    gather_model = csr_bytes(n, nnzA, s) + 8 * nnzA + (4 + s) * products(A) + csr_bytes(n, nnzC, s)
+    gbytes = gustavson_bytes(A, A, nnzC, s)
+    achieved = gbytes / (num_ms / 1e3) / 1e9
+    if wl["scale"]:
+        sp_ms = statistics.mean(sum(i["phases64"][:5]) for i in infos)
+    else:
+        sp_ms = statistics.mean(i["spgemm_ms"] for i in infos)
+    # fp64 instruction rate of the numeric phase (one DFMA per product), informational
+    dfma_per_s = nprod_of(A) / (num_ms / 1e3)
 
     # end to end: host (pinned) inputs -> device -> the same step -> results back to host
     e2e = None
@@ -329,6 +351,8 @@ def run_stc(args):
             forms["spmm_e1"] = measure_spmm_e1(stc, H)
         if "mlp" in want:
             forms["mlp_forward"] = measure_mlp(stc, H)
+        if "er4096" in want:
+            forms["er4096"] = measure_er4096(stc, H)
         if "batched" in want:
             forms["batched_vs_per_call"] = measure_batched(stc, H)
         if "mfbc" in want:
@@ -347,20 +371,20 @@ def run_stc(args):
                        "n": A.nrows, "nnz": A.nnz, "nnzC": nnzC, "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "flushed between timed steps (write of 2x L2)",
                        "ops_per_step": ops_total // args.steps},
-            "roofline": ({"bound": "alu", "achieved": fp64_tflops, "peak": FP64_FMA_PEAK_TFLOPS,
-                          "unit": "TFLOP/s", "frac": fp64_tflops / FP64_FMA_PEAK_TFLOPS,
-                          "traffic": (NUMERIC_FP64_DRAM_BYTES_PER_ENTRY * nnzC
-                                      if NUMERIC_FP64_DRAM_BYTES_PER_ENTRY else None),
-                          "traffic_note": "ncu capture at R-MAT scale 16 scaled by nnz(C)",
-                          "kernel": "k_numeric_rank + k_copy_rows (fp64 SpGEMM numeric phase)",
-                          "peak_source": "derived: 2 DFMA/clk/SM x 2 flops x 148 SMs x 2032 MHz",
-                          "algorithmic_flops": 2 * nprod_of(A), "kernel_ms": num_ms,
-                          "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                                  "peak_source": peak_kind, "algorithmic_bytes": compulsory},
-                          "gather_model_bytes": gather_model} if wl["scale"] else
-                         {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                          "frac": achieved / hbm, "traffic": None, "kernel": "k_numeric_rank (int32)",
-                          "peak_source": peak_kind, "algorithmic_bytes": compulsory, "kernel_ms": num_ms}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                         if peak_kind == "measured" else "fallback 6.4 TB/s",
+                         "traffic": (NUMERIC_FP64_DRAM_BYTES_PER_ENTRY * nnzC
+                                     if (NUMERIC_FP64_DRAM_BYTES_PER_ENTRY and wl["scale"]) else None),
+                         "traffic_note": "ncu DRAM bytes of the numeric kernel at R-MAT scale 16 scaled by nnz(C)",
+                         "kernel": ("k_numeric_rank + k_copy_rows (numeric phase of the fp64 SpGEMM)"
+                                    if wl["scale"] else "numeric phase of the (min,+) int32 SpGEMM"),
+                         "kernel_ms": num_ms, "algorithmic_bytes": gbytes,
+                         "bytes_model": "|A| + sum over stored A_ik of (8 + nnz(B_k)(4+s)) + |C|",
+                         "whole_spgemm": {"ms": sp_ms, "frac": gbytes / (sp_ms / 1e3) / 1e9 / hbm},
+                         "compulsory": {"bytes": compulsory,
+                                        "frac": compulsory / (num_ms / 1e3) / 1e9 / hbm},
+                         "fp64_dfma_per_s": dfma_per_s if wl["scale"] else None},
             "gpu_launches": launches,
             "tuning": tuning,
             "clocks": clk.summary(),
@@ -451,6 +475,15 @@ def measure_learned(stc, H, wl, dev):
             torch.cuda.empty_cache()
         res["model_stats"] = stats.get("model")
         res["upper_bound_stats"] = stats.get("upper_bound")
+        nnzC = (stats.get("model") or {}).get("nnz")
+        if nnzC:
+            hbm, peak_kind = peaks()
+            gb = gustavson_bytes(A, A, int(nnzC), 4)
+            res["roofline"] = {"bound": "hbm", "algorithmic_bytes": gb, "unit": "GB/s", "peak": hbm,
+                               "peak_source": peak_kind}
+            for key in ("plain", "learned", "upper_bound"):
+                if res.get(key + "_ms"):
+                    res["roofline"][key + "_frac"] = gb / (res[key + "_ms"] / 1e3) / 1e9 / hbm
         out[name] = res
         del d32
         torch.cuda.empty_cache()
@@ -583,13 +616,22 @@ def measure_spmm_e1(stc, H, n=16384, k=8192, densities=(0.01, 0.16)):
 
 
 def measure_batched(stc, H):
-    """4096 independent (+,x) fp32 pairs: one batched call vs one call per pair."""
+    """4096 independent (+,x) fp32 pairs: one batched call vs one call per pair.
+    Roofline: the row-wise traffic model summed over the pairs (gustavson_bytes)
+    over the batched call's time, against the measured HBM bandwidth."""
     import torch
     sizes, As, Bs = W.powerlaw_batch(4096, 64, 16384, 2.1, 4, 64, seed=0)
     dA = [stc.DeviceCsr.from_host(a.nrows, a.ncols, a.rowptr, a.col, a.val) for a in As]
     dB = [stc.DeviceCsr.from_host(b.nrows, b.ncols, b.rowptr, b.col, b.val) for b in Bs]
     nprod = sum(int(np.diff(b.rowptr)[a.col].sum()) for a, b in zip(As, Bs))
-    t_b = _timed(lambda: H.spgemm_batched(stc.PLUS_TIMES_F32, dA, dB), 3)
+    nnz = {}
+
+    def batched():
+        Cs = H.spgemm_batched(stc.PLUS_TIMES_F32, dA, dB)
+        nnz["c"] = [c.nnz for c in Cs]
+    t_b = _timed(batched, 3)
+    gbytes = sum(gustavson_bytes(a, b, c, 4) for a, b, c in zip(As, Bs, nnz["c"]))
+    hbm, peak_kind = peaks()
 
     def per_call():
         for a, b in zip(dA, dB):
@@ -597,8 +639,43 @@ def measure_batched(stc, H):
     t_p = _timed(per_call, 1)
     torch.cuda.empty_cache()
     return {"unit": UNIT, "workload": "4096 pairs, rows power-law [64,16384] exp 2.1, U{4..64}/row, N(0,1) fp32",
-            "products": nprod, "batched": nprod / t_b, "per_call": nprod / t_p,
-            "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p}}
+            "products": nprod, "nnzC": sum(nnz["c"]), "batched": nprod / t_b, "per_call": nprod / t_p,
+            "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p},
+            "roofline": {"bound": "hbm", "algorithmic_bytes": gbytes, "achieved": gbytes / t_b / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": gbytes / t_b / 1e9 / hbm, "peak_source": peak_kind,
+                         "time": "whole batched call (wall clock, device synchronised)"}}
+
+
+def measure_er4096(stc, H, reps=20):
+    """The small (min,+) int32 case: C = A (x) A for an Erdos-Renyi digraph on 4096
+    vertices with exactly 8 distinct uniform columns per row, weights U[1,1000]
+    (seed 0); plain two-pass call, wall clock per call and the numeric phase from the
+    library's events, each against the row-wise traffic model."""
+    import torch
+    A = W.er_fixed_degree(4096, 8, seed=0)
+    A.val = W.weights_int(A.nnz, 1, 1000, seed=0)
+    d = stc.DeviceCsr.from_host(A.nrows, A.ncols, A.rowptr, A.col, A.val)
+    nprod = products(A)
+    for _ in range(3):
+        C = H.spgemm(stc.MIN_PLUS_I32, d, d)
+    nnzC = C.nnz
+    t = _timed(lambda: H.spgemm(stc.MIN_PLUS_I32, d, d), reps)
+    H.set_timing(True)
+    ph = []
+    for _ in range(reps):
+        H.spgemm(stc.MIN_PLUS_I32, d, d)
+        ph.append(H.phase_times())
+    H.set_timing(False)
+    num_ms = statistics.median(p[4] for p in ph)
+    gbytes = gustavson_bytes(A, A, nnzC, 4)
+    hbm, peak_kind = peaks()
+    torch.cuda.empty_cache()
+    return {"unit": UNIT, "workload": "er4096: (min,+) int32 A(x)A, 8 distinct columns per row, U[1,1000]",
+            "products": nprod, "nnzC": nnzC, "ms": 1e3 * t, "value": nprod / t, "numeric_ms": num_ms,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": gbytes, "unit": "GB/s", "peak": hbm,
+                         "peak_source": peak_kind, "call_frac": gbytes / t / 1e9 / hbm,
+                         "numeric_frac": gbytes / (num_ms / 1e3) / 1e9 / hbm,
+                         "note": "4.7 MB of traffic: launch- and latency-bound at any speed"}}
 
 
 def measure_bf_drivers(stc, H, wl):
@@ -630,6 +707,12 @@ def measure_mfbc(stc, H, scale=22, nsrc=4096, batch=256):
         t = _timed(lambda: H.mfbc(d, src, batch=batch), 1)
         out[name] = len(src) * G.nnz / t / 1e9
         out[name + "_ms"] = 1e3 * t
+        hbm, peak_kind = peaks()
+        gb = MFBC_BYTES_PER_TRAVERSAL * 2 * len(src) * G.nnz
+        out[name + "_roofline"] = {"bound": "hbm", "algorithmic_bytes": gb, "unit": "GB/s",
+                                   "achieved": gb / t / 1e9, "peak": hbm, "frac": gb / t / 1e9 / hbm,
+                                   "peak_source": peak_kind,
+                                   "model": f"{MFBC_BYTES_PER_TRAVERSAL} B per (edge, source), forward and backward"}
         one = src[:batch]
         for drv in ("graph", "host"):
             H.set_round_driver(drv)
@@ -730,7 +813,7 @@ def main():
                     help="rmat<scale> (the R-MAT step; rmat18 is the benchmark) or er4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the light-row autotuning before the warm-up")
-    ap.add_argument("--forms", default="bf,learned,masked,apsp,spmm,mlp,batched,mfbc",
+    ap.add_argument("--forms", default="bf,er4096,learned,masked,apsp,spmm,mlp,batched,mfbc",
                     help="comma-separated subset of the comparison forms to run after the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mfbc-scale", type=int, default=22, help="R-MAT scale of the mfbc form")
