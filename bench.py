@@ -628,9 +628,9 @@ def measure_batched(stc, H):
 
     def batched():
         Cs = H.spgemm_batched(stc.PLUS_TIMES_F32, dA, dB)
-        nnz["c"] = [c.nnz for c in Cs]
+        nnz["c"] = Cs._nnz
     t_b = _timed(batched, 3)
-    gbytes = sum(gustavson_bytes(a, b, c, 4) for a, b, c in zip(As, Bs, nnz["c"]))
+    gbytes = sum(gustavson_bytes(a, b, int(c), 4) for a, b, c in zip(As, Bs, nnz["c"]))
     hbm, peak_kind = peaks()
 
     def per_call():
@@ -639,7 +639,7 @@ def measure_batched(stc, H):
     t_p = _timed(per_call, 1)
     torch.cuda.empty_cache()
     return {"unit": UNIT, "workload": "4096 pairs, rows power-law [64,16384] exp 2.1, U{4..64}/row, N(0,1) fp32",
-            "products": nprod, "nnzC": sum(nnz["c"]), "batched": nprod / t_b, "per_call": nprod / t_p,
+            "products": nprod, "nnzC": int(nnz["c"].sum()), "batched": nprod / t_b, "per_call": nprod / t_p,
             "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p},
             "roofline": {"bound": "hbm", "algorithmic_bytes": gbytes, "achieved": gbytes / t_b / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": gbytes / t_b / 1e9 / hbm, "peak_source": peak_kind,
@@ -688,6 +688,20 @@ def measure_bf_drivers(stc, H, wl):
     for name, mode in (("host_loop", 0), ("persistent", 1), ("cuda_graph", 2)):
         H.bellman_ford(stc.MIN_PLUS_F32, dg, 0, persistent=mode)  # warm
         out[name] = 1e3 * _timed(lambda: H.bellman_ford(stc.MIN_PLUS_F32, dg, 0, persistent=mode), 5)
+    # many short calls: R-MAT 14, 1000 sources one call each (the graph is
+    # instantiated once per handle and reused; each call rewrites its parameters)
+    G = W.rmat(14, seed=0)
+    d14 = stc.DeviceCsr.from_host(G.nrows, G.ncols, G.rowptr, G.col, W.weights_unit01(G.nnz, seed=1).astype(np.float32))
+    srcs = W.sample_sources(G, 1000, seed=0)
+    short = {"workload": "rmat14 (min,+) fp32, 1000 calls from sampled sources", "unit": "ms per call"}
+    for name, mode in (("host_loop", 0), ("persistent", 1), ("cuda_graph", 2)):
+        H.bellman_ford(stc.MIN_PLUS_F32, d14, int(srcs[0]), persistent=mode)
+
+        def many():
+            for v in srcs:
+                H.bellman_ford(stc.MIN_PLUS_F32, d14, int(v), persistent=mode)
+        short[name] = 1e3 * _timed(many, 1) / len(srcs)
+    out["short_calls"] = short
     return out
 
 

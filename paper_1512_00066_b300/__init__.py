@@ -253,6 +253,53 @@ def values_to_device(val: np.ndarray, device="cuda") -> torch.Tensor:
     return torch.from_numpy(a).to(device)
 
 
+class BatchedResult:
+    """The results of one batched call: C_b as DeviceCsr views into the three
+    shared allocations, made on first access (the offsets come from the
+    descriptors the library filled in)."""
+
+    def __init__(self, alg, C, rp, col, raw):
+        nb = len(C)
+        desc = np.frombuffer(memoryview(C).cast("B"), dtype=np.int64).reshape(nb, 6)
+        self._alg = alg
+        self._nrows = desc[:, 0].copy()
+        self._ncols = desc[:, 1].copy()
+        self._nnz = desc[:, 2].copy()
+        self._r0 = (desc[:, 3] - desc[0, 3]) // 8
+        self._c0 = (desc[:, 4] - desc[0, 4]) // 4
+        self._rp, self._col, self._raw = rp, col, raw
+        ct = _DT[alg][2]
+        self._vb = DSIG_BYTES if ct == "dsig" else torch.empty(0, dtype=ct).element_size()
+        self._cache = {}
+
+    def __len__(self):
+        return self._nrows.size
+
+    @property
+    def nnz_total(self) -> int:
+        return int(self._nnz.sum())
+
+    def __getitem__(self, b):
+        if isinstance(b, slice):
+            return [self[i] for i in range(*b.indices(len(self)))]
+        b = int(b) + (len(self) if b < 0 else 0)
+        if not 0 <= b < len(self):
+            raise IndexError(b)
+        v = self._cache.get(b)
+        if v is None:
+            nnz, r0, c0, n = int(self._nnz[b]), int(self._r0[b]), int(self._c0[b]), int(self._nrows[b])
+            ct = _DT[self._alg][2]
+            raw = self._raw[c0 * self._vb: (c0 + nnz) * self._vb]
+            val = raw.view(nnz, DSIG_BYTES) if ct == "dsig" else raw.view(ct)
+            v = self._cache[b] = DeviceCsr(n, int(self._ncols[b]), self._rp[r0: r0 + n + 1],
+                                           self._col[c0: c0 + nnz], val)
+        return v
+
+    def __iter__(self):
+        for b in range(len(self)):
+            yield self[b]
+
+
 # ----------------------------------------------------------------- handle
 
 class Handle:
@@ -371,8 +418,9 @@ class Handle:
     def spgemm_batched(self, alg: int, As, Bs, skip_validation: bool = False, light_rows: int = 0, stream=None):
         """C_b = A_b (x) B_b for every pair, in one batched call (one synchronisation).
 
-        Returns a list of DeviceCsr whose tensors are views into three shared
-        allocations (row pointers, columns, values) owned by the first result.
+        Returns a sequence of DeviceCsr (BatchedResult) whose tensors are views into
+        three shared allocations (row pointers, columns, values); the views are
+        made when an element is first read.
         """
         nb = len(As)
         assert nb == len(Bs) and nb > 0
@@ -385,19 +433,7 @@ class Handle:
         rp = self._take(C[0].rowptr).view(torch.int64)
         col = self._take(C[0].col).view(torch.int32)
         raw = self._take(C[0].val)
-        ct = _DT[alg][2]
-        vb = DSIG_BYTES if ct == "dsig" else torch.empty(0, dtype=ct).element_size()
-        out = []
-        for b in range(nb):
-            r0 = (C[b].rowptr - C[0].rowptr) // 8
-            c0 = (C[b].col - C[0].col) // 4
-            nnz = int(C[b].nnz)
-            rowptr = rp[r0: r0 + int(C[b].nrows) + 1]
-            cols = col[c0: c0 + nnz]
-            v = raw[c0 * vb: (c0 + nnz) * vb]
-            val = v.view(nnz, DSIG_BYTES) if ct == "dsig" else v.view(ct)
-            out.append(DeviceCsr(int(C[b].nrows), int(C[b].ncols), rowptr, cols, val))
-        return out
+        return BatchedResult(alg, C, rp, col, raw)
 
     def spmm(self, alg: int, A: DeviceCsr, X: torch.Tensor, Y: Optional[torch.Tensor] = None,
              accumulate: bool = False, stream=None) -> torch.Tensor:

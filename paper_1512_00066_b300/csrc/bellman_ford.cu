@@ -177,11 +177,21 @@ __global__ void __launch_bounds__(BF_NT) k_bf_persistent(BfArgs a, typename BfT<
     if (blockIdx.x == 0 && threadIdx.x == 0) *rounds_out = changed_rounds;
 }
 
-// Graph form: the round index lives on the device; the body of a conditional
-// WHILE node runs this kernel then k_bf_check.
+// Arguments of the cached graph's kernels, read from the handle's device
+// parameter block (rewritten by every call before the graph is launched).
+struct BfGraphParams {
+    BfArgs a;
+    void* dist;
+    int* d_round;
+    int* d_changed;
+};
+
 template <int ALG>
-__global__ void __launch_bounds__(BF_NT) k_bf_round_dev(BfArgs a, typename BfT<ALG>::D* dist, const int* d_round) {
-    const int r = *d_round;
+__global__ void __launch_bounds__(BF_NT) k_bf_round_g(const BfGraphParams* __restrict__ p) {
+    using D = typename BfT<ALG>::D;
+    const BfArgs a = p->a;
+    D* dist = static_cast<D*>(p->dist);
+    const int r = *p->d_round;
     const int ncur = a.cnt[r % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt[(r + 2) % 3] = 0;
     relax_round<ALG>(a, dist, r, a.frontier[r & 1], ncur, a.frontier[(r + 1) & 1], &a.cnt[(r + 1) % 3]);
@@ -190,21 +200,76 @@ __global__ void __launch_bounds__(BF_NT) k_bf_round_dev(BfArgs a, typename BfT<A
 // Termination test of the graph form (one thread): stop when the round produced
 // an empty frontier, or flag a negative cycle when |V| rounds all changed
 // something; otherwise advance the round and run the body again.
-__global__ void k_bf_check(BfArgs a, int* d_round, int* d_changed, int* flags, cudaGraphConditionalHandle loop) {
-    const int r = *d_round;
+__global__ void k_bf_check_g(const BfGraphParams* __restrict__ p, int* flags, cudaGraphConditionalHandle loop) {
+    const BfArgs a = p->a;
+    const int r = *p->d_round;
     const int nnext = a.cnt[(r + 1) % 3];
     unsigned go = 0;
     if (nnext > 0) {
-        const int changed = *d_changed + 1;
-        *d_changed = changed;
+        const int changed = *p->d_changed + 1;
+        *p->d_changed = changed;
         if (int64_t(changed) >= a.n) {
             atomicOr(flags, STC_FLAG_NEG_CYCLE);
         } else {
-            *d_round = r + 1;
+            *p->d_round = r + 1;
             go = 1;
         }
     }
     cudaGraphSetConditional(loop, go);
+}
+
+// The cached graph of algebra ALG: WHILE{k_bf_round_g -> k_bf_check_g}, built and
+// instantiated once per handle; its kernel arguments are the parameter block.
+template <int ALG>
+cudaError_t bf_graph_exec(stc_handle* h, cudaGraphExec_t* out) {
+    const int idx = ALG == ALG_MP_I32 ? 0 : 1;
+    if (h->bf_exec[idx]) {
+        *out = h->bf_exec[idx];
+        return cudaSuccess;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    do {
+        if (e != cudaSuccess) break;
+        cudaGraphConditionalHandle loop;
+        if ((e = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode, n1, n2;
+        if ((e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        const BfGraphParams* params = static_cast<const BfGraphParams*>(h->d_params);
+        int* flags = h->d_flags;
+        void* round_args[] = {&params};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)k_bf_round_g<ALG>;
+        kp.gridDim = dim3(h->num_sms * 4);
+        kp.blockDim = dim3(BF_NT);
+        kp.kernelParams = round_args;
+        if ((e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp)) != cudaSuccess) break;
+        void* check_args[] = {&params, &flags, &loop};
+        cudaKernelNodeParams kc = {};
+        kc.func = (void*)k_bf_check_g;
+        kc.gridDim = dim3(1);
+        kc.blockDim = dim3(1);
+        kc.kernelParams = check_args;
+        if ((e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kc)) != cudaSuccess) break;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+    } while (0);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        return e;
+    }
+    h->bf_graph[idx] = graph;
+    h->bf_exec[idx] = exec;
+    *out = exec;
+    return cudaSuccess;
 }
 
 template <int ALG>
@@ -268,61 +333,26 @@ stc_status run_bf(stc_handle* h, const stc_csr* G, int32_t source, void* dist_ou
         STC_CUDA_TRY(cudaStreamSynchronize(s));
         rounds = reinterpret_cast<int*>(&h->h_stage[0])[0];
     } else if (persistent == 2) {
-        // graph form: one CUDA graph whose conditional WHILE node repeats {round, check}
+        // graph form: the handle's cached graph (conditional WHILE node repeating
+        // {round, check}); this call's arguments go to its parameter block first
+        static_assert(sizeof(BfGraphParams) <= STC_PARAM_BYTES, "parameter block");
         int* d_round = ints + 10;
         int* d_changed = ints + 11;
-        int* flags = h->d_flags;
-        cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        stc_status gst = STC_OK;
-        do {
-            if (cudaGraphCreate(&graph, 0) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
-            cudaGraphConditionalHandle loop;
-            if (cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-                gst = STC_ERR_CUDA;
-                break;
-            }
-            cudaGraphNodeParams cp = {};
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = loop;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t cnode;
-            if (cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            void* round_args[] = {&a, &dist, &d_round};
-            cudaKernelNodeParams kp = {};
-            kp.func = (void*)k_bf_round_dev<ALG>;
-            kp.gridDim = dim3(h->num_sms * 4);
-            kp.blockDim = dim3(BF_NT);
-            kp.kernelParams = round_args;
-            cudaGraphNode_t n1, n2;
-            if (cudaGraphAddKernelNode(&n1, body, nullptr, 0, &kp) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
-            void* check_args[] = {&a, &d_round, &d_changed, &flags, &loop};
-            cudaKernelNodeParams kc = {};
-            kc.func = (void*)k_bf_check;
-            kc.gridDim = dim3(1);
-            kc.blockDim = dim3(1);
-            kc.kernelParams = check_args;
-            if (cudaGraphAddKernelNode(&n2, body, &n1, 1, &kc) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
-            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
-            if (cudaGraphLaunch(exec, s) != cudaSuccess) { gst = STC_ERR_CUDA; break; }
-            stc_count(h, 2);  // the body's two kernels (repeated on the device)
-        } while (0);
-        if (gst != STC_OK) {
-            (void)cudaGetLastError();
-            if (exec) cudaGraphExecDestroy(exec);
-            if (graph) cudaGraphDestroy(graph);
-            return gst;
-        }
+        STC_CUDA_TRY(bf_graph_exec<ALG>(h, &exec));
+        BfGraphParams* hp = static_cast<BfGraphParams*>(h->h_params);
+        hp->a = a;
+        hp->dist = dist;
+        hp->d_round = d_round;
+        hp->d_changed = d_changed;
+        STC_CUDA_TRY(cudaMemcpyAsync(h->d_params, hp, sizeof(BfGraphParams), cudaMemcpyHostToDevice, s));
+        STC_CUDA_TRY(cudaGraphLaunch(exec, s));
+        stc_count(h, 2);  // the body's two kernels (repeated on the device)
         stc_mark(h, s, 2);
         STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[0], d_changed, sizeof(int), cudaMemcpyDeviceToHost, s));
         STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[1], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
         STC_CUDA_TRY(cudaMemcpyAsync(&h->h_stage[2], a.relax, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        const cudaError_t se = cudaStreamSynchronize(s);
-        cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        STC_CUDA_TRY(se);
+        STC_CUDA_TRY(cudaStreamSynchronize(s));
         rounds = reinterpret_cast<int*>(&h->h_stage[0])[0];
     } else {
         // plain form: one launch per round, frontier size read back each round

@@ -96,12 +96,27 @@ __global__ void __launch_bounds__(256) k_features(int64_t nA, int64_t K, int64_t
             ub += __shfl_down_sync(0xffffffffu, ub, o);
             mx = max(mx, (int64_t)__shfl_down_sync(0xffffffffu, mx, o));
         }
+        // bucket-wise minimum over the row's B sketches: 32 entries of A at a time
+        // (lane j reads entry j), then eight sketch loads in flight per lane
         unsigned long long m = EMPTY;
-        for (int64_t p = lo; p < hi; ++p) {
-            const int32_t k = a_col[p];
-            if ((uint64_t)k >= (uint64_t)K) continue;
-            const unsigned long long v = sketch[int64_t(k) * 32 + lane];
-            m = v < m ? v : m;
+        for (int64_t p0 = lo; p0 < hi; p0 += 32) {
+            const int64_t p = p0 + lane;
+            int32_t kl = -1;
+            if (p < hi) {
+                const int32_t k = a_col[p];
+                if ((uint64_t)k < (uint64_t)K) kl = k;
+            }
+            const int nk = int(hi - p0 < 32 ? hi - p0 : 32);
+            for (int t0 = 0; t0 < nk; t0 += 8) {
+                unsigned long long v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = __shfl_sync(0xffffffffu, kl, (t0 + u) & 31);
+                    v[u] = (t0 + u < nk && k >= 0) ? sketch[int64_t(k) * 32 + lane] : EMPTY;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) m = v[u] < m ? v[u] : m;
+            }
         }
         float* f = feat + i * NFP;
         if (lane == 0) {

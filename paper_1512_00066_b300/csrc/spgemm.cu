@@ -686,7 +686,7 @@ __device__ __forceinline__ void walk_tasks(const SpgArgs& g, TaskSmem<NT>& ts, i
 // Symbolic walk: set the bitmap bit of every product's column.  All the task's
 // bitmap reads are issued before its atomics (a read after an atomic would wait
 // for it), and the summary bits are derived from the bitmap afterwards.
-template <int NT, int SUB = RK_SUB>
+template <int NT, int SUB = RK_SUB, int STRIDE = 1>
 __device__ __forceinline__ void walk_tasks_bits(const SpgArgs& g, TaskSmem<NT>& ts, int ntasks,
                                                 uint32_t* bits) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -711,12 +711,12 @@ __device__ __forceinline__ void walk_tasks_bits(const SpgArgs& g, TaskSmem<NT>& 
         uint32_t cur[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            cur[u] = (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) ? bits[col[u] >> 5] : ~0u;
+            cur[u] = (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) ? bits[(col[u] >> 5) * STRIDE] : ~0u;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (u < nu && (uint64_t)col[u] < (uint64_t)g.ncols) {
                 const uint32_t m = 1u << (col[u] & 31);
-                if (!(cur[u] & m)) atomicOr(&bits[col[u] >> 5], m);
+                if (!(cur[u] & m)) atomicOr(&bits[(col[u] >> 5) * STRIDE], m);
             }
         }
         t = __shfl_sync(0xffffffffu, nt, 0);
@@ -775,15 +775,6 @@ __device__ __forceinline__ void walk_tasks_rank(const SpgArgs& g, TaskSmem<NT>& 
 //                 the output row) of the word's first present column
 //   summ[ncell]   bit w%32 of summ[w/32] set when word w is non-zero
 //   cellbase[ncell+1]  rank of the first present column of each 1024-column cell
-__device__ __forceinline__ void set_bit2(uint32_t* wbx, uint32_t* summ, int col) {
-    const int w = col >> 5;
-    const uint32_t m = 1u << (col & 31);
-    if (!(wbx[2 * w] & m)) {
-        uint32_t old = atomicOr(&wbx[2 * w], m);
-        if (old == 0u) atomicOr(&summ[w >> 5], 1u << (w & 31));
-    }
-}
-
 struct RankLayout {
     size_t wb, summ, cellbase, winfirst, vals, scol, sig, total;
 };
@@ -1053,7 +1044,7 @@ __global__ void k_cell_offsets(SpgRows R) {
 // null, a row with one stored entry whose B row is not empty goes to BIN_COPY and
 // its output count is final: single[gi] = ub (one product per output column).
 __global__ void k_row_ub_b(SpgRows R, int64_t NR, int64_t* __restrict__ ub, int* __restrict__ bin_count,
-                           int64_t* __restrict__ single) {
+                           int64_t* __restrict__ single, int32_t* __restrict__ row_mat = nullptr) {
     __shared__ int s_bins[NBINS_ALL];
     for (int t = threadIdx.x; t < NBINS_ALL; t += blockDim.x) s_bins[t] = 0;
     __syncthreads();
@@ -1067,6 +1058,7 @@ __global__ void k_row_ub_b(SpgRows R, int64_t NR, int64_t* __restrict__ ub, int*
             const int b = batch_of(R, gi);
             g = R.table[b];
             i = gi - R.row_off[b];
+            if (row_mat && lane == 0) row_mat[gi] = b;
         } else {
             g = R.one;
         }
@@ -1132,6 +1124,316 @@ __global__ void __launch_bounds__(256) k_copy_rows(SpgRows R, const int32_t* __r
         for (int64_t e = bl + lane; e < bh; e += 32) {
             c_col[o0 + e] = g.b_col[e] + g.col_base;
             cval[o0 + e] = T::one(a, bval[e]);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- warp-per-row kernels
+//
+// Narrow outputs (at most WR_MAX_COLS columns, e.g. many small independent
+// products): one warp owns one output row, with its own slice of shared memory and
+// no CTA barrier.  The products of a row are walked flattened: 32 stored entries
+// A_ik at a time, lane j holds entry j and its B row; an inclusive warp scan of the
+// B row lengths numbers the chunk's products 0..T-1, and product q belongs to the
+// first lane whose prefix exceeds q (a five-step shuffle search), so every lane
+// works on a product whatever the B row lengths are.  Rows are claimed from a
+// device counter, heaviest first (the order of the row list).
+//
+//   count pass:   bitmap of the row's columns (one bit per output column), popcount
+//   numeric pass: the same bitmap, the rank of every 32-column word (prefix of
+//                 popcounts, words owned lane-strided so the prefix is one warp
+//                 scan per 32 words), then every product accumulated into the
+//                 rank-indexed value array with the algebra's (+), columns written
+//                 from the bitmap and values by rank, both coalesced.
+
+constexpr int WR_MAX_COLS = 16384;
+constexpr int WR_WORDS = WR_MAX_COLS / 32;  // 512 bitmap words per warp
+constexpr int WR_ROUNDS = WR_WORDS / 32;    // 16 words per lane
+constexpr int WR_U = 8;                     // products per lane in flight per step
+constexpr int WR_VCAP = 2560;               // value slots per warp of the wide numeric instance
+constexpr int WR_VCAP_S = 1024;             // value slots per warp of the narrow numeric instance
+constexpr int WR_UB_LOG2 = 15;              // rows with 2^15 products or more stay on the CTA kernels
+constexpr int WR_COUNT_WARPS = 8;           // warps per CTA of the count pass
+constexpr int WR_NUM_WARPS = 4;             // warps per CTA of the wide numeric instance
+constexpr int WR_NUM_WARPS_S = 8;           // warps per CTA of the narrow numeric instance
+
+template <int ALG, int VCAP>
+__host__ __device__ constexpr size_t wr_warp_bytes() {
+    return size_t(WR_WORDS) * 4 + size_t(WR_WORDS) * 2 + size_t(VCAP) * sizeof(typename Tr<ALG>::Acc);
+}
+
+// Matrix of global row gi: its arguments and its row inside the matrix.
+__device__ __forceinline__ const SpgArgs& wr_args(const SpgRows& R, const int32_t* __restrict__ row_mat,
+                                                  int64_t gi, int64_t& i) {
+    if (!R.table) {
+        i = gi;
+        return R.one;
+    }
+    const int b = row_mat[gi];
+    i = gi - R.row_off[b];
+    return R.table[b];
+}
+
+// Per-warp table of the current chunk of (at most 32) stored entries of A: the
+// end of each entry's product range, the B position of its product q (shift + q)
+// and its value.
+template <class AT>
+struct WrChunk {
+    int end[32];
+    int64_t shift[32];
+    AT aval[32];
+};
+
+// Walk the products of row [alo, ahi) of A: f(col[], bv[], av[]) receives WR_U
+// products per lane per call (col < 0: no product in that slot).  Lane j loads
+// entry j of a 32-entry chunk; an inclusive warp scan of the B row lengths numbers
+// the chunk's products, and every lane follows its products' owners in the chunk
+// table (owners only move forward as q grows, a step or two per 32 products).
+template <bool WITH_VAL, class AT, class BT, class F>
+__device__ __forceinline__ void wr_walk(const SpgArgs& g, int64_t alo, int64_t ahi, int lane, WrChunk<AT>& tab,
+                                        F f) {
+    const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
+    for (int64_t c0 = alo; c0 < ahi; c0 += 32) {
+        const int64_t p = c0 + lane;
+        int len = 0;
+        int64_t base = 0;
+        AT av = AT();
+        if (p < ahi) {
+            const int32_t k = g.a_col[p];
+            if ((uint64_t)k < (uint64_t)g.K) {
+                int64_t bl, bh;
+                row_range(g.b_ptr, k, g.nnzB, bl, bh);
+                len = int(bh - bl);
+                base = bl;
+                if (WITH_VAL) av = static_cast<const AT*>(g.a_val)[p];
+            }
+        }
+        int end = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, end, o);
+            if (lane >= o) end += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, end, 31);
+        __syncwarp();
+        tab.end[lane] = end;
+        tab.shift[lane] = base - (end - len);  // B position of product q of this entry: shift + q
+        if (WITH_VAL) tab.aval[lane] = av;
+        __syncwarp();
+        int own = 0;
+        for (int q0 = 0; q0 < total; q0 += 32 * WR_U) {
+            int col[WR_U];
+            BT bv[WR_U];
+            AT aa[WR_U];
+#pragma unroll
+            for (int u = 0; u < WR_U; ++u) {
+                col[u] = -1;
+                const int q = q0 + u * 32 + lane;
+                if (q < total) {
+                    while (tab.end[own] <= q) ++own;  // q < total = end[31]: stops at 31 at the latest
+                    const int64_t pos = tab.shift[own] + q;
+                    col[u] = g.b_col[pos];
+                    if (WITH_VAL) {
+                        bv[u] = bval[pos];
+                        aa[u] = tab.aval[own];
+                    }
+                }
+            }
+            f(col, bv, aa);
+        }
+    }
+}
+
+// Set the bitmap bit of every product's column (columns outside [0, ncols) are
+// skipped: they can only come from input that validation would reject).
+template <class AT, class BT>
+__device__ __forceinline__ void wr_bits(const SpgArgs& g, int64_t alo, int64_t ahi, int lane, uint32_t* bits,
+                                        WrChunk<AT>& tab) {
+    const unsigned nc = unsigned(g.ncols);
+    wr_walk<false, AT, BT>(g, alo, ahi, lane, tab, [&](const int* col, const BT*, const AT*) {
+        uint32_t cur[WR_U];
+#pragma unroll
+        for (int u = 0; u < WR_U; ++u) cur[u] = unsigned(col[u]) < nc ? bits[col[u] >> 5] : ~0u;
+#pragma unroll
+        for (int u = 0; u < WR_U; ++u) {
+            if (unsigned(col[u]) < nc) {
+                const uint32_t m = 1u << (col[u] & 31);
+                if (!(cur[u] & m)) atomicOr(&bits[col[u] >> 5], m);
+            }
+        }
+    });
+}
+
+// Count pass: row_nnz[gi] = nnz(C_i) for the listed rows [*lo_ptr, *hi_ptr)
+// (lo_ptr NULL: from 0).
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_wr_count(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __restrict__ rowlist,
+           const int* __restrict__ lo_ptr, const int* __restrict__ hi_ptr, int* __restrict__ counter,
+           int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz) {
+    __shared__ uint32_t s_bits[WARPS][WR_WORDS];
+    __shared__ WrChunk<int> s_tab[WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* bits = s_bits[wid];
+#pragma unroll
+    for (int t = 0; t < WR_ROUNDS; ++t) bits[t * 32 + lane] = 0u;
+    __syncwarp();
+    const int first = lo_ptr ? *lo_ptr : 0, last = *hi_ptr;
+    int local_max = 0;
+    for (;;) {
+        int r = 0;
+        if (lane == 0) r = first + atomicAdd(counter, 1);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (r >= last) break;
+        const int64_t gi = rowlist[r];
+        int64_t i;
+        const SpgArgs& g = wr_args(R, row_mat, gi, i);
+        int64_t alo, ahi;
+        row_range(g.a_ptr, i, g.nnzA, alo, ahi);
+        wr_bits<int, int>(g, alo, ahi, lane, bits, s_tab[wid]);
+        __syncwarp();
+        int n = 0;
+#pragma unroll
+        for (int t = 0; t < WR_ROUNDS; ++t) {
+            n += __popc(bits[t * 32 + lane]);
+            bits[t * 32 + lane] = 0u;
+        }
+        n = __reduce_add_sync(0xffffffffu, n);
+        if (lane == 0) row_nnz[gi] = n;
+        local_max = max(local_max, n);
+        __syncwarp();
+    }
+    if (lane == 0 && local_max) atomicMax(max_nnz, local_max);
+}
+
+// Numeric pass over the listed rows [0, *nlist), every one with at most VCAP
+// output entries: C_i written at c_ptr[gi] (columns ascending).  A row whose
+// count differs from its slot raises STC_FLAG_INTERNAL and is not written.
+template <int ALG, int WARPS, int VCAP>
+__global__ void __launch_bounds__(WARPS * 32)
+k_wr_numeric(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __restrict__ rowlist,
+             const int* __restrict__ nlist_ptr, int* __restrict__ counter, const int64_t* __restrict__ c_ptr,
+             int32_t* __restrict__ c_col, void* __restrict__ c_val, int* __restrict__ flags) {
+    static_assert(VCAP <= 65535 && WR_MAX_COLS <= 65535, "ranks are kept in 16 bits");
+    using T = Tr<ALG>;
+    using AT = typename T::A;
+    using BT = typename T::B;
+    using Acc = typename T::Acc;
+    extern __shared__ uint4 smem_raw[];
+    __shared__ WrChunk<AT> s_tab[WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char* base = reinterpret_cast<unsigned char*>(smem_raw) + size_t(wid) * wr_warp_bytes<ALG, VCAP>();
+    uint32_t* bits = reinterpret_cast<uint32_t*>(base);
+    uint16_t* wpre = reinterpret_cast<uint16_t*>(base + WR_WORDS * 4);
+    Acc* vals = reinterpret_cast<Acc*>(base + WR_WORDS * 6);
+#pragma unroll
+    for (int t = 0; t < WR_ROUNDS; ++t) bits[t * 32 + lane] = 0u;
+    for (int r = lane; r < VCAP; r += 32) vals[r] = T::empty();
+    __syncwarp();
+    auto* cval = static_cast<typename T::C*>(c_val);
+    const int nlist = *nlist_ptr;
+    for (;;) {
+        int r = 0;
+        if (lane == 0) r = atomicAdd(counter, 1);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (r >= nlist) break;
+        const int64_t gi = rowlist[r];
+        int64_t i;
+        const SpgArgs& g = wr_args(R, row_mat, gi, i);
+        int64_t alo, ahi;
+        row_range(g.a_ptr, i, g.nnzA, alo, ahi);
+        const int64_t o0 = c_ptr[gi];
+        const int64_t want = c_ptr[gi + 1] - o0;
+        // 1) bitmap
+        wr_bits<AT, BT>(g, alo, ahi, lane, bits, s_tab[wid]);
+        __syncwarp();
+        // 2) ranks: words owned lane-strided, one warp scan per round of 32 words
+        int run = 0;
+#pragma unroll
+        for (int t = 0; t < WR_ROUNDS; ++t) {
+            const int c = __popc(bits[t * 32 + lane]);
+            int x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            wpre[t * 32 + lane] = uint16_t(run + x - c);
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        const int count = run;
+        const bool ok = count == want && count <= VCAP;
+        if (!ok && lane == 0) atomicOr(flags, STC_FLAG_INTERNAL);
+        __syncwarp();
+        if (ok) {
+            // 3) values by rank
+            const unsigned nc = unsigned(g.ncols);
+            wr_walk<true, AT, BT>(g, alo, ahi, lane, s_tab[wid], [&](const int* col, const BT* bv, const AT* av) {
+                int rk[WR_U];
+#pragma unroll
+                for (int u = 0; u < WR_U; ++u) {
+                    rk[u] = -1;
+                    if (unsigned(col[u]) < nc) {
+                        const int w = col[u] >> 5;
+                        rk[u] = int(wpre[w]) + __popc(bits[w] & ((1u << (col[u] & 31)) - 1u));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < WR_U; ++u)
+                    if (rk[u] >= 0) T::combine(vals, rk[u], av[u], bv[u]);
+            });
+            __syncwarp();
+            // 4) columns from the bitmap (each lane's word covers ranks wpre[w] ..)
+#pragma unroll 1
+            for (int t = 0; t < WR_ROUNDS; ++t) {
+                const int w = t * 32 + lane;
+                uint32_t b = bits[w];
+                int64_t dst = o0 + wpre[w];
+                while (b) {
+                    const int bit = __ffs(b) - 1;
+                    b &= b - 1;
+                    c_col[dst++] = w * 32 + bit + g.col_base;
+                }
+            }
+            for (int q = lane; q < count; q += 32) {
+                cval[o0 + q] = T::out(vals[q]);
+                vals[q] = T::empty();
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < WR_ROUNDS; ++t) bits[t * 32 + lane] = 0u;
+        __syncwarp();
+    }
+}
+
+// Rows of the list [0, *nlist) split for the numeric pass into three lists
+// (order inside a list follows the row list): out[0] rows with at most WR_VCAP_S
+// output entries, out[1] rows with at most WR_VCAP, out[2] the heavy prefix
+// [0, *heavy_ptr) (too many products for one warp) and the rest; n[0..2] sizes.
+__global__ void k_split_by_count(const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
+                                 const int* __restrict__ heavy_ptr, const int64_t* __restrict__ c_ptr,
+                                 int32_t* __restrict__ out0, int32_t* __restrict__ out1, int32_t* __restrict__ out2,
+                                 int* __restrict__ n) {
+    const int nlist = *nlist_ptr, heavy = *heavy_ptr;
+    const int lane = threadIdx.x & 31;
+    for (int r0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; r0 < nlist; r0 += gridDim.x * blockDim.x) {
+        const int r = r0 + lane;
+        int32_t gi = -1;
+        int cls = 3;
+        if (r < nlist) {
+            gi = rowlist[r];
+            const int64_t c = c_ptr[gi + 1] - c_ptr[gi];
+            cls = r < heavy ? 2 : c <= WR_VCAP_S ? 0 : c <= WR_VCAP ? 1 : 2;
+        }
+        const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, cls == k);
+            int b = 0;
+            if (lane == 0 && m) b = atomicAdd(&n[k], __popc(m));
+            b = __shfl_sync(0xffffffffu, b, 0);
+            int32_t* out = k == 0 ? out0 : k == 1 ? out1 : out2;
+            if (cls == k) out[b + __popc(m & below)] = gi;
         }
     }
 }
@@ -1243,12 +1545,19 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                 __syncthreads();
             }
         } else {
-        // 1) bitmap of the row's columns
+        // 1) bitmap of the row's columns (all of a task's word reads before its
+        //    atomics), then the summary bits by one ballot per 32 words
         for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
             const int ntasks = load_tasks<NT, AT, false>(g, nullptr, 0, p0, ahi, 0, 0, ts, nullptr);
-            walk_tasks<NT>(g, ts, ntasks, [&](int64_t, int col, int) {
-                if ((uint64_t)col < (uint64_t)g.ncols) set_bit2(wbx, summ, col);
-            });
+            walk_tasks_bits<NT, RK_SUB, 2>(g, ts, ntasks, wbx);
+            __syncthreads();
+        }
+        {
+            const int lane = threadIdx.x & 31;
+            for (int c = threadIdx.x >> 5; c < ncell; c += NT / 32) {
+                const unsigned m = __ballot_sync(0xffffffffu, wbx[2 * (c * 32 + lane)] != 0u);
+                if (lane == 0) summ[c] = m;
+            }
             __syncthreads();
         }
 
@@ -1533,6 +1842,56 @@ stc_status run_copy_any(stc_handle* h, int alg, const SpgRows& R, const int32_t*
     return STC_OK;
 }
 
+// Algebras of the warp-per-row kernels (the others keep the CTA kernels).
+bool wr_supported(int alg) {
+    return alg == ALG_PT_F32 || alg == ALG_PT_F64 || alg == ALG_MP_I32 || alg == ALG_MP_F32 || alg == ALG_BOOL;
+}
+
+template <int ALG, int WARPS, int VCAP>
+stc_status launch_wr_numeric(stc_handle* h, const SpgRows& R, const int32_t* row_mat, const int32_t* rowlist,
+                             const int* nlist, int* counter, const int64_t* c_ptr, int32_t* c_col, void* c_val,
+                             int64_t NR, stc_stream s) {
+    auto kern = k_wr_numeric<ALG, WARPS, VCAP>;
+    const size_t smem = WARPS * wr_warp_bytes<ALG, VCAP>();
+    STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int per_sm = 0;
+    STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem));
+    if (per_sm < 1) return STC_ERR_CUDA;
+    int64_t grid = int64_t(per_sm) * h->num_sms;
+    if (grid * WARPS > NR) grid = (NR + WARPS - 1) / WARPS;
+    kern<<<unsigned(grid > 0 ? grid : 1), WARPS * 32, smem, s>>>(R, row_mat, rowlist, nlist, counter, c_ptr, c_col,
+                                                                c_val, h->d_flags);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return STC_OK;
+}
+
+// wide == false: the instance for rows of at most WR_VCAP_S entries (more warps
+// per SM), else the one for rows of at most WR_VCAP.
+template <int ALG>
+stc_status launch_wr_numeric_any(stc_handle* h, bool wide, const SpgRows& R, const int32_t* row_mat,
+                                 const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
+                                 int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+    if (wide)
+        return launch_wr_numeric<ALG, WR_NUM_WARPS, WR_VCAP>(h, R, row_mat, rowlist, nlist, counter, c_ptr, c_col,
+                                                             c_val, NR, s);
+    return launch_wr_numeric<ALG, WR_NUM_WARPS_S, WR_VCAP_S>(h, R, row_mat, rowlist, nlist, counter, c_ptr, c_col,
+                                                             c_val, NR, s);
+}
+
+stc_status run_wr_numeric(stc_handle* h, int alg, bool wide, const SpgRows& R, const int32_t* row_mat,
+                          const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
+                          int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+    switch (alg) {
+    case ALG_PT_F32: return launch_wr_numeric_any<ALG_PT_F32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
+    case ALG_PT_F64: return launch_wr_numeric_any<ALG_PT_F64>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
+    case ALG_MP_I32: return launch_wr_numeric_any<ALG_MP_I32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
+    case ALG_MP_F32: return launch_wr_numeric_any<ALG_MP_F32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
+    case ALG_BOOL: return launch_wr_numeric_any<ALG_BOOL>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
+    default: return STC_ERR_ALGEBRA;
+    }
+}
+
 // light != 0: the configuration of the light-row launch (512 threads, two CTAs
 // per SM sharing its shared memory, a value buffer of a few thousand ranks).
 RankCfg rank_config(int alg, int64_t ncols_max, int ncell_max, bool light = false) {
@@ -1577,10 +1936,13 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
                               ? int((ncols_max + RK_CELL - 1) >> RK_CELL_SHIFT) : 1;
     const RankCfg cfg = rank_config(alg, ncols_max, ncell_max);
     if (!cfg.vcap) return STC_ERR_INVALID_ARG;
+    // narrow outputs: warp-per-row count and numeric passes (rows above the warp's
+    // value slots go to the CTA kernel)
+    const bool warp_path = ncols_max <= WR_MAX_COLS && wr_supported(alg);
     // light rows (ub < 2^light_log2) get their own launch of 512-thread CTAs, two per
     // SM, beside the wide launch; only when their whole row fits one rank window
     RankCfg lcfg{};
-    int L = light_log2 > 0 && light_log2 < NBINS ? light_log2 : 0;
+    int L = (!warp_path && light_log2 > 0 && light_log2 < NBINS) ? light_log2 : 0;
     if (L) {
         lcfg = rank_config(alg, ncols_max, ncell_max, true);
         if (!lcfg.vcap || (int64_t(1) << L) > int64_t(lcfg.vcap - RK_CELL)) L = 0;
@@ -1623,10 +1985,11 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     }
     int64_t* ub = sc.get<int64_t>(size_t(NR));
     int32_t* rowlist = sc.get<int32_t>(size_t(NR));
-    int* ints = sc.get<int>(2 * NBINS_ALL + 8);
+    int* ints = sc.get<int>(2 * NBINS_ALL + 24);
     int64_t* bounds_d = sc.get<int64_t>(size_t(nb) + 1);
+    int32_t* row_mat = (warp_path && nb > 1) ? sc.get<int32_t>(size_t(NR)) : nullptr;
     if (sc.failed) return fail(STC_ERR_OOM);
-    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS_ALL + 8), s) != cudaSuccess) return fail(STC_ERR_CUDA);
+    if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS_ALL + 24), s) != cudaSuccess) return fail(STC_ERR_CUDA);
     int* bin_count = ints;
     int* cursor = ints + NBINS_ALL;
     int* nlist = ints + 2 * NBINS_ALL;
@@ -1635,7 +1998,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     if (NR > 0) {
         int64_t blocks = (NR * 32 + 255) / 256;
         if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, c_ptr + 1);
+        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, c_ptr + 1, row_mat);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
         k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, c_ptr + 1, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
@@ -1647,12 +2010,45 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     const size_t rec_bytes = rank_layout(ncell_max, 0, 0, 4, false).winfirst;
     uint4* rec = nullptr;
     int2* rec_meta = nullptr;  // per record: (number of words of a sparse record or -1, row count)
-    if (NR > 0 && double(NR) * double(rec_bytes) <= RK_RECORD_BUDGET) {
+    if (NR > 0 && !warp_path && double(NR) * double(rec_bytes) <= RK_RECORD_BUDGET) {
         rec = sc.get<uint4>(size_t(NR) * (rec_bytes / 16));
         rec_meta = sc.get<int2>(size_t(NR));
         if (!rec || !rec_meta) return fail(STC_ERR_OOM);
     }
-    if (NR > 0) {
+    // ints past the bins: [0] nlist, [1..3] pass counters, [4] max row, [5..6] light split,
+    // [8..10] numeric list sizes, [11..13] their counters, [14] count-pass counter,
+    // [16..17] rows with >= 2^WR_UB_LOG2 products / the others
+    int* wr_heavy = ints + 2 * NBINS_ALL + 16;
+    if (NR > 0 && warp_path) {
+        // heavy prefix of the row list on the CTA kernel, the rest one warp per row
+        k_split_counts<<<1, 32, 0, s>>>(bin_count, WR_UB_LOG2, wr_heavy);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+        {
+            const size_t smem = sym_layout(ncell_max).total;
+            auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+            STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            int per_sm = 0;
+            STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
+            if (per_sm < 1) return fail(STC_ERR_CUDA);
+            int64_t grid = int64_t(per_sm) * h->num_sms;
+            if (grid > NR) grid = NR;
+            kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell_max, rowlist, wr_heavy, counters, c_ptr + 1,
+                                                         max_nnz, nullptr, nullptr, 0);
+            if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+            stc_count(h);
+        }
+        auto kern = k_wr_count<WR_COUNT_WARPS>;
+        int per_sm = 0;
+        STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WR_COUNT_WARPS * 32, 0));
+        if (per_sm < 1) return fail(STC_ERR_CUDA);
+        int64_t grid = int64_t(per_sm) * h->num_sms;
+        if (grid * WR_COUNT_WARPS > NR) grid = (NR + WR_COUNT_WARPS - 1) / WR_COUNT_WARPS;
+        kern<<<unsigned(grid), WR_COUNT_WARPS * 32, 0, s>>>(R, row_mat, rowlist, wr_heavy, nlist,
+                                                           ints + 2 * NBINS_ALL + 14, c_ptr + 1, max_nnz);
+        if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+        stc_count(h);
+    } else if (NR > 0) {
         const size_t smem = sym_layout(ncell_max).total;
         auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
         STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -1681,8 +2077,8 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&stage_i[0], h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&stage_i[1], max_nnz, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        (L && cudaMemcpyAsync(stage_bins, bin_count, sizeof(int) * NBINS_ALL, cudaMemcpyDeviceToHost, s) !=
-                  cudaSuccess) ||
+        ((L || warp_path) &&
+         cudaMemcpyAsync(stage_bins, bin_count, sizeof(int) * NBINS_ALL, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
         (nb > 1 && cudaMemcpyAsync(bounds_h, bounds_d, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToHost, s) !=
                        cudaSuccess) ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -1740,7 +2136,42 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         if (nb > 1 && cudaStreamSynchronize(s) != cudaSuccess) return fail(STC_ERR_CUDA);  // args vector lifetime
     }
     stc_mark(h, s, 4);
-    if (nnz > 0) {
+    if (nnz > 0 && warp_path) {
+        RankOut out{};
+        out.ptr = c_ptr;
+        int* nsplit = ints + 2 * NBINS_ALL + 8;   // [0..2] sizes of the three lists
+        int* wcounter = ints + 2 * NBINS_ALL + 11;  // [0] narrow warp instance, [1] wide, [2] CTA kernel
+        int64_t wr_heavy_rows = 0;
+        for (int b = WR_UB_LOG2 + 1; b < NBINS; ++b) wr_heavy_rows += stage_bins[b];
+        if (max_row <= WR_VCAP_S && wr_heavy_rows == 0) {
+            if ((st = run_wr_numeric(h, alg, false, R, row_mat, rowlist, nlist, wcounter, c_ptr, c_col, c_val, NR,
+                                     s)) != STC_OK)
+                return fail(st);
+        } else {
+            int32_t* lists = sc.get<int32_t>(3 * size_t(NR));
+            if (!lists) return fail(STC_ERR_OOM);
+            int64_t blocks = (NR + 255) / 256;
+            if (blocks > int64_t(h->num_sms) * 8) blocks = int64_t(h->num_sms) * 8;
+            k_split_by_count<<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, wr_heavy, c_ptr, lists, lists + NR,
+                                                              lists + 2 * NR, nsplit);
+            if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
+            stc_count(h);
+            if (max_row > WR_VCAP || wr_heavy_rows > 0) {
+                if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, lists + 2 * NR, nsplit + 2, wcounter + 2, out,
+                                          c_col, c_val, NR, s)) != STC_OK)
+                    return fail(st);
+            }
+            if (max_row > WR_VCAP_S &&
+                (st = run_wr_numeric(h, alg, true, R, row_mat, lists + NR, nsplit + 1, wcounter + 1, c_ptr, c_col,
+                                     c_val, NR, s)) != STC_OK)
+                return fail(st);
+            if ((st = run_wr_numeric(h, alg, false, R, row_mat, lists, nsplit, wcounter, c_ptr, c_col, c_val, NR,
+                                     s)) != STC_OK)
+                return fail(st);
+        }
+        if ((st = run_copy_any(h, alg, R, rowlist, nlist, bin_count + BIN_COPY, c_ptr, c_col, c_val, s)) != STC_OK)
+            return fail(st);
+    } else if (nnz > 0) {
         RankOut out{};
         out.ptr = c_ptr;
         if (L) {
@@ -2549,7 +2980,6 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
     int32_t* ovf_scratch = sc.get<int32_t>(size_t(NR));
     int* ints = sc.get<int>(size_t(S) * NI + 8);
     double* err = sc.get<double>(1);
-    float* pred = weights ? sc.get<float>(size_t(NR)) : nullptr;
     float* feat = weights ? sc.get<float>(size_t(NR) * STC_MLP_FEAT_STRIDE) : nullptr;
     if (sc.failed) return fail(STC_ERR_OOM);
     if (cudaMemsetAsync(cnt, 0, sizeof(int64_t) * size_t(S) * size_t(NR), s) != cudaSuccess ||
@@ -2563,7 +2993,9 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
     int64_t scratch_total = 0;
     stc_mark(h, s, 2);
 
-    // 1) per slab: analysis, capacities, one numeric pass into the slab's scratch
+    // 1) per slab: analysis, features and model, capacities and scratch offsets
+    float* preds = weights ? sc.get<float>(size_t(S) * size_t(NR)) : nullptr;
+    if (weights && !preds) return fail(STC_ERR_OOM);
     for (int t = 0; t < S && NR > 0; ++t) {
         SpgRows R{};
         R.one = sl.args[t];
@@ -2572,12 +3004,11 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         int* bin_count = ti;
         int* cursor = ti + NBINS_ALL;
         int* nlist = ti + 2 * NBINS_ALL;
-        int* counters = ti + 2 * NBINS_ALL + 1;
         int* maxcap = ti + 2 * NBINS_ALL + 4;
-        int* novf = ti + 2 * NBINS_ALL + 5;
         int32_t* rowlist = rowlists + size_t(t) * NR;
         int64_t* cap_t = cap + size_t(t) * NR;
         int64_t* soff_t = soff + size_t(t) * (NR + 1);
+        float* pred_t = weights ? preds + size_t(t) * NR : nullptr;
         int64_t blocks = (NR * 32 + 255) / 256;
         if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
         k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, nullptr);
@@ -2587,29 +3018,56 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         stc_count(h, 3);
         if (weights) {
             if ((st = stc_features_impl(h, sc, A, &sl.view[t], feat, s)) != STC_OK) return fail(st);
-            if ((st = stc_mlp_forward_tc_impl(h, weights, feat, NR, pred, s)) != STC_OK) return fail(st);
+            if ((st = stc_mlp_forward_tc_impl(h, weights, feat, NR, pred_t, s)) != STC_OK) return fail(st);
         }
         int64_t cb = (NR + 255) / 256;
         if (cb > int64_t(h->num_sms) * 8) cb = int64_t(h->num_sms) * 8;
-        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred, margin, sl.args[t].ncols, nullptr, cap_t, soff_t + 1,
+        k_capacity<<<unsigned(cb), 256, 0, s>>>(NR, ub, pred_t, margin, sl.args[t].ncols, nullptr, cap_t, soff_t + 1,
                                                  maxcap);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h);
         if ((st = stc_inclusive_scan_i64(h, sc, soff_t + 1, NR, s)) != STC_OK) return fail(st);
-        int* mc = reinterpret_cast<int*>(&h->h_stage[1]);
-        *mc = 0;
-        if (cudaMemcpyAsync(&h->h_stage[0], soff_t + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaMemcpyAsync(mc, maxcap, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return fail(STC_ERR_CUDA);
-        const int64_t S_t = h->h_stage[0];
-        const int max_cap = *mc;
-        scratch_total += S_t;
-        s_cols[t] = sc.get<int32_t>(size_t(S_t) + 1);
-        s_vals[t] = sc.get<unsigned char>((size_t(S_t) + 1) * vbytes);
+    }
+    // one synchronisation: every slab's scratch size and largest capacity
+    std::vector<int64_t> S_t(S, 0);
+    std::vector<int> max_cap(S, 0);
+    if (NR > 0) {
+        int* mc = reinterpret_cast<int*>(&h->h_stage[SLAB_MAX]);  // S ints
+        for (int t = 0; t < S; ++t) {
+            h->h_stage[t] = 0;
+            mc[t] = 0;
+            if (cudaMemcpyAsync(&h->h_stage[t], soff + size_t(t) * (NR + 1) + NR, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(&mc[t], ints + size_t(t) * NI + 2 * NBINS_ALL + 4, sizeof(int), cudaMemcpyDeviceToHost,
+                                s) != cudaSuccess)
+                return fail(STC_ERR_CUDA);
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) return fail(STC_ERR_CUDA);
+        for (int t = 0; t < S; ++t) {
+            S_t[t] = h->h_stage[t];
+            max_cap[t] = mc[t];
+        }
+    }
+    for (int t = 0; t < S && NR > 0; ++t) {
+        scratch_total += S_t[t];
+        s_cols[t] = sc.get<int32_t>(size_t(S_t[t]) + 1);
+        s_vals[t] = sc.get<unsigned char>((size_t(S_t[t]) + 1) * vbytes);
         if (!s_cols[t] || !s_vals[t]) return fail(STC_ERR_OOM);
+    }
+    stc_mark(h, s, 3);
+
+    // one numeric pass per slab into its scratch (exact sizes and overflows recorded)
+    for (int t = 0; t < S && NR > 0; ++t) {
+        SpgRows R{};
+        R.one = sl.args[t];
+        R.nb = 1;
+        int* ti = ints + size_t(t) * NI;
+        int* nlist = ti + 2 * NBINS_ALL;
+        int* counters = ti + 2 * NBINS_ALL + 1;
+        int* novf = ti + 2 * NBINS_ALL + 5;
+        int32_t* rowlist = rowlists + size_t(t) * NR;
         StcScratch sct(h, s);  // the slab's cell-offset table
-        if (max_cap >= sl.cfg[t].vcap - RK_CELL) {
+        if (max_cap[t] >= sl.cfg[t].vcap - RK_CELL) {
             int32_t* ctab = sct.get<int32_t>(size_t(K) * size_t(sl.ncell[t] + 1));
             if (!ctab) return fail(STC_ERR_OOM);
             R.one.ctab = ctab;
@@ -2620,18 +3078,18 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
             stc_count(h);
         }
         RankOut out{};
-        out.ptr = soff_t;
-        out.cap = cap_t;
+        out.ptr = soff + size_t(t) * (NR + 1);
+        out.cap = cap + size_t(t) * NR;
         out.nnz = cnt + size_t(t) * NR;
         out.ovf = ovfs + size_t(t) * NR;
         out.novf = novf;
-        out.pred = pred;
+        out.pred = weights ? preds + size_t(t) * NR : nullptr;
         out.err = err;
         if ((st = run_numeric_any(h, alg, R, sl.ncell[t], sl.cfg[t], rowlist, nlist, counters, out, s_cols[t],
                                   s_vals[t], NR, s)) != STC_OK)
             return fail(st);
     }
-    stc_mark(h, s, 3);
+    stc_mark(h, s, 4);
 
     // 2) row pointers and per-slab offsets
     if (NR > 0) {
@@ -2676,7 +3134,7 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
     c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
     c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
     if ((!c_col || !c_val) && nnz > 0) return fail(STC_ERR_OOM);
-    stc_mark(h, s, 4);
+    stc_mark(h, s, 5);
 
     // 3) per slab: compaction of the rows that fit, exact recomputation of the others
     int units = 0, overflows = 0;
@@ -2706,7 +3164,7 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         units += n_rows[t];
         overflows += n_ovf[t];
     }
-    stc_mark(h, s, 5);
+    stc_mark(h, s, 6);
     if (stats) {
         stats->rows = units;
         stats->overflow_rows = overflows;

@@ -70,9 +70,13 @@ extern "C" stc_status stc_create(stc_handle** out, stc_alloc_fn alloc, stc_free_
             cudaSuccess ||
         cudaMalloc(&h->d_flags, 64) != cudaSuccess ||
         cudaMemset(h->d_flags, 0, 64) != cudaSuccess ||
-        cudaMallocHost(&h->h_stage, 64 * sizeof(int64_t)) != cudaSuccess) {
+        cudaMallocHost(&h->h_stage, 64 * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_params, STC_PARAM_BYTES) != cudaSuccess ||
+        cudaMallocHost(&h->h_params, STC_PARAM_BYTES) != cudaSuccess) {
         (void)cudaGetLastError();
         if (h->d_flags) cudaFree(h->d_flags);
+        if (h->h_stage) cudaFreeHost(h->h_stage);
+        if (h->d_params) cudaFree(h->d_params);
         delete h;
         return STC_ERR_CUDA;
     }
@@ -114,8 +118,14 @@ extern "C" void stc_destroy(stc_handle* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (int a = 0; a < 2; ++a) {
+        if (h->bf_exec[a]) cudaGraphExecDestroy(h->bf_exec[a]);
+        if (h->bf_graph[a]) cudaGraphDestroy(h->bf_graph[a]);
+    }
     if (h->d_flags) cudaFree(h->d_flags);
     if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->d_params) cudaFree(h->d_params);
+    if (h->h_params) cudaFreeHost(h->h_params);
     delete h;
 }
 

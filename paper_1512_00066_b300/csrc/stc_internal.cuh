@@ -27,6 +27,13 @@ struct stc_handle {
     int round_driver = 1;          // multi-round loops: 0 host-driven, 1 CUDA graph
     cudaStream_t aux = nullptr;    // second stream for concurrent launches (created on first use)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // Bellman-Ford CUDA graph per algebra (0: int32, 1: fp32), instantiated on the
+    // first graph-driven call and reused by later ones: its kernels read their
+    // arguments from the device parameter block, which each call rewrites
+    cudaGraph_t bf_graph[2] = {};
+    cudaGraphExec_t bf_exec[2] = {};
+    void* d_params = nullptr;  // device parameter block, STC_PARAM_BYTES
+    void* h_params = nullptr;  // pinned host staging of that block
     // tuned light-row threshold per (algebra, ceil(log2 output columns)): -128 unknown,
     // -1 no light launch, L > 0 rows with ub < 2^L
     signed char tune_light[6][40];
@@ -35,6 +42,8 @@ struct stc_handle {
             for (auto& x : row) x = -128;
     }
 };
+
+constexpr size_t STC_PARAM_BYTES = 4096;
 
 // The auxiliary stream; run work on it between stc_fork and stc_join (stream order
 // of `s` is kept: the auxiliary work starts after what is queued on `s` and `s`

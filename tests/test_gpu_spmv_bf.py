@@ -150,6 +150,36 @@ def test_bellman_ford_closed_forms_and_cycles(H):
     assert np.array_equal(d.cpu().numpy(), 7 * np.arange(n))
 
 
+def test_bellman_ford_graph_is_reused_across_calls(H):
+    """The graph driver instantiates its CUDA graph once per handle and algebra and
+    rewrites only its parameter block per call: graphs of different sizes, both
+    algebras interleaved, many sources in a row, each call against the oracle.
+    A graph with a negative cycle in between leaves later calls correct."""
+    cases = []
+    for scale, seed in ((10, 31), (13, 32), (8, 33)):
+        G = W.rmat(scale, seed=seed)
+        gi = G.with_val(W.weights_int(G.nnz, 1, 100, seed + 1))
+        gf = G.with_val(W.weights_unit01(G.nnz, seed + 2).astype(np.float32))
+        cases.append((gi, to_dev(gi), gf, to_dev(gf), W.sample_sources(G, 4, seed=seed + 3)))
+    n = 50
+    C = W.csr_from_coo(np.arange(n), (np.arange(n) + 1) % n, n, n)
+    C.val = np.full(n, -1, np.int32)
+    for rep in range(2):
+        for gi, dgi, gf, dgf, srcs in cases:
+            for v in srcs:
+                d, _ = H.bellman_ford(O.MP_I32, dgi, int(v), persistent="graph")
+                ref, _ = O.bellman_ford(O.MP_I32, gi, int(v))
+                assert np.array_equal(d.cpu().numpy(), ref)
+                d, _ = H.bellman_ford(O.MP_F32, dgf, int(v), persistent="graph")
+                ref, _ = O.bellman_ford(O.MP_F32, gf, int(v))
+                assert d.cpu().numpy().tobytes() == ref.tobytes()
+        if rep == 0:
+            import paper_1512_00066_b300 as stc
+            with pytest.raises(stc.StcError) as e:
+                H.bellman_ford(O.MP_I32, to_dev(C), 0, persistent="graph")
+            assert e.value.status == 7
+
+
 def test_bellman_ford_drivers_are_distinct(H):
     """Each driver runs its own launch pattern: the host loop launches one kernel
     per round, the cooperative form one kernel in all, and the graph form counts
