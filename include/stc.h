@@ -471,9 +471,10 @@ STC_API stc_status stc_model_load(const char* path, float* weights, stc_stream s
 typedef struct {
     int64_t rows;              /* output rows with at least one product (-1: exact path used) */
     int64_t overflow_rows;     /* rows whose predicted capacity was too small */
-    int64_t scratch_entries;   /* total predicted capacity */
+    int64_t scratch_entries;   /* total predicted capacity (the slots, without the overflow pool) */
     int64_t nnz;               /* nnz(C) */
     double mean_abs_log2_error; /* mean |prediction - log2(1 + nnz(C_i))| (-1 without a model) */
+    int64_t recomputed_rows;   /* overflow rows that also missed the overflow pool: recomputed */
 } stc_learned_stats;
 
 /*
@@ -482,8 +483,9 @@ typedef struct {
  * pass.  Every row gets a capacity -- (1 + margin) * (2^prediction - 1) + 8 from
  * the model `weights`, clipped to [1, min(ub_i, ncols)], or min(ub_i, ncols) when
  * weights is NULL -- and one numeric pass writes it into scratch of that size
- * while counting it exactly; rows that fit are compacted into C, rows that did
- * not are recomputed exactly.  Outputs wider than 2^18 columns (at most 32
+ * while counting it exactly; a row larger than its capacity goes to an overflow
+ * pool after the slots (an eighth of their size); rows that fit are compacted
+ * into C, rows that missed the pool too are recomputed exactly.  Outputs wider than 2^18 columns (at most 32
  * column slabs of 2^18) run the same single pass slab by slab: every slab B_s
  * is its own learned product A B_s, and stats count (row, slab) units; wider
  * outputs than that use the exact two-pass path (stats->rows = -1).

@@ -69,7 +69,8 @@ class _Opts(ctypes.Structure):
 
 class _LearnedStats(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("overflow_rows", ctypes.c_int64), ("scratch_entries", ctypes.c_int64),
-                ("nnz", ctypes.c_int64), ("mean_abs_log2_error", ctypes.c_double)]
+                ("nnz", ctypes.c_int64), ("mean_abs_log2_error", ctypes.c_double),
+                ("recomputed_rows", ctypes.c_int64)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

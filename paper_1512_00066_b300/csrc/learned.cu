@@ -47,25 +47,31 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
 }
 
 // sketch[k][b] = min over columns j of B_k in bucket b of the low 32 bits of
-// splitmix64(j), or 2^32 when the bucket is empty.  One warp per row.
+// splitmix64(j), or 2^32 when the bucket is empty.  One warp per row: 32-bit
+// minima in shared memory, the buckets hit kept as a per-lane mask and OR-reduced
+// over the warp at the end.
 __global__ void __launch_bounds__(256) k_sketch_rows(int64_t K, int64_t nnzB, const int64_t* __restrict__ b_ptr,
                                                      const int32_t* __restrict__ b_col,
                                                      unsigned long long* __restrict__ sketch) {
-    __shared__ unsigned long long s[8][32];
+    __shared__ unsigned s[8][32];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t k = warp; k < K; k += nwarps) {
-        s[wl][lane] = EMPTY;
+        s[wl][lane] = 0xFFFFFFFFu;
         __syncwarp();
         int64_t lo, hi;
         row_range(b_ptr, k, nnzB, lo, hi);
+        unsigned hit = 0u;
         for (int64_t p = lo + lane; p < hi; p += 32) {
             const unsigned long long h = splitmix64((unsigned long long)(unsigned)b_col[p]);
-            atomicMin(&s[wl][h >> 59], h & 0xFFFFFFFFull);
+            const unsigned b = unsigned(h >> 59), key = unsigned(h & 0xFFFFFFFFull);
+            hit |= 1u << b;
+            if (key < s[wl][b]) atomicMin(&s[wl][b], key);
         }
+        hit = __reduce_or_sync(0xffffffffu, hit);
         __syncwarp();
-        sketch[k * 32 + lane] = s[wl][lane];
+        sketch[k * 32 + lane] = ((hit >> lane) & 1u) ? (unsigned long long)s[wl][lane] : EMPTY;
         __syncwarp();
     }
 }

@@ -68,6 +68,14 @@ struct RankOut {
     int* __restrict__ novf;
     const float* __restrict__ pred;  // predicted log2(1 + nnz), or null
     double* __restrict__ err;        // sum of |pred - log2(1 + nnz)|
+    // Learned form: a row larger than its capacity is written to the overflow pool
+    // [pool_base, pool_base + pool_cap) of the scratch instead (bump allocation in
+    // *pool_used) and listed in ovf only when the pool is full.  where[gi] (may be
+    // null) receives the scratch offset the row was written at, or -1.
+    unsigned long long* __restrict__ pool_used;
+    int64_t pool_base, pool_cap;
+    int64_t* __restrict__ where;
+    int* __restrict__ n_over;  // rows larger than their capacity, pooled or not (may be null)
 };
 
 __device__ __forceinline__ int batch_of(const SpgRows& R, int64_t gi) {
@@ -1493,6 +1501,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
     __shared__ int64_t s_row[3];
     __shared__ int s_warp[NT / 32 + 1];
     __shared__ int s_nwin;
+    __shared__ int64_t s_dst;
+    __shared__ int s_fits;
 
     for (int w = threadIdx.x; w < ncell_max * 32; w += NT) wb[w] = make_uint2(0u, 0u);
     for (int c = threadIdx.x; c < ncell_max; c += NT) summ[c] = 0u;
@@ -1599,16 +1609,30 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         }
         if (threadIdx.x == 0) {
             cellbase[ncell] = total;
+            int64_t dst = o0;
+            int ok = total <= o1 - o0;
             if (out.cap) {
                 out.nnz[gi] = total;
-                if (total > o1 - o0) out.ovf[atomicAdd(out.novf, 1)] = int32_t(gi);
+                if (!ok && out.n_over) atomicAdd(out.n_over, 1);
+                if (!ok && out.pool_used) {
+                    const unsigned long long at = atomicAdd(out.pool_used, (unsigned long long)total);
+                    if (int64_t(at) + total <= out.pool_cap) {
+                        dst = out.pool_base + int64_t(at);
+                        ok = 1;
+                    }
+                }
+                if (!ok) out.ovf[atomicAdd(out.novf, 1)] = int32_t(gi);
+                if (out.where) out.where[gi] = ok ? dst : -1;
                 if (out.pred) atomicAdd(out.err, fabs(double(out.pred[gi]) - log2(1.0 + double(total))));
             } else if (total != int(o1 - o0)) {
                 atomicOr(flags, STC_FLAG_INTERNAL);
             }
+            s_dst = dst;
+            s_fits = ok;
         }
         __syncthreads();
-        const bool fits = total <= int(o1 - o0);
+        const bool fits = s_fits != 0;
+        const int64_t od = s_dst;  // where this row's entries go
         if (!sparse) {
             for (int c = threadIdx.x; c < ncell; c += NT) {
                 const int wc = cellbase[c] / vstep;
@@ -1659,18 +1683,18 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             }
             for (int r = threadIdx.x; r < rcount; r += NT) {
                 if (fits) {
-                    if constexpr (!MASKED) c_col[o0 + rb + r] = scol[r] + g.col_base;
+                    if constexpr (!MASKED) c_col[od + rb + r] = scol[r] + g.col_base;
                     if constexpr (ALG == ALG_MULTPATH) {
                         DSig o;
                         o.d = (MASKED && vals[r] == T::empty()) ? STC_MIN_PLUS_I32_IDENTITY : vals[r];
                         o.pad = 0;
                         o.s = sig[r];
-                        cval[o0 + rb + r] = o;
+                        cval[od + rb + r] = o;
                         sig[r] = 0.0;
                     } else if constexpr (MASKED) {
-                        cval[o0 + rb + r] = vals[r] == T::empty() ? T::identity() : T::out(vals[r]);
+                        cval[od + rb + r] = vals[r] == T::empty() ? T::identity() : T::out(vals[r]);
                     } else {
-                        cval[o0 + rb + r] = T::out(vals[r]);
+                        cval[od + rb + r] = T::out(vals[r]);
                     }
                 }
                 vals[r] = T::empty();
@@ -2257,12 +2281,14 @@ __global__ void k_capacity(int64_t NR, const int64_t* __restrict__ ub, const flo
 // Copy every listed row that fit its capacity from the scratch to C (warp per row).
 // The row's size is cnt[i] when cnt != null (c_ptr then holds destinations only),
 // else c_ptr[i + 1] - c_ptr[i].
+// where (may be null): the scratch offset each row was written at (slot or
+// overflow pool), -1 for a row left to the exact recomputation.
 template <class V>
 __global__ void k_compact(const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                           const int64_t* __restrict__ soff, const int64_t* __restrict__ cap,
-                          const int64_t* __restrict__ c_ptr, const int64_t* __restrict__ cnt,
-                          const int32_t* __restrict__ scol, const V* __restrict__ sval, int32_t* __restrict__ c_col,
-                          V* __restrict__ c_val) {
+                          const int64_t* __restrict__ where, const int64_t* __restrict__ c_ptr,
+                          const int64_t* __restrict__ cnt, const int32_t* __restrict__ scol,
+                          const V* __restrict__ sval, int32_t* __restrict__ c_col, V* __restrict__ c_val) {
     const int lane = threadIdx.x & 31;
     const int nlist = *nlist_ptr;
     int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -2270,8 +2296,14 @@ __global__ void k_compact(const int32_t* __restrict__ rowlist, const int* __rest
     for (int64_t r = warp; r < nlist; r += nwarps) {
         const int32_t i = rowlist[r];
         const int64_t d0 = c_ptr[i], n = cnt ? cnt[i] : c_ptr[i + 1] - d0;
-        if (n > cap[i]) continue;  // overflow: recomputed exactly
-        const int64_t s0 = soff[i];
+        int64_t s0;
+        if (where) {
+            s0 = where[i];
+            if (s0 < 0) continue;  // recomputed exactly
+        } else {
+            if (n > cap[i]) continue;
+            s0 = soff[i];
+        }
         for (int64_t e = lane; e < n; e += 32) {
             c_col[d0 + e] = scol[s0 + e];
             c_val[d0 + e] = sval[s0 + e];
@@ -2280,17 +2312,18 @@ __global__ void k_compact(const int32_t* __restrict__ rowlist, const int* __rest
 }
 
 stc_status run_compact(stc_handle* h, size_t vbytes, const int32_t* rowlist, const int* nlist, int n_rows,
-                       const int64_t* soff, const int64_t* cap, const int64_t* dst, const int64_t* cnt,
-                       const int32_t* scol, const void* sval, int32_t* c_col, void* c_val, stc_stream s) {
+                       const int64_t* soff, const int64_t* cap, const int64_t* where, const int64_t* dst,
+                       const int64_t* cnt, const int32_t* scol, const void* sval, int32_t* c_col, void* c_val,
+                       stc_stream s) {
     int64_t blocks = (int64_t(n_rows) * 32 + 255) / 256;
     if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
     if (blocks < 1) blocks = 1;
     const unsigned gb = unsigned(blocks);
     switch (vbytes) {
-    case 1: k_compact<uint8_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint8_t*>(sval), c_col, static_cast<uint8_t*>(c_val)); break;
-    case 4: k_compact<uint32_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint32_t*>(sval), c_col, static_cast<uint32_t*>(c_val)); break;
-    case 8: k_compact<uint64_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint64_t*>(sval), c_col, static_cast<uint64_t*>(c_val)); break;
-    default: k_compact<uint4><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, dst, cnt, scol, static_cast<const uint4*>(sval), c_col, static_cast<uint4*>(c_val)); break;
+    case 1: k_compact<uint8_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, where, dst, cnt, scol, static_cast<const uint8_t*>(sval), c_col, static_cast<uint8_t*>(c_val)); break;
+    case 4: k_compact<uint32_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, where, dst, cnt, scol, static_cast<const uint32_t*>(sval), c_col, static_cast<uint32_t*>(c_val)); break;
+    case 8: k_compact<uint64_t><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, where, dst, cnt, scol, static_cast<const uint64_t*>(sval), c_col, static_cast<uint64_t*>(c_val)); break;
+    default: k_compact<uint4><<<gb, 256, 0, s>>>(rowlist, nlist, soff, cap, where, dst, cnt, scol, static_cast<const uint4*>(sval), c_col, static_cast<uint4*>(c_val)); break;
     }
     STC_LAUNCH_CHECK();
     stc_count(h);
@@ -2854,9 +2887,15 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
         return fail(stc_flags_to_status(f));
     }
     const int max_cap = stage_i[1];
-    int32_t* scol = sc.get<int32_t>(size_t(S_total));
-    unsigned char* sval = sc.get<unsigned char>(size_t(S_total) * vbytes);
+    // the slots, then an overflow pool of an eighth of them for rows the model
+    // under-sized (only rows that miss the pool too are recomputed)
+    const int64_t pool = S_total / 8 + 4096;
+    int32_t* scol = sc.get<int32_t>(size_t(S_total + pool));
+    unsigned char* sval = sc.get<unsigned char>(size_t(S_total + pool) * vbytes);
+    int64_t* where = sc.get<int64_t>(size_t(NR) + 1);
+    unsigned long long* pool_used = sc.get<unsigned long long>(1);
     if (sc.failed) return fail(STC_ERR_OOM);
+    if (cudaMemsetAsync(pool_used, 0, sizeof(unsigned long long), s) != cudaSuccess) return fail(STC_ERR_CUDA);
     if (NR > 0 && max_cap >= cfg.vcap - RK_CELL) {
         int32_t* ctab = sc.get<int32_t>(size_t(g.K) * size_t(g.ncell + 1));
         if (!ctab) return fail(STC_ERR_OOM);
@@ -2877,33 +2916,41 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
         out.novf = novf;
         out.pred = pred;
         out.err = err;
+        out.pool_used = pool_used;
+        out.pool_base = S_total;
+        out.pool_cap = pool;
+        out.where = where;
+        out.n_over = novf + 1;
         if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, rowlist, nlist, counters, out, scol, sval, NR, s)) !=
             STC_OK)
             return fail(st);
         if ((st = stc_inclusive_scan_i64(h, sc, c_ptr + 1, NR, s)) != STC_OK) return fail(st);
     }
     // synchronisation 2: nnz, overflowing rows, listed rows, prediction error
-    int* st2 = reinterpret_cast<int*>(&h->h_stage[8]);
+    int* st2 = reinterpret_cast<int*>(&h->h_stage[8]);   // [0] recomputed, [1] listed rows
+    int* st_over = reinterpret_cast<int*>(&h->h_stage[10]);  // rows above their capacity
     st2[0] = st2[1] = 0;
+    *st_over = 0;
     double* err_h = reinterpret_cast<double*>(&h->h_stage[9]);
     *err_h = 0.0;
     if (cudaMemcpyAsync(&h->h_stage[0], c_ptr + NR, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&st2[0], novf, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&st2[1], nlist, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(st_over, novf + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(err_h, err, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(STC_ERR_CUDA);
     }
     const int64_t nnz = h->h_stage[0];
-    const int n_ovf = st2[0], n_rows = st2[1];
+    const int n_ovf = st2[0], n_rows = st2[1], n_over = *st_over;
     const double err_sum = *err_h;
     c_col = static_cast<int32_t*>(stc_alloc_bytes(h, size_t(nnz) * 4, s));
     c_val = stc_alloc_bytes(h, size_t(nnz) * vbytes, s);
     if (!c_col || !c_val) return fail(STC_ERR_OOM);
     stc_mark(h, s, 4);
     if (NR > 0 && nnz > 0) {
-        if ((st = run_compact(h, vbytes, rowlist, nlist, n_rows, soff, cap, c_ptr, nullptr, scol, sval, c_col, c_val,
+        if ((st = run_compact(h, vbytes, rowlist, nlist, n_rows, soff, cap, where, c_ptr, nullptr, scol, sval, c_col, c_val,
                               s)) != STC_OK)
             return fail(st);
         if ((st = run_copy_any(h, alg, R, rowlist, nlist, bin_count + BIN_COPY, c_ptr, c_col, c_val, s)) != STC_OK)
@@ -2919,7 +2966,8 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
     stc_mark(h, s, 5);
     if (stats) {
         stats->rows = n_rows;
-        stats->overflow_rows = n_ovf;
+        stats->overflow_rows = n_over;
+        stats->recomputed_rows = n_ovf;
         stats->scratch_entries = S_total;
         stats->nnz = nnz;
         stats->mean_abs_log2_error = (weights && n_rows > 0) ? err_sum / n_rows : -1.0;
@@ -3048,10 +3096,18 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
             max_cap[t] = mc[t];
         }
     }
+    // per slab: the slots, then an overflow pool of an eighth of them
+    std::vector<int64_t> pool_t(S, 0);
+    int64_t* wheres = sc.get<int64_t>(size_t(S) * size_t(NR) + 1);
+    unsigned long long* pool_used = sc.get<unsigned long long>(size_t(S));
+    if (!wheres || !pool_used) return fail(STC_ERR_OOM);
+    if (cudaMemsetAsync(pool_used, 0, sizeof(unsigned long long) * size_t(S), s) != cudaSuccess)
+        return fail(STC_ERR_CUDA);
     for (int t = 0; t < S && NR > 0; ++t) {
         scratch_total += S_t[t];
-        s_cols[t] = sc.get<int32_t>(size_t(S_t[t]) + 1);
-        s_vals[t] = sc.get<unsigned char>((size_t(S_t[t]) + 1) * vbytes);
+        pool_t[t] = S_t[t] / 8 + 4096;
+        s_cols[t] = sc.get<int32_t>(size_t(S_t[t] + pool_t[t]));
+        s_vals[t] = sc.get<unsigned char>(size_t(S_t[t] + pool_t[t]) * vbytes);
         if (!s_cols[t] || !s_vals[t]) return fail(STC_ERR_OOM);
     }
     stc_mark(h, s, 3);
@@ -3085,6 +3141,11 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         out.novf = novf;
         out.pred = weights ? preds + size_t(t) * NR : nullptr;
         out.err = err;
+        out.pool_used = pool_used + t;
+        out.pool_base = S_t[t];
+        out.pool_cap = pool_t[t];
+        out.where = wheres + size_t(t) * NR;
+        out.n_over = ti + 2 * NBINS_ALL + 6;
         if ((st = run_numeric_any(h, alg, R, sl.ncell[t], sl.cfg[t], rowlist, nlist, counters, out, s_cols[t],
                                   s_vals[t], NR, s)) != STC_OK)
             return fail(st);
@@ -3102,11 +3163,13 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         stc_count(h, 2);
     }
     int64_t nnz = 0;
-    std::vector<int> n_ovf(S, 0), n_rows(S, 0);
+    std::vector<int> n_ovf(S, 0), n_rows(S, 0), n_over(S, 0);
     double err_sum = 0.0;
     {
         int* v = reinterpret_cast<int*>(&h->h_stage[2]);  // 2 S ints: h_stage[2 .. 2 + S)
+        int* vo = reinterpret_cast<int*>(&h->h_stage[SLAB_MAX + 12]);  // S ints
         for (int t = 0; t < 2 * S; ++t) v[t] = 0;
+        for (int t = 0; t < S; ++t) vo[t] = 0;
         h->h_stage[SLAB_MAX + 8] = 0;
         double* e = reinterpret_cast<double*>(&h->h_stage[SLAB_MAX + 9]);
         *e = 0.0;
@@ -3115,6 +3178,8 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
             if (cudaMemcpyAsync(&v[2 * t], ti + 2 * NBINS_ALL + 5, sizeof(int), cudaMemcpyDeviceToHost, s) !=
                     cudaSuccess ||
                 cudaMemcpyAsync(&v[2 * t + 1], ti + 2 * NBINS_ALL, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(&vo[t], ti + 2 * NBINS_ALL + 6, sizeof(int), cudaMemcpyDeviceToHost, s) !=
                     cudaSuccess)
                 return fail(STC_ERR_CUDA);
         }
@@ -3128,6 +3193,7 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         for (int t = 0; t < S; ++t) {
             n_ovf[t] = v[2 * t];
             n_rows[t] = v[2 * t + 1];
+            n_over[t] = vo[t];
         }
     }
     if (nnz < 0) return fail(STC_ERR_CUDA);
@@ -3137,14 +3203,14 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
     stc_mark(h, s, 5);
 
     // 3) per slab: compaction of the rows that fit, exact recomputation of the others
-    int units = 0, overflows = 0;
+    int units = 0, overflows = 0, recomputed = 0;
     for (int t = 0; t < S && NR > 0 && nnz > 0; ++t) {
         const int* ti = ints + size_t(t) * NI;
         int64_t* cnt_t = cnt + size_t(t) * NR;
         int64_t* off_t = off + size_t(t) * NR;
         if ((st = run_compact(h, vbytes, rowlists + size_t(t) * NR, ti + 2 * NBINS_ALL, n_rows[t],
-                              soff + size_t(t) * (NR + 1), cap + size_t(t) * NR, off_t, cnt_t, s_cols[t], s_vals[t],
-                              c_col, c_val, s)) != STC_OK)
+                              soff + size_t(t) * (NR + 1), cap + size_t(t) * NR, wheres + size_t(t) * NR, off_t,
+                              cnt_t, s_cols[t], s_vals[t], c_col, c_val, s)) != STC_OK)
             return fail(st);
         if (n_ovf[t] > 0) {
             SpgRows R{};
@@ -3162,12 +3228,14 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
                 return fail(st);
         }
         units += n_rows[t];
-        overflows += n_ovf[t];
+        overflows += n_over[t];
+        recomputed += n_ovf[t];
     }
     stc_mark(h, s, 6);
     if (stats) {
         stats->rows = units;
         stats->overflow_rows = overflows;
+        stats->recomputed_rows = recomputed;
         stats->scratch_entries = scratch_total;
         stats->nnz = nnz;
         stats->mean_abs_log2_error = (weights && units > 0) ? err_sum / units : -1.0;
@@ -3614,6 +3682,7 @@ stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, con
         if (stats) {
             stats->rows = -1;
             stats->overflow_rows = 0;
+            stats->recomputed_rows = 0;
             stats->scratch_entries = 0;
             stats->mean_abs_log2_error = -1.0;
         }

@@ -170,7 +170,12 @@ def test_learned_equals_plain_for_any_model(H, trained, alg):
         _same(alg, C, plain)
         assert st["nnz"] == plain.nnz
     C, st = H.spgemm_learned(alg, dA, dB, under, 0.0)
-    assert st["overflow_rows"] > 0  # the fallback really ran
+    assert st["recomputed_rows"] > 0  # the exact recomputation really ran
+    # a trained model with no margin: rows above their capacity land in the
+    # overflow pool instead of being recomputed
+    C, st = H.spgemm_learned(alg, dA, dB, w, 0.0)
+    _same(alg, C, plain)
+    assert st["overflow_rows"] > st["recomputed_rows"]
 
 
 def test_learned_rows_against_oracle(H, trained):
@@ -223,7 +228,7 @@ def test_learned_column_slabs_equal_plain(H, trained, alg):
         _same(alg, C, plain)
         assert st["nnz"] == plain.nnz and st["rows"] > A.nrows  # (row, slab) units
     C, st = H.spgemm_learned(alg, dA, dB, under, 0.0)
-    assert st["overflow_rows"] > 0
+    assert st["overflow_rows"] > 0 and st["recomputed_rows"] > 0
     if alg == O.PT_F32:
         rp, col, val = C.to_host()
         ptr, rcol, rval, rabs = O.spgemm(alg, A, B, want_abs=True)
