@@ -230,8 +230,23 @@ class DeviceCsr:
         return int(self.col.numel())
 
     def _c(self) -> _Csr:
-        return _Csr(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
-                    self.val.data_ptr() if self.val is not None and self.val.numel() else None)
+        """The C descriptor, rebuilt only when a field changed (batched calls marshal
+        thousands of them)."""
+        return self._cached()[1]
+
+    def _c_bytes(self) -> bytes:
+        """The C descriptor's bytes (for building descriptor arrays of batched calls)."""
+        return self._cached()[2]
+
+    def _cached(self):
+        key = (self.nrows, self.ncols, id(self.rowptr), id(self.col), id(self.val))
+        cached = self.__dict__.get("_c_cache")
+        if cached is not None and cached[0] == key:
+            return cached
+        c = _Csr(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
+                 self.val.data_ptr() if self.val is not None and self.val.numel() else None)
+        cached = self.__dict__["_c_cache"] = (key, c, bytes(c))
+        return cached
 
     @staticmethod
     def from_host(nrows, ncols, rowptr, col, val=None, device="cuda") -> "DeviceCsr":
@@ -425,8 +440,8 @@ class Handle:
         """
         nb = len(As)
         assert nb == len(Bs) and nb > 0
-        A = (_Csr * nb)(*[a._c() for a in As])
-        B = (_Csr * nb)(*[b._c() for b in Bs])
+        A = (_Csr * nb).from_buffer_copy(b"".join([a._c_bytes() for a in As]))
+        B = (_Csr * nb).from_buffer_copy(b"".join([b._c_bytes() for b in Bs]))
         C = (_Csr * nb)()
         opts = _Opts(1 if skip_validation else 0, 0, int(light_rows))
         st = lib().stc_contract_spgemm_batched(self._h, alg, nb, A, B, C, ctypes.byref(opts), _stream_ptr(stream))
