@@ -330,6 +330,11 @@ def run_stc(args):
         sp_ms = statistics.mean(i["spgemm_ms"] for i in infos)
     # fp64 instruction rate of the numeric phase (one DFMA per product), informational
     dfma_per_s = nprod_of(A) / (num_ms / 1e3)
+    # the accumulator bound: products per second that shared-memory accumulation
+    # with the algebra's (+) absorbs on this device (calibration kernel of the library)
+    acc_alg = stc.PLUS_TIMES_F64 if wl["scale"] else stc.MIN_PLUS_I32
+    acc_rate = H.calibrate_accumulate(acc_alg)
+    acc_achieved = nprod_of(A) / (num_ms / 1e3)
 
     # end to end: host (pinned) inputs -> device -> the same step -> results back to host
     e2e = None
@@ -384,7 +389,10 @@ def run_stc(args):
                          "whole_spgemm": {"ms": sp_ms, "frac": gbytes / (sp_ms / 1e3) / 1e9 / hbm},
                          "compulsory": {"bytes": compulsory,
                                         "frac": compulsory / (num_ms / 1e3) / 1e9 / hbm},
-                         "fp64_dfma_per_s": dfma_per_s if wl["scale"] else None},
+                         "fp64_dfma_per_s": dfma_per_s if wl["scale"] else None,
+                         "smem_accumulate": {"achieved": acc_achieved, "peak": acc_rate,
+                                             "unit": "products/s", "frac": acc_achieved / acc_rate,
+                                             "peak_source": "stc_calibrate_accumulate on this device"}},
             "gpu_launches": launches,
             "tuning": tuning,
             "clocks": clk.summary(),

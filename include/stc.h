@@ -484,7 +484,7 @@ typedef struct {
  * the model `weights`, clipped to [1, min(ub_i, ncols)], or min(ub_i, ncols) when
  * weights is NULL -- and one numeric pass writes it into scratch of that size
  * while counting it exactly; a row larger than its capacity goes to an overflow
- * pool after the slots (an eighth of their size); rows that fit are compacted
+ * pool after the slots (a quarter of their size); rows that fit are compacted
  * into C, rows that missed the pool too are recomputed exactly.  Outputs wider than 2^18 columns (at most 32
  * column slabs of 2^18) run the same single pass slab by slab: every slab B_s
  * is its own learned product A B_s, and stats count (row, slab) units; wider
@@ -548,6 +548,19 @@ STC_API stc_status stc_selftest_barrier(stc_handle* h, int32_t missing, int32_t 
 STC_API stc_status stc_set_timing(stc_handle* h, int32_t enable);
 STC_API int32_t stc_phase_times(stc_handle* h, float* ms_out, int32_t max_phases);
 STC_API int64_t stc_kernel_launches(const stc_handle* h);
+
+/*
+ * Calibration of the numeric pass's accumulator (the paper has no counterpart;
+ * it measures the bound of the SpGEMM numeric phase on the running device).  One
+ * CTA of 1024 threads per SM has every thread combine 8192 products into 8192
+ * shared-memory accumulators at pseudo-random positions with the algebra's (+),
+ * applied as the numeric kernel applies it (fp64 (+,x): compare-and-swap of an
+ * fma).  *updates_per_s (host) receives the fastest of three timed runs after one
+ * warm-up, in products absorbed per second.  STC_ERR_ALGEBRA for the
+ * (distance, multiplicity) monoid.  Synchronises `stream`.
+ */
+STC_API stc_status stc_calibrate_accumulate(stc_handle* h, stc_algebra alg, double* updates_per_s,
+                                            stc_stream stream);
 
 /*
  * Allocation-free Bellman-Ford.  The paper has no counterpart: this entry point

@@ -168,6 +168,8 @@ def lib():
             L.stc_model_save.restype = ctypes.c_int
             L.stc_model_load.argtypes = [ctypes.c_char_p, p, p]
             L.stc_model_load.restype = ctypes.c_int
+            L.stc_calibrate_accumulate.argtypes = [p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), p]
+            L.stc_calibrate_accumulate.restype = ctypes.c_int
             L.stc_bellman_ford_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(_Csr), i32, p,
                                                    ctypes.POINTER(i32), p]
             L.stc_bellman_ford_noalloc.restype = ctypes.c_int
@@ -643,6 +645,14 @@ class Handle:
         _check(lib().stc_set_round_driver(self._h, code), "stc_set_round_driver")
 
     # -------------------------------------------------------------- instrumentation
+
+    def calibrate_accumulate(self, alg: int, stream=None) -> float:
+        """Products per second the numeric pass's shared-memory accumulator absorbs
+        on this device (stc_calibrate_accumulate)."""
+        r = ctypes.c_double(0.0)
+        _check(lib().stc_calibrate_accumulate(self._h, alg, ctypes.byref(r), _stream_ptr(stream)),
+               "stc_calibrate_accumulate")
+        return float(r.value)
 
     def set_timing(self, enable: bool = True):
         _check(lib().stc_set_timing(self._h, 1 if enable else 0), "stc_set_timing")

@@ -44,6 +44,7 @@ struct SpgArgs {
     const int32_t* __restrict__ ctab;  // rank path: [K][ncell+1] per-cell offsets in B rows, or null
     int ncell;                         // rank path: 1024-column cells of the output
     int col_base;                      // added to every written column (column slabs of a wide B)
+    int64_t bm_off;                    // warp-per-row passes: first bitmap word of this matrix's rows
 };
 
 // Rows of one matrix (table == null: `one`) or of a batch of independent
@@ -948,7 +949,7 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
             }
             if (threadIdx.x == 0) cellbase[g.ncell] = tot;
             __syncthreads();
-            unsigned char* dst = reinterpret_cast<unsigned char*>(rec) + s_row[2] * rec_bytes;
+            unsigned char* dst = reinterpret_cast<unsigned char*>(rec) + gi * rec_bytes;  // slot of the global row
             // light rows (one rank window in the numeric pass, few non-zero words): only
             // the non-zero words, as (bits, word << 18 | rank of the word's first column)
             bool sparse = false;
@@ -976,7 +977,7 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
                             }
                         }
                     }
-                    if (threadIdx.x == 0) rec_meta[s_row[2]] = make_int2(nzt, tot);
+                    if (threadIdx.x == 0) rec_meta[gi] = make_int2(nzt, tot);
                 }
             }
             if (!sparse) {
@@ -994,7 +995,7 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
                 for (int c = threadIdx.x; c < ncell_max; c += NT) dsumm[c] = summ[c];
                 int* dcb = reinterpret_cast<int*>(dst + LR.cellbase);
                 for (int c = threadIdx.x; c <= ncell_max; c += NT) dcb[c] = c <= g.ncell ? cellbase[c] : tot;
-                if (threadIdx.x == 0) rec_meta[s_row[2]] = make_int2(-1, tot);
+                if (threadIdx.x == 0) rec_meta[gi] = make_int2(-1, tot);
             }
             __syncthreads();
             for (int c = threadIdx.x; c < g.ncell; c += NT) {
@@ -1276,11 +1277,13 @@ __device__ __forceinline__ void wr_bits(const SpgArgs& g, int64_t alo, int64_t a
 
 // Count pass: row_nnz[gi] = nnz(C_i) for the listed rows [*lo_ptr, *hi_ptr)
 // (lo_ptr NULL: from 0).
+// bm (may be null): every row's bitmap is also stored, ceil(ncols / 32) words at
+// bm[g.bm_off + i * ceil(ncols / 32)], for the numeric pass.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_wr_count(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __restrict__ rowlist,
            const int* __restrict__ lo_ptr, const int* __restrict__ hi_ptr, int* __restrict__ counter,
-           int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz) {
+           int64_t* __restrict__ row_nnz, int* __restrict__ max_nnz, uint32_t* __restrict__ bm) {
     __shared__ uint32_t s_bits[WARPS][WR_WORDS];
     __shared__ WrChunk<int> s_tab[WARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1303,9 +1306,12 @@ k_wr_count(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __rest
         wr_bits<int, int>(g, alo, ahi, lane, bits, s_tab[wid]);
         __syncwarp();
         int n = 0;
-#pragma unroll
-        for (int t = 0; t < WR_ROUNDS; ++t) {
-            n += __popc(bits[t * 32 + lane]);
+        const int nw = int((g.ncols + 31) >> 5), nr = (nw + 31) >> 5;  // words, rounds of 32 words
+        uint32_t* dst = bm ? bm + g.bm_off + i * nw : nullptr;
+        for (int t = 0; t < nr; ++t) {
+            const uint32_t b = bits[t * 32 + lane];
+            n += __popc(b);
+            if (dst && t * 32 + lane < nw) dst[t * 32 + lane] = b;
             bits[t * 32 + lane] = 0u;
         }
         n = __reduce_add_sync(0xffffffffu, n);
@@ -1323,7 +1329,8 @@ template <int ALG, int WARPS, int VCAP>
 __global__ void __launch_bounds__(WARPS * 32)
 k_wr_numeric(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __restrict__ rowlist,
              const int* __restrict__ nlist_ptr, int* __restrict__ counter, const int64_t* __restrict__ c_ptr,
-             int32_t* __restrict__ c_col, void* __restrict__ c_val, int* __restrict__ flags) {
+             int32_t* __restrict__ c_col, void* __restrict__ c_val, int* __restrict__ flags,
+             const uint32_t* __restrict__ bm) {
     static_assert(VCAP <= 65535 && WR_MAX_COLS <= 65535, "ranks are kept in 16 bits");
     using T = Tr<ALG>;
     using AT = typename T::A;
@@ -1354,13 +1361,20 @@ k_wr_numeric(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __re
         row_range(g.a_ptr, i, g.nnzA, alo, ahi);
         const int64_t o0 = c_ptr[gi];
         const int64_t want = c_ptr[gi + 1] - o0;
-        // 1) bitmap
-        wr_bits<AT, BT>(g, alo, ahi, lane, bits, s_tab[wid]);
+        // only the words of the matrix's columns are used: nr rounds of 32 words
+        const int nw = int((g.ncols + 31) >> 5), nr = (nw + 31) >> 5;
+        // 1) bitmap: stored by the count pass (bm), else built here
+        if (bm) {
+            const uint32_t* src = bm + g.bm_off + i * nw;
+            for (int t = 0; t < nr; ++t)
+                if (t * 32 + lane < nw) bits[t * 32 + lane] = src[t * 32 + lane];
+        } else {
+            wr_bits<AT, BT>(g, alo, ahi, lane, bits, s_tab[wid]);
+        }
         __syncwarp();
         // 2) ranks: words owned lane-strided, one warp scan per round of 32 words
         int run = 0;
-#pragma unroll
-        for (int t = 0; t < WR_ROUNDS; ++t) {
+        for (int t = 0; t < nr; ++t) {
             const int c = __popc(bits[t * 32 + lane]);
             int x = c;
 #pragma unroll
@@ -1395,7 +1409,7 @@ k_wr_numeric(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __re
             __syncwarp();
             // 4) columns from the bitmap (each lane's word covers ranks wpre[w] ..)
 #pragma unroll 1
-            for (int t = 0; t < WR_ROUNDS; ++t) {
+            for (int t = 0; t < nr; ++t) {
                 const int w = t * 32 + lane;
                 uint32_t b = bits[w];
                 int64_t dst = o0 + wpre[w];
@@ -1410,8 +1424,7 @@ k_wr_numeric(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __re
                 vals[q] = T::empty();
             }
         }
-#pragma unroll
-        for (int t = 0; t < WR_ROUNDS; ++t) bits[t * 32 + lane] = 0u;
+        for (int t = 0; t < nr; ++t) bits[t * 32 + lane] = 0u;
         __syncwarp();
     }
 }
@@ -1517,6 +1530,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
     claim_init(rc, counter, nlist, rowlist);
     const int vstep = vcap - RK_CELL;  // rank span that starts a new window
     auto* cval = static_cast<typename T::C*>(c_val);
+    double err_sum = 0.0;  // thread 0: this CTA's share of out.err, added once at the end
 
     for (;;) {
         const int64_t gi = next_row_b(rc, counter, nlist, rowlist, R, &s_args, s_row);
@@ -1532,12 +1546,14 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
 
         int total;
         bool sparse = false;  // one rank window, no cell prefixes
-        if (rec) {
+        // a record with meta.y < 0 was not written (the row's count came from another
+        // pass): the bitmap is rebuilt
+        const int2 meta = rec ? rec_meta[gi] : make_int2(0, -1);
+        if (meta.y >= 0) {
             // the symbolic pass stored this row's bitmap, word prefixes and cell prefixes
             // (dense), or only its non-zero words with their ranks (sparse)
             const int rec16 = int(L.winfirst / 16);
-            const uint4* src = rec + s_row[2] * int64_t(rec16);
-            const int2 meta = rec_meta[s_row[2]];
+            const uint4* src = rec + gi * int64_t(rec16);  // records are slotted by global row
             if (meta.x >= 0) {
                 sparse = true;
                 const uint2* sp = reinterpret_cast<const uint2*>(src);
@@ -1625,7 +1641,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                 }
                 if (!ok) out.ovf[atomicAdd(out.novf, 1)] = int32_t(gi);
                 if (out.where) out.where[gi] = ok ? dst : -1;
-                if (out.pred) atomicAdd(out.err, fabs(double(out.pred[gi]) - log2(1.0 + double(total))));
+                if (out.pred) err_sum += fabs(double(out.pred[gi]) - log2(1.0 + double(total)));
             } else if (total != int(o1 - o0)) {
                 atomicOr(flags, STC_FLAG_INTERNAL);
             }
@@ -1715,6 +1731,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
             }
         }
     }
+    if (threadIdx.x == 0 && err_sum != 0.0) atomicAdd(out.err, err_sum);
 }
 
 // ----------------------------------------------------------------- host side
@@ -1876,7 +1893,7 @@ bool wr_supported(int alg) {
 template <int ALG, int WARPS, int VCAP>
 stc_status launch_wr_numeric(stc_handle* h, const SpgRows& R, const int32_t* row_mat, const int32_t* rowlist,
                              const int* nlist, int* counter, const int64_t* c_ptr, int32_t* c_col, void* c_val,
-                             int64_t NR, stc_stream s) {
+                             int64_t NR, const uint32_t* bm, stc_stream s) {
     auto kern = k_wr_numeric<ALG, WARPS, VCAP>;
     const size_t smem = WARPS * wr_warp_bytes<ALG, VCAP>();
     STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -1886,7 +1903,7 @@ stc_status launch_wr_numeric(stc_handle* h, const SpgRows& R, const int32_t* row
     int64_t grid = int64_t(per_sm) * h->num_sms;
     if (grid * WARPS > NR) grid = (NR + WARPS - 1) / WARPS;
     kern<<<unsigned(grid > 0 ? grid : 1), WARPS * 32, smem, s>>>(R, row_mat, rowlist, nlist, counter, c_ptr, c_col,
-                                                                c_val, h->d_flags);
+                                                                c_val, h->d_flags, bm);
     STC_LAUNCH_CHECK();
     stc_count(h);
     return STC_OK;
@@ -1897,23 +1914,23 @@ stc_status launch_wr_numeric(stc_handle* h, const SpgRows& R, const int32_t* row
 template <int ALG>
 stc_status launch_wr_numeric_any(stc_handle* h, bool wide, const SpgRows& R, const int32_t* row_mat,
                                  const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
-                                 int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+                                 int32_t* c_col, void* c_val, int64_t NR, const uint32_t* bm, stc_stream s) {
     if (wide)
         return launch_wr_numeric<ALG, WR_NUM_WARPS, WR_VCAP>(h, R, row_mat, rowlist, nlist, counter, c_ptr, c_col,
-                                                             c_val, NR, s);
+                                                             c_val, NR, bm, s);
     return launch_wr_numeric<ALG, WR_NUM_WARPS_S, WR_VCAP_S>(h, R, row_mat, rowlist, nlist, counter, c_ptr, c_col,
-                                                             c_val, NR, s);
+                                                             c_val, NR, bm, s);
 }
 
 stc_status run_wr_numeric(stc_handle* h, int alg, bool wide, const SpgRows& R, const int32_t* row_mat,
                           const int32_t* rowlist, const int* nlist, int* counter, const int64_t* c_ptr,
-                          int32_t* c_col, void* c_val, int64_t NR, stc_stream s) {
+                          int32_t* c_col, void* c_val, int64_t NR, const uint32_t* bm, stc_stream s) {
     switch (alg) {
-    case ALG_PT_F32: return launch_wr_numeric_any<ALG_PT_F32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
-    case ALG_PT_F64: return launch_wr_numeric_any<ALG_PT_F64>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
-    case ALG_MP_I32: return launch_wr_numeric_any<ALG_MP_I32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
-    case ALG_MP_F32: return launch_wr_numeric_any<ALG_MP_F32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
-    case ALG_BOOL: return launch_wr_numeric_any<ALG_BOOL>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, s);
+    case ALG_PT_F32: return launch_wr_numeric_any<ALG_PT_F32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, bm, s);
+    case ALG_PT_F64: return launch_wr_numeric_any<ALG_PT_F64>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, bm, s);
+    case ALG_MP_I32: return launch_wr_numeric_any<ALG_MP_I32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, bm, s);
+    case ALG_MP_F32: return launch_wr_numeric_any<ALG_MP_F32>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, bm, s);
+    case ALG_BOOL: return launch_wr_numeric_any<ALG_BOOL>(h, wide, R, row_mat, rowlist, nlist, counter, c_ptr, c_col, c_val, NR, bm, s);
     default: return STC_ERR_ALGEBRA;
     }
 }
@@ -1997,6 +2014,18 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     SpgRows R{};
     R.nb = nb;
     SpgArgs* table_d = nullptr;
+    // warp-per-row passes: every matrix's row bitmaps (ceil(ncols / 32) words a row),
+    // written by the count pass and read by the numeric pass
+    std::vector<SpgArgs> args_w;
+    int64_t bm_words = 0;
+    if (warp_path) {
+        args_w.assign(args_h, args_h + nb);
+        for (int b = 0; b < nb; ++b) {
+            args_w[b].bm_off = bm_words;
+            bm_words += args_w[b].nA * ((args_w[b].ncols + 31) / 32);
+        }
+        args_h = args_w.data();
+    }
     if (nb == 1) {
         R.one = args_h[0];
     } else {
@@ -2014,6 +2043,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     int* ints = sc.get<int>(2 * NBINS_ALL + 24);
     int64_t* bounds_d = sc.get<int64_t>(size_t(nb) + 1);
     int32_t* row_mat = (warp_path && nb > 1) ? sc.get<int32_t>(size_t(NR)) : nullptr;
+    uint32_t* bm = warp_path ? sc.get<uint32_t>(size_t(bm_words) + 1) : nullptr;
     if (sc.failed) return fail(STC_ERR_OOM);
     if (cudaMemsetAsync(ints, 0, sizeof(int) * (2 * NBINS_ALL + 24), s) != cudaSuccess) return fail(STC_ERR_CUDA);
     int* bin_count = ints;
@@ -2036,10 +2066,16 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     const size_t rec_bytes = rank_layout(ncell_max, 0, 0, 4, false).winfirst;
     uint4* rec = nullptr;
     int2* rec_meta = nullptr;  // per record: (number of words of a sparse record or -1, row count)
-    if (NR > 0 && !warp_path && double(NR) * double(rec_bytes) <= RK_RECORD_BUDGET) {
+    // (warp path: records only serve the heavy rows of the CTA kernels; kept when a
+    // slot per row costs at most 1 GB)
+    if (NR > 0 && double(NR) * double(rec_bytes) <= (warp_path ? 1e9 : RK_RECORD_BUDGET)) {
         rec = sc.get<uint4>(size_t(NR) * (rec_bytes / 16));
         rec_meta = sc.get<int2>(size_t(NR));
         if (!rec || !rec_meta) return fail(STC_ERR_OOM);
+        // only the CTA symbolic pass writes records; rows counted by the warp pass
+        // keep (-1, -1) and are rebuilt by the CTA numeric kernel if they go there
+        if (warp_path && cudaMemsetAsync(rec_meta, 0xff, sizeof(int2) * size_t(NR), s) != cudaSuccess)
+            return fail(STC_ERR_CUDA);
     }
     // ints past the bins: [0] nlist, [1..3] pass counters, [4] max row, [5..6] light split,
     // [8..10] numeric list sizes, [11..13] their counters, [14] count-pass counter,
@@ -2060,7 +2096,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
             int64_t grid = int64_t(per_sm) * h->num_sms;
             if (grid > NR) grid = NR;
             kern<<<unsigned(grid), RK_SYM_NT, smem, s>>>(R, ncell_max, rowlist, wr_heavy, counters, c_ptr + 1,
-                                                         max_nnz, nullptr, nullptr, 0);
+                                                         max_nnz, rec, rec_meta, cfg.vcap - RK_CELL);
             if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
             stc_count(h);
         }
@@ -2071,7 +2107,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         int64_t grid = int64_t(per_sm) * h->num_sms;
         if (grid * WR_COUNT_WARPS > NR) grid = (NR + WR_COUNT_WARPS - 1) / WR_COUNT_WARPS;
         kern<<<unsigned(grid), WR_COUNT_WARPS * 32, 0, s>>>(R, row_mat, rowlist, wr_heavy, nlist,
-                                                           ints + 2 * NBINS_ALL + 14, c_ptr + 1, max_nnz);
+                                                           ints + 2 * NBINS_ALL + 14, c_ptr + 1, max_nnz, bm);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
         stc_count(h);
     } else if (NR > 0) {
@@ -2171,7 +2207,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         for (int b = WR_UB_LOG2 + 1; b < NBINS; ++b) wr_heavy_rows += stage_bins[b];
         if (max_row <= WR_VCAP_S && wr_heavy_rows == 0) {
             if ((st = run_wr_numeric(h, alg, false, R, row_mat, rowlist, nlist, wcounter, c_ptr, c_col, c_val, NR,
-                                     s)) != STC_OK)
+                                     bm, s)) != STC_OK)
                 return fail(st);
         } else {
             int32_t* lists = sc.get<int32_t>(3 * size_t(NR));
@@ -2184,15 +2220,15 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
             stc_count(h);
             if (max_row > WR_VCAP || wr_heavy_rows > 0) {
                 if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, lists + 2 * NR, nsplit + 2, wcounter + 2, out,
-                                          c_col, c_val, NR, s)) != STC_OK)
+                                          c_col, c_val, NR, s, rec, rec_meta)) != STC_OK)
                     return fail(st);
             }
             if (max_row > WR_VCAP_S &&
                 (st = run_wr_numeric(h, alg, true, R, row_mat, lists + NR, nsplit + 1, wcounter + 1, c_ptr, c_col,
-                                     c_val, NR, s)) != STC_OK)
+                                     c_val, NR, bm, s)) != STC_OK)
                 return fail(st);
             if ((st = run_wr_numeric(h, alg, false, R, row_mat, lists, nsplit, wcounter, c_ptr, c_col, c_val, NR,
-                                     s)) != STC_OK)
+                                     bm, s)) != STC_OK)
                 return fail(st);
         }
         if ((st = run_copy_any(h, alg, R, rowlist, nlist, bin_count + BIN_COPY, c_ptr, c_col, c_val, s)) != STC_OK)
@@ -2212,10 +2248,8 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
                 return fail(st);
             cudaStream_t aux;
             if ((st = stc_fork(h, s, &aux)) != STC_OK) return fail(st);
-            const size_t rec16 = rec_bytes / 16;
             st = run_numeric_any(h, alg, R, ncell_max, lcfg, rowlist + n_heavy, split + 1, counters + 2, out, c_col,
-                                 c_val, NR, aux, rec ? rec + size_t(n_heavy) * rec16 : nullptr,
-                                 rec_meta ? rec_meta + n_heavy : nullptr);
+                                 c_val, NR, aux, rec, rec_meta);
             const stc_status sj = stc_join(h, s);
             if (st != STC_OK) return fail(st);
             if (sj != STC_OK) return fail(sj);
@@ -2889,9 +2923,9 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
         return fail(stc_flags_to_status(f));
     }
     const int max_cap = stage_i[1];
-    // the slots, then an overflow pool of an eighth of them for rows the model
+    // the slots, then an overflow pool of a quarter of them for rows the model
     // under-sized (only rows that miss the pool too are recomputed)
-    const int64_t pool = S_total / 8 + 4096;
+    const int64_t pool = S_total / 4 + 4096;
     int32_t* scol = sc.get<int32_t>(size_t(S_total + pool));
     unsigned char* sval = sc.get<unsigned char>(size_t(S_total + pool) * vbytes);
     int64_t* where = sc.get<int64_t>(size_t(NR) + 1);
@@ -3098,7 +3132,7 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
             max_cap[t] = mc[t];
         }
     }
-    // per slab: the slots, then an overflow pool of an eighth of them
+    // per slab: the slots, then an overflow pool of a quarter of them
     std::vector<int64_t> pool_t(S, 0);
     int64_t* wheres = sc.get<int64_t>(size_t(S) * size_t(NR) + 1);
     unsigned long long* pool_used = sc.get<unsigned long long>(size_t(S));
@@ -3107,7 +3141,7 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         return fail(STC_ERR_CUDA);
     for (int t = 0; t < S && NR > 0; ++t) {
         scratch_total += S_t[t];
-        pool_t[t] = S_t[t] / 8 + 4096;
+        pool_t[t] = S_t[t] / 4 + 4096;
         s_cols[t] = sc.get<int32_t>(size_t(S_t[t] + pool_t[t]));
         s_vals[t] = sc.get<unsigned char>(size_t(S_t[t] + pool_t[t]) * vbytes);
         if (!s_cols[t] || !s_vals[t]) return fail(STC_ERR_OOM);
@@ -3698,4 +3732,86 @@ stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, con
 stc_status stc_row_counts_impl(stc_handle* h, const stc_csr* A, const stc_csr* B, int64_t* counts,
                                const stc_opts* opts, stc_stream s) {
     return row_counts_impl(h, A, B, counts, !(opts && opts->skip_validation), s);
+}
+
+// ----------------------------------------------------------------- calibration
+//
+// The rate at which the numeric rank kernel's accumulator can absorb products:
+// one CTA of 1024 threads per SM combines `iters` x 8 products per thread into a
+// shared-memory array of 8192 accumulators at pseudo-random positions (a linear
+// congruential sequence per thread), with the algebra's (+) exactly as the numeric
+// kernel applies it (fp64 (+,x): compare-and-swap of an fma).
+namespace {
+
+constexpr int CAL_SLOTS = 8192;
+
+template <int ALG>
+__global__ void __launch_bounds__(1024, 1) k_calibrate_acc(int iters, unsigned long long* sink) {
+    using T = Tr<ALG>;
+    using Acc = typename T::Acc;
+    __shared__ Acc acc[CAL_SLOTS];
+    for (int i = threadIdx.x; i < CAL_SLOTS; i += blockDim.x) acc[i] = T::empty();
+    __syncthreads();
+    unsigned s = threadIdx.x * 2654435761u + blockIdx.x * 97u + 1u;
+    const typename T::A a = typename T::A(1);
+    const typename T::B b = typename T::B(1);
+    for (int it = 0; it < iters; ++it) {
+        s = s * 1664525u + 1013904223u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) T::combine(acc, int(((s >> 7) + unsigned(u) * 1031u) & (CAL_SLOTS - 1)), a, b);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long x = 0;
+        for (int i = 0; i < 8; ++i) x += (unsigned long long)(acc[i] != T::empty());
+        atomicAdd(sink, x);
+    }
+}
+
+template <int ALG>
+stc_status calibrate_acc(stc_handle* h, double* rate, stc_stream s) {
+    StcScratch sc(h, s);
+    unsigned long long* sink = sc.get<unsigned long long>(1);
+    if (!sink) return STC_ERR_OOM;
+    STC_CUDA_TRY(cudaMemsetAsync(sink, 0, sizeof(unsigned long long), s));
+    const int iters = 1024;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    STC_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return STC_ERR_CUDA;
+    }
+    float best = 0.0f;
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {  // the first run warms up; the fastest of the others counts
+        ok = cudaEventRecord(e0, s) == cudaSuccess;
+        k_calibrate_acc<ALG><<<unsigned(h->num_sms), 1024, 0, s>>>(iters, sink);
+        ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(e1, s) == cudaSuccess &&
+             cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.0f;
+        ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        stc_count(h);
+        if (ok && rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok || !(best > 0.0f)) {
+        (void)cudaGetLastError();
+        return STC_ERR_CUDA;
+    }
+    *rate = double(h->num_sms) * 1024.0 * iters * 8.0 / (double(best) * 1e-3);
+    return STC_OK;
+}
+
+}  // namespace
+
+stc_status stc_calibrate_accumulate_impl(stc_handle* h, int alg, double* rate, stc_stream s) {
+    switch (alg) {
+    case ALG_PT_F32: return calibrate_acc<ALG_PT_F32>(h, rate, s);
+    case ALG_PT_F64: return calibrate_acc<ALG_PT_F64>(h, rate, s);
+    case ALG_MP_I32: return calibrate_acc<ALG_MP_I32>(h, rate, s);
+    case ALG_MP_F32: return calibrate_acc<ALG_MP_F32>(h, rate, s);
+    case ALG_BOOL: return calibrate_acc<ALG_BOOL>(h, rate, s);
+    default: return STC_ERR_ALGEBRA;
+    }
 }

@@ -635,3 +635,9 @@ extern "C" stc_status stc_contract_spgemm_learned(stc_handle* h, stc_algebra alg
         if (opts->light_rows < -1 || opts->light_rows > 30) return STC_ERR_INVALID_ARG;
     return stc_spgemm_learned_impl(h, alg, A, B, C, weights, margin, stats, opts, stream);
 }
+
+extern "C" stc_status stc_calibrate_accumulate(stc_handle* h, stc_algebra alg, double* updates_per_s,
+                                               stc_stream stream) {
+    if (!h || !updates_per_s) return STC_ERR_INVALID_ARG;
+    return stc_calibrate_accumulate_impl(h, int(alg), updates_per_s, stream);
+}

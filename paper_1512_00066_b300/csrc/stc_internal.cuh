@@ -227,6 +227,7 @@ stc_status stc_spgemm_masked_impl(stc_handle* h, int alg, const stc_csr* A, cons
                                   void* c_val, const stc_opts* opts, stc_stream s);
 stc_status stc_autotune_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, int32_t* best_out,
                              int32_t* cand_out, float* ms_out, int32_t* ncand_out, stc_stream s);
+stc_status stc_calibrate_accumulate_impl(stc_handle* h, int alg, double* rate, stc_stream s);
 stc_status stc_row_counts_impl(stc_handle* h, const stc_csr* A, const stc_csr* B, int64_t* counts,
                                const stc_opts* opts, stc_stream s);
 stc_status stc_spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const stc_csr* B, stc_csr* C,
