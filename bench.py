@@ -341,14 +341,17 @@ def run_stc(args):
     if not args.no_e2e:
         e2e = measure_e2e(args, stc, H, wl, dev)
     forms = {}
-    if not args.no_forms and wl["scale"] is not None and rank == 0:
+    if not args.no_forms and rank == 0:
         H.set_timing(False)
         want = set(args.forms.split(","))
-        if "bf" in want:
+        rmat = wl["scale"] is not None  # forms that run on the step's own R-MAT graph
+        if "bf" in want and rmat:
             forms["bellman_ford_drivers"] = measure_bf_drivers(stc, H, wl)
-        if "learned" in want:
+        if "er4096" in want:
+            forms["er4096"] = measure_er4096(stc, H)
+        if "learned" in want and rmat:
             forms["learned_vs_plain"] = measure_learned(stc, H, wl, dev)
-        if "masked" in want:
+        if "masked" in want and rmat:
             forms["masked_vs_plain"] = measure_masked(stc, H, wl)
         if "apsp" in want:
             forms["apsp_path_doubling"] = measure_apsp(stc, H)
@@ -356,10 +359,8 @@ def run_stc(args):
             forms["spmm_e1"] = measure_spmm_e1(stc, H)
         if "mlp" in want:
             forms["mlp_forward"] = measure_mlp(stc, H)
-        if "er4096" in want:
-            forms["er4096"] = measure_er4096(stc, H)
         if "batched" in want:
-            forms["batched_vs_per_call"] = measure_batched(stc, H)
+            forms["batched_vs_per_call"] = measure_batched(stc, H, args.batched_pairs, not args.batched_no_per_call)
         if "mfbc" in want:
             forms["mfbc"] = measure_mfbc(stc, H, scale=args.mfbc_scale, nsrc=args.mfbc_sources)
 
@@ -623,12 +624,13 @@ def measure_spmm_e1(stc, H, n=16384, k=8192, densities=(0.01, 0.16)):
     return out
 
 
-def measure_batched(stc, H):
+def measure_batched(stc, H, npairs=4096, per_call=True):
     """4096 independent (+,x) fp32 pairs: one batched call vs one call per pair.
     Roofline: the row-wise traffic model summed over the pairs (gustavson_bytes)
-    over the batched call's time, against the measured HBM bandwidth."""
+    over the batched call's time, against the measured HBM bandwidth.  npairs and
+    per_call select a smaller batch and skip the per-call loop (profiling runs)."""
     import torch
-    sizes, As, Bs = W.powerlaw_batch(4096, 64, 16384, 2.1, 4, 64, seed=0)
+    sizes, As, Bs = W.powerlaw_batch(npairs, 64, 16384, 2.1, 4, 64, seed=0)
     dA = [stc.DeviceCsr.from_host(a.nrows, a.ncols, a.rowptr, a.col, a.val) for a in As]
     dB = [stc.DeviceCsr.from_host(b.nrows, b.ncols, b.rowptr, b.col, b.val) for b in Bs]
     nprod = sum(int(np.diff(b.rowptr)[a.col].sum()) for a, b in zip(As, Bs))
@@ -644,9 +646,9 @@ def measure_batched(stc, H):
     def per_call():
         for a, b in zip(dA, dB):
             H.spgemm(stc.PLUS_TIMES_F32, a, b)
-    t_p = _timed(per_call, 1)
+    t_p = _timed(per_call, 1) if per_call else float("nan")
     torch.cuda.empty_cache()
-    return {"unit": UNIT, "workload": "4096 pairs, rows power-law [64,16384] exp 2.1, U{4..64}/row, N(0,1) fp32",
+    return {"unit": UNIT, "workload": f"{npairs} pairs, rows power-law [64,16384] exp 2.1, U{{4..64}}/row, N(0,1) fp32",
             "products": nprod, "nnzC": int(nnz["c"].sum()), "batched": nprod / t_b, "per_call": nprod / t_p,
             "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p},
             "roofline": {"bound": "hbm", "algorithmic_bytes": gbytes, "achieved": gbytes / t_b / 1e9, "peak": hbm,
@@ -840,6 +842,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mfbc-scale", type=int, default=22, help="R-MAT scale of the mfbc form")
     ap.add_argument("--mfbc-sources", type=int, default=4096, help="sampled sources of the mfbc form")
+    ap.add_argument("--batched-pairs", type=int, default=4096, help="pairs of the batched form")
+    ap.add_argument("--batched-no-per-call", action="store_true",
+                    help="skip the one-call-per-pair comparison of the batched form")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned / batched / centrality measurements")
     args = ap.parse_args()

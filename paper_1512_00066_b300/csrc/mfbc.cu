@@ -445,8 +445,11 @@ __global__ void k_mf_back_check(MfState st, int64_t n, int* flags, int in_graph,
 }
 
 // bc[v] += sum over sources s != v of delta_s(v).
+// skip (may be null): when *skip != 0 the batch's results are discarded (the
+// unit-length kernels gave up and the batch is recomputed) and nothing is added.
 __global__ void __launch_bounds__(MF_NT) k_mf_bc(MfState st, int64_t n, const int32_t* __restrict__ src,
-                                                 double* __restrict__ bc) {
+                                                 double* __restrict__ bc, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const int S = st.S;
     const int s = threadIdx.x;
     __shared__ double red[MF_NT / 32];
@@ -505,6 +508,259 @@ __global__ void k_mf_check_len(const int32_t* __restrict__ w, int64_t nnz, int* 
     for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nnz; p += int64_t(gridDim.x) * blockDim.x)
         bad |= w[p] < 1;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, STC_FLAG_INVALID);
+}
+
+// ------------------------------------------------------------------- unit lengths: bitset frontiers
+//
+// With unit lengths every source's search is a breadth-first search and all of a
+// batch's searches advance one level per round together, so a round is described by
+// per-vertex source masks (256 bits for a batch of up to 256 sources):
+//   vis[v]  sources that reached v at a level <= r,
+//   fm[v]   sources for which v is on level r (the frontier),
+//   nxt[v]  sources reaching v in round r (built by the round, level r + 1).
+// A round takes the frontier's work items one warp each, one out-edge per lane:
+// cand = fm[u] & ~vis[v] are the sources for which u -> v is a shortest-path edge;
+// for each of them sigma_s(v) gathers sigma_s(u) (an fp64 atomic add of integers,
+// exact below 2^53) and nxt[v] collects them.  The edge costs a 32-byte mask read
+// whatever the number of sources; only shortest-path (edge, source) pairs cost a
+// multiplicity update.  The update step turns nxt into distances, multiplicities,
+// the next frontier and its work items.  Every round's items are kept: round l's items
+// are the vertices at level l for some source.
+//
+// Backward, level by level from the deepest: for a vertex v at level l of source s,
+// delta_s(v) = sigma_s(v) * sum over out-edges v -> w with d_s(w) = l + 1 of
+// (1 + delta_s(w)) / sigma_s(w).  Block per work item of level l, thread per source,
+// pulling the successors' coefficients (no successor counts); items of one vertex
+// add their partial sums atomically, then each vertex's sum becomes delta and its
+// coefficient.
+
+constexpr int MU_W = 8;                  // mask words per vertex (MF_NT = 256 sources)
+constexpr int MU_MAX_ROUNDS = 4096;      // rounds recorded; deeper searches use the general kernels
+enum : int {
+    MU_C_ITEMS = 0,   // items appended by the current round's update
+    MU_C_ROUND = 1,   // forward round / backward level
+    MU_C_GO = 2,      // 1 while the last checked loop goes on
+    MU_C_FAIL = 3,    // item buffer or round table exhausted: rerun with the general kernels
+    MU_C_LAST = 4,    // deepest level reached
+    MU_C_NUM = 8,
+};
+
+struct MuState {
+    uint32_t* vis;
+    uint32_t* nxt;
+    uint32_t* fm;
+    int2* items;       // all rounds' work items, round r at [off[r], off[r + 1])
+    int64_t item_cap;
+    int* off;          // MU_MAX_ROUNDS + 2 offsets
+    int* cnt;          // MU_C_* counters
+};
+
+__device__ __forceinline__ void mu_load_mask(const uint32_t* __restrict__ m, int32_t v, uint32_t (&x)[MU_W]) {
+    const uint4* p = reinterpret_cast<const uint4*>(m + int64_t(v) * MU_W);
+    const uint4 a = p[0], b = p[1];
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+
+// Sources: level 0, one path; their vertices form round 0's items.
+__global__ void k_mu_seed(MfGraph g, MfState st, MuState u, const int32_t* __restrict__ src) {
+    const int s = threadIdx.x;
+    if (s < st.S) {
+        const int32_t v = src[s];
+        const int64_t i = int64_t(v) * st.S + s;
+        st.d[i] = 0;
+        st.sig[i] = 1.0;
+        atomicOr(&u.vis[int64_t(v) * MU_W + (s >> 5)], 1u << (s & 31));
+        atomicOr(&u.fm[int64_t(v) * MU_W + (s >> 5)], 1u << (s & 31));
+        if (atomicExch(&st.stamp[v], -2) != -2) {
+            const int nch = mf_chunks(g, v);
+            const int base = atomicAdd(&u.cnt[MU_C_ITEMS], nch);
+            for (int c = 0; c < nch; ++c) u.items[base + c] = make_int2(v, c);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u.off[0] = 0;
+        u.off[1] = u.cnt[MU_C_ITEMS];
+        u.cnt[MU_C_ITEMS] = 0;
+        u.cnt[MU_C_ROUND] = 0;
+    }
+}
+
+// One round: warp per item of the frontier, lane per out-edge.
+__global__ void __launch_bounds__(256) k_mu_push(MfGraph g, MfState st, MuState u) {
+    const int S = st.S;
+    const int lane = threadIdx.x & 31;
+    const int r = u.cnt[MU_C_ROUND];
+    const int i0 = u.off[r], i1 = u.off[r + 1];
+    const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+    for (int t = i0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); t < i1; t += nwarps) {
+        const int2 it = u.items[t];
+        const int32_t x = it.x;
+        int64_t e0, e1;
+        mf_item_edges(g, it, e0, e1);
+        uint32_t F[MU_W];
+        mu_load_mask(u.fm, x, F);
+        const double* __restrict__ sx = st.sig + int64_t(x) * S;
+        for (int64_t p = e0 + lane; p < e1; p += 32) {
+            const int32_t v = g.col[p];
+            if ((uint64_t)v >= (uint64_t)g.n) continue;
+            uint32_t V[MU_W];
+            mu_load_mask(u.vis, v, V);
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < MU_W; ++k) {
+                uint32_t c = F[k] & ~V[k];
+                if (!c) continue;
+                any = true;
+                atomicOr(&u.nxt[int64_t(v) * MU_W + k], c);
+                while (c) {
+                    const int s = k * 32 + __ffs(c) - 1;
+                    c &= c - 1;
+                    atomicAdd(&st.dln[int64_t(v) * S + s], sx[s]);
+                }
+            }
+            if (any) mf_touch(st.stamp, st.list[1], &st.cnt[MF_C_TOUCHED], v, r);
+        }
+    }
+}
+
+// End of a round's pushes: every touched vertex turns its new sources into distance
+// r + 1 and multiplicity, becomes part of the next frontier and appends its items.
+__global__ void __launch_bounds__(256) k_mu_update(MfGraph g, MfState st, MuState u) {
+    const int S = st.S;
+    const int lane = threadIdx.x & 31;
+    const int r = u.cnt[MU_C_ROUND];
+    const int nT = st.cnt[MF_C_TOUCHED];
+    const int base_next = u.off[r + 1];
+    const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+    for (int t = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); t < nT; t += nwarps) {
+        const int32_t v = st.list[1][t];
+        uint32_t N[MU_W];
+        mu_load_mask(u.nxt, v, N);
+        __syncwarp();
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < MU_W; ++k) {
+            if (!N[k]) continue;
+            any = true;
+            const int s = k * 32 + lane;
+            if ((N[k] >> lane) & 1u) {
+                const int64_t i = int64_t(v) * S + s;
+                st.d[i] = r + 1;
+                st.sig[i] = st.dln[i];
+                st.dln[i] = 0.0;
+            }
+        }
+        if (lane < MU_W) {
+            const int64_t q = int64_t(v) * MU_W + lane;
+            u.fm[q] = N[lane];
+            u.vis[q] |= N[lane];
+            u.nxt[q] = 0u;
+        }
+        if (any && lane == 0) {
+            const int nch = mf_chunks(g, v);
+            const int b = atomicAdd(&u.cnt[MU_C_ITEMS], nch);
+            if (int64_t(base_next) + b + nch <= u.item_cap) {
+                for (int c = 0; c < nch; ++c) u.items[base_next + b + c] = make_int2(v, c);
+            } else {
+                u.cnt[MU_C_FAIL] = 1;
+            }
+        }
+    }
+}
+
+// End of a forward round (one thread).
+__global__ void k_mu_fwd_check(MfState st, MuState u, int in_graph, cudaGraphConditionalHandle loop) {
+    const int r = u.cnt[MU_C_ROUND];
+    const int n_next = u.cnt[MU_C_ITEMS];
+    unsigned go = 0;
+    if (n_next > 0 && !u.cnt[MU_C_FAIL]) {
+        if (r + 2 > MU_MAX_ROUNDS || int64_t(u.off[r + 1]) + n_next > u.item_cap) {
+            u.cnt[MU_C_FAIL] = 1;
+        } else {
+            u.off[r + 2] = u.off[r + 1] + n_next;
+            u.cnt[MU_C_ROUND] = r + 1;
+            go = 1;
+        }
+    }
+    if (!go) u.cnt[MU_C_LAST] = r;  // levels 0 .. r hold items
+    u.cnt[MU_C_ITEMS] = 0;
+    st.cnt[MF_C_TOUCHED] = 0;
+    u.cnt[MU_C_GO] = int(go);
+    st.cnt[MF_C_GO] = int(go);
+    if (in_graph) cudaGraphSetConditional(loop, go);
+}
+
+// Backward start: from the deepest level.
+__global__ void k_mu_back_init(MuState u) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) u.cnt[MU_C_ROUND] = u.cnt[MU_C_FAIL] ? -1 : u.cnt[MU_C_LAST];
+}
+
+// Partial sums of level l's items: acc (st.dl) += sum over the item's out-edges
+// v -> w with d_s(w) = l + 1 of coef_s(w) (st.dln of level l + 1).
+__global__ void __launch_bounds__(MF_NT) k_mu_pull(MfGraph g, MfState st, MuState u) {
+    const int S = st.S;
+    const int s = threadIdx.x;
+    const int l = u.cnt[MU_C_ROUND];
+    if (l < 0) return;
+    const int i0 = u.off[l], i1 = u.off[l + 1];
+    for (int t = i0 + blockIdx.x; t < i1; t += gridDim.x) {
+        const int2 it = u.items[t];
+        const int32_t v = it.x;
+        int64_t e0, e1;
+        mf_item_edges(g, it, e0, e1);
+        const bool act = s < S && st.d[int64_t(v) * S + s] == l;
+        if (!act) continue;  // a warp whose sources are all elsewhere skips the item
+        double acc = 0.0;
+        for (int64_t p0 = e0; p0 < e1; p0 += MF_UNR) {
+            int32_t w[MF_UNR];
+            int dw[MF_UNR];
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) {
+                const int64_t p = p0 + k;
+                w[k] = -1;
+                if (p < e1) {
+                    const int32_t y = g.col[p];
+                    if ((uint64_t)y < (uint64_t)g.n) w[k] = y;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k) dw[k] = w[k] >= 0 ? st.d[int64_t(w[k]) * S + s] : -1;
+#pragma unroll
+            for (int k = 0; k < MF_UNR; ++k)
+                if (dw[k] == l + 1) acc += st.dln[int64_t(w[k]) * S + s];
+        }
+        if (acc != 0.0) atomicAdd(&st.dl[int64_t(v) * S + s], acc);
+    }
+}
+
+// Level l's sums become delta_s(v) = sigma_s(v) * sum and coef_s(v) = (1 + delta) /
+// sigma (one block per vertex: its chunk-0 item); then the next level up.
+__global__ void __launch_bounds__(MF_NT) k_mu_final(MfState st, MuState u) {
+    const int S = st.S;
+    const int s = threadIdx.x;
+    const int l = u.cnt[MU_C_ROUND];
+    if (l < 0) return;
+    const int i0 = u.off[l], i1 = u.off[l + 1];
+    for (int t = i0 + blockIdx.x; t < i1; t += gridDim.x) {
+        const int2 it = u.items[t];
+        if (it.y != 0 || s >= S) continue;
+        const int64_t i = int64_t(it.x) * S + s;
+        if (st.d[i] != l) continue;
+        const double sg = st.sig[i];
+        const double dlt = sg * st.dl[i];
+        st.dl[i] = dlt;
+        st.dln[i] = (1.0 + dlt) / sg;
+    }
+}
+
+__global__ void k_mu_back_check(MfState st, MuState u, int in_graph, cudaGraphConditionalHandle loop) {
+    const int l = u.cnt[MU_C_ROUND];
+    const unsigned go = l > 0 ? 1u : 0u;
+    u.cnt[MU_C_ROUND] = l - 1;
+    st.cnt[MF_C_GO] = int(go);
+    if (in_graph) cudaGraphSetConditional(loop, go);
 }
 
 unsigned grid_for(stc_handle* h, int64_t work, int per_sm) {
@@ -566,7 +822,7 @@ stc_status mf_run_host(stc_handle* h, const MfBatch& b, stc_stream s) {
         STC_CUDA_TRY(cudaStreamSynchronize(s));
         if (!*go) break;
     }
-    k_mf_bc<<<grid_for(h, g.n, 32), MF_NT, 0, s>>>(st, g.n, b.src, b.bc);
+    k_mf_bc<<<grid_for(h, g.n, 32), MF_NT, 0, s>>>(st, g.n, b.src, b.bc, nullptr);
     STC_LAUNCH_CHECK();
     stc_count(h);
     return STC_OK;
@@ -671,7 +927,8 @@ cudaError_t mf_build_graph(stc_handle* h, MfBatch b, MfGraphExec& x) {
         void* a_chk[] = {&b.st, &n, &flags, &in_graph, &hb};
         MF_G(mf_add_kernel(bb, &k1, nullptr, (const void*)k_mf_back, rg, MF_NT, a_back));
         MF_G(mf_add_kernel(bb, &k2, &k1, (const void*)k_mf_back_check, 1, 1, a_chk));
-        void* a_bc[] = {&b.st, &n, &b.src, &b.bc};
+        const int* no_skip = nullptr;
+        void* a_bc[] = {&b.st, &n, &b.src, &b.bc, &no_skip};
         MF_G(mf_add_kernel(x.graph, &n_bc, &n_bw, (const void*)k_mf_bc, grid_for(h, n, 32), MF_NT, a_bc));
         x.nodes += 4;
     }
@@ -695,6 +952,165 @@ stc_status mf_run(stc_handle* h, const MfBatch& b, MfGraphExec& x, stc_stream s)
     }
     STC_CUDA_TRY(cudaGraphLaunch(x.exec, s));
     stc_count(h, x.nodes);  // each node once (the device repeats the loop bodies)
+    return STC_OK;
+}
+
+// ------------------------------------------------------------------- unit-length drivers
+
+stc_status mu_alloc(StcScratch& sc, const MfGraph& g, MuState& u) {
+    const size_t n = size_t(g.n);
+    u.vis = sc.get<uint32_t>(n * MU_W);
+    u.nxt = sc.get<uint32_t>(n * MU_W);
+    u.fm = sc.get<uint32_t>(n * MU_W);
+    // every vertex on a few levels: eight times one round's worth of items
+    u.item_cap = 8 * (int64_t(g.n) + g.nnz / MF_ITEM_EDGES + 1) + 1024;
+    if (u.item_cap > int64_t(INT32_MAX)) u.item_cap = INT32_MAX;
+    u.items = sc.get<int2>(size_t(u.item_cap));
+    u.off = sc.get<int>(size_t(MU_MAX_ROUNDS) + 2);
+    u.cnt = sc.get<int>(MU_C_NUM);
+    return sc.failed ? STC_ERR_OOM : STC_OK;
+}
+
+stc_status mu_clear(stc_handle* h, const MfBatch& b, const MuState& u, stc_stream s) {
+    const size_t n = size_t(b.g.n);
+    STC_CUDA_TRY(cudaMemsetAsync(u.vis, 0, n * MU_W * 4, s));
+    STC_CUDA_TRY(cudaMemsetAsync(u.nxt, 0, n * MU_W * 4, s));
+    STC_CUDA_TRY(cudaMemsetAsync(u.fm, 0, n * MU_W * 4, s));
+    STC_CUDA_TRY(cudaMemsetAsync(u.cnt, 0, MU_C_NUM * sizeof(int), s));
+    (void)h;
+    return STC_OK;
+}
+
+unsigned mu_warp_grid(stc_handle* h) { return unsigned(h->num_sms * 8); }  // 256-thread CTAs, 64 warps per SM
+
+// Host driver of the unit-length batch: each round, then MF_C_GO read back.
+stc_status mu_run_host(stc_handle* h, const MfBatch& b, const MuState& u, stc_stream s) {
+    const MfGraph& g = b.g;
+    const MfState& st = b.st;
+    const unsigned rg = mf_round_grid(h), wg = mu_warp_grid(h);
+    const cudaGraphConditionalHandle none = 0;
+    int* go = reinterpret_cast<int*>(&h->h_stage[4]);
+    stc_status e;
+    if ((e = mu_clear(h, b, u, s)) != STC_OK) return e;
+    k_mf_init<<<mf_init_grid(h, b), 256, 0, s>>>(g, st);
+    k_mu_seed<<<1, MF_NT, 0, s>>>(g, st, u, b.src);
+    STC_LAUNCH_CHECK();
+    stc_count(h, 2);
+    for (;;) {
+        k_mu_push<<<wg, 256, 0, s>>>(g, st, u);
+        k_mu_update<<<wg, 256, 0, s>>>(g, st, u);
+        k_mu_fwd_check<<<1, 1, 0, s>>>(st, u, 0, none);
+        STC_LAUNCH_CHECK();
+        stc_count(h, 3);
+        STC_CUDA_TRY(cudaMemcpyAsync(go, &u.cnt[MU_C_GO], sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!*go) break;
+    }
+    if (!b.bc) return STC_OK;
+    k_mu_back_init<<<1, 1, 0, s>>>(u);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    for (;;) {
+        k_mu_pull<<<rg, MF_NT, 0, s>>>(g, st, u);
+        k_mu_final<<<rg, MF_NT, 0, s>>>(st, u);
+        k_mu_back_check<<<1, 1, 0, s>>>(st, u, 0, none);
+        STC_LAUNCH_CHECK();
+        stc_count(h, 3);
+        STC_CUDA_TRY(cudaMemcpyAsync(go, &st.cnt[MF_C_GO], sizeof(int), cudaMemcpyDeviceToHost, s));
+        STC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!*go) break;
+    }
+    k_mf_bc<<<grid_for(h, g.n, 32), MF_NT, 0, s>>>(st, g.n, b.src, b.bc, &u.cnt[MU_C_FAIL]);
+    STC_LAUNCH_CHECK();
+    stc_count(h);
+    return STC_OK;
+}
+
+#define MF_G(call)                                  \
+    do {                                            \
+        const cudaError_t e_ = (call);              \
+        if (e_ != cudaSuccess) return e_;           \
+    } while (0)
+
+// Graph driver of the unit-length batch:
+//   seed -> WHILE{push -> update -> check} [-> back_init -> WHILE{pull -> final -> check} -> bc]
+// (the clears and k_mf_init run on the stream before each launch).
+cudaError_t mu_build_graph(stc_handle* h, MfBatch b, MuState u, MfGraphExec& x) {
+    x.reset();
+    MF_G(cudaGraphCreate(&x.graph, 0));
+    const unsigned rg = mf_round_grid(h), wg = mu_warp_grid(h);
+    int in_graph = 1;
+    int64_t n = b.g.n;
+    cudaGraphNode_t n_seed, n_fw;
+    void* a_seed[] = {&b.g, &b.st, &u, &b.src};
+    MF_G(mf_add_kernel(x.graph, &n_seed, nullptr, (const void*)k_mu_seed, 1, MF_NT, a_seed));
+    cudaGraphConditionalHandle hf;
+    cudaGraph_t fb;
+    MF_G(mf_add_while(x.graph, &n_fw, &n_seed, &hf, &fb));
+    {
+        cudaGraphNode_t k1, k2, k3;
+        void* a_gsu[] = {&b.g, &b.st, &u};
+        void* a_chk[] = {&b.st, &u, &in_graph, &hf};
+        MF_G(mf_add_kernel(fb, &k1, nullptr, (const void*)k_mu_push, wg, 256, a_gsu));
+        MF_G(mf_add_kernel(fb, &k2, &k1, (const void*)k_mu_update, wg, 256, a_gsu));
+        MF_G(mf_add_kernel(fb, &k3, &k2, (const void*)k_mu_fwd_check, 1, 1, a_chk));
+    }
+    x.nodes = 4;
+    if (b.bc) {
+        cudaGraphNode_t n_bi, n_bw, n_bc;
+        void* a_u[] = {&u};
+        MF_G(mf_add_kernel(x.graph, &n_bi, &n_fw, (const void*)k_mu_back_init, 1, 1, a_u));
+        cudaGraphConditionalHandle hb;
+        cudaGraph_t bb;
+        MF_G(mf_add_while(x.graph, &n_bw, &n_bi, &hb, &bb));
+        cudaGraphNode_t k1, k2, k3;
+        void* a_pull[] = {&b.g, &b.st, &u};
+        void* a_fin[] = {&b.st, &u};
+        void* a_chk[] = {&b.st, &u, &in_graph, &hb};
+        MF_G(mf_add_kernel(bb, &k1, nullptr, (const void*)k_mu_pull, rg, MF_NT, a_pull));
+        MF_G(mf_add_kernel(bb, &k2, &k1, (const void*)k_mu_final, rg, MF_NT, a_fin));
+        MF_G(mf_add_kernel(bb, &k3, &k2, (const void*)k_mu_back_check, 1, 1, a_chk));
+        const int* skip = &u.cnt[MU_C_FAIL];
+        void* a_bc[] = {&b.st, &n, &b.src, &b.bc, &skip};
+        MF_G(mf_add_kernel(x.graph, &n_bc, &n_bw, (const void*)k_mf_bc, grid_for(h, n, 32), MF_NT, a_bc));
+        x.nodes += 5;
+    }
+    MF_G(cudaGraphInstantiate(&x.exec, x.graph, 0));
+    x.S = b.st.S;
+    return cudaSuccess;
+}
+
+#undef MF_G
+
+// One unit-length batch with the handle's driver; *fallback is set when the
+// bitset kernels gave up (too many rounds or items) and the batch must be run by the
+// general kernels (nothing was added to bc).  Synchronises `s`.
+stc_status mu_run(stc_handle* h, const MfBatch& b, const MuState& u, MfGraphExec& x, bool* fallback, stc_stream s) {
+    *fallback = false;
+    stc_status e;
+    if (h->round_driver == 0) {
+        if ((e = mu_run_host(h, b, u, s)) != STC_OK) return e;
+    } else {
+        if (x.S != b.st.S) {
+            const cudaError_t ce = mu_build_graph(h, b, u, x);
+            if (ce != cudaSuccess) {
+                (void)cudaGetLastError();
+                x.reset();
+                return STC_ERR_CUDA;
+            }
+        }
+        if ((e = mu_clear(h, b, u, s)) != STC_OK) return e;
+        k_mf_init<<<mf_init_grid(h, b), 256, 0, s>>>(b.g, b.st);
+        STC_LAUNCH_CHECK();
+        stc_count(h);
+        STC_CUDA_TRY(cudaGraphLaunch(x.exec, s));
+        stc_count(h, x.nodes);
+    }
+    int* f = reinterpret_cast<int*>(&h->h_stage[3]);
+    *f = 0;
+    STC_CUDA_TRY(cudaMemcpyAsync(f, &u.cnt[MU_C_FAIL], sizeof(int), cudaMemcpyDeviceToHost, s));
+    STC_CUDA_TRY(cudaStreamSynchronize(s));
+    *fallback = *f != 0;
     return STC_OK;
 }
 
@@ -765,7 +1181,17 @@ stc_status stc_mfbc_sssp_impl(stc_handle* h, const stc_csr* G, const int32_t* so
     b.src = d_src;
     STC_CUDA_TRY(cudaMemcpyAsync(d_src, sources, sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, s));
     MfGraphExec x(s);
-    if ((st = mf_run(h, b, x, s)) != STC_OK) return st;
+    bool general = g.w != nullptr;
+    if (!general) {
+        // unit lengths: bitset frontiers (the general kernels when they give up)
+        MuState u{};
+        if ((st = mu_alloc(sc, g, u)) != STC_OK) return st;
+        MfGraphExec xu(s);
+        if ((st = mu_run(h, b, u, xu, &general, s)) != STC_OK) return st;
+        STC_CUDA_TRY(cudaMemcpyAsync(&b.st.cnt[MF_C_FROUND], &u.cnt[MU_C_LAST], sizeof(int), cudaMemcpyDeviceToDevice,
+                                     s));
+    }
+    if (general && (st = mf_run(h, b, x, s)) != STC_OK) return st;
     STC_CUDA_TRY(cudaMemcpyAsync(d_out, b.st.d, sizeof(int) * size_t(g.n) * nsrc, cudaMemcpyDeviceToDevice, s));
     STC_CUDA_TRY(cudaMemcpyAsync(sigma_out, b.st.sig, sizeof(double) * size_t(g.n) * nsrc,
                                  cudaMemcpyDeviceToDevice, s));
@@ -806,11 +1232,15 @@ stc_status stc_mfbc_impl(stc_handle* h, const stc_csr* G, const int32_t* sources
     k_mf_zero<<<grid_for(h, g.n / 256 + 1, 16), 256, 0, s>>>(bc, g.n);
     STC_LAUNCH_CHECK();
     stc_count(h);
-    MfGraphExec x(s);
+    MfGraphExec x(s), xu(s);
+    MuState u{};
+    if (!g.w && (st = mu_alloc(sc, g, u)) != STC_OK) return st;
     for (int32_t b0 = 0; b0 < nsrc; b0 += batch) {
         b.st.S = nsrc - b0 < batch ? nsrc - b0 : batch;
         STC_CUDA_TRY(cudaMemcpyAsync(d_src, sources + b0, sizeof(int32_t) * b.st.S, cudaMemcpyHostToDevice, s));
-        if ((st = mf_run(h, b, x, s)) != STC_OK) return st;
+        bool general = g.w != nullptr;
+        if (!general && (st = mu_run(h, b, u, xu, &general, s)) != STC_OK) return st;
+        if (general && (st = mf_run(h, b, x, s)) != STC_OK) return st;
     }
     return mf_read_flags(h, s);
 }

@@ -164,6 +164,40 @@ def test_round_drivers_agree(H, weighted):
     assert np.array_equal(h[0], g[0]) and np.array_equal(h[1], g[1]) and h[2] == g[2]
     bc_close(g[3], O.brandes(G, src, weighted))
     bc_close(h[3], g[3])
-    # host: 5 kernels per forward round (4 with unit lengths); graph: one node each
-    assert h[4] >= 2 + (5 if weighted else 4) * h[2] and g[4] < h[4]
+    # host: 5 kernels per forward round (3 with unit lengths: bitset push, update,
+    # check); graph: one node each
+    assert h[4] >= 2 + (5 if weighted else 3) * h[2] and g[4] < h[4]
     assert g[5] < h[5]
+
+
+def test_unit_lengths_fall_back_when_the_bitset_kernels_give_up(H):
+    """Unit lengths run on bitset frontiers, which keep every round's work items and
+    at most 4096 rounds.  A path of 5000 vertices needs more rounds, and a cycle with
+    sources all around it puts every vertex on hundreds of levels (more items than
+    kept): both batches are recomputed by the general kernels, with the oracle's
+    centrality and the exact distances and path counts."""
+    n = 5000
+    P = W.csr_from_coo(np.arange(n - 1), np.arange(1, n), n, n)
+    src = np.array([0, 3, 4000], np.int32)
+    bc_close(H.mfbc(to_dev(P), src).cpu().numpy(), O.brandes(P, src, False))
+    check_forward(H, P, src, False)
+    m = 600
+    Cy = W.csr_from_coo(np.arange(m), (np.arange(m) + 1) % m, m, m)
+    src = np.arange(0, m, 2, dtype=np.int32)[:256]
+    bc_close(H.mfbc(to_dev(Cy), src).cpu().numpy(), O.brandes(Cy, src, False))
+    check_forward(H, Cy, src[:100], False)
+
+
+@pytest.mark.parametrize("driver", ["host", "graph"])
+def test_unit_lengths_bitset_kernels_match_brandes_rmat14(H, driver):
+    """The bitset-frontier path on a skewed graph, both round drivers, a ragged last
+    batch: centrality against Brandes and forward distances/path counts exact."""
+    G = graph(14, 21, False)
+    src = W.sample_sources(G, 300, seed=22)
+    try:
+        H.set_round_driver(driver)
+        bc = H.mfbc(to_dev(G), src, batch=128).cpu().numpy()
+        check_forward(H, G, src[:70], False)
+    finally:
+        H.set_round_driver("graph")
+    bc_close(bc, O.brandes(G, src, False))
