@@ -624,11 +624,11 @@ def measure_spmm_e1(stc, H, n=16384, k=8192, densities=(0.01, 0.16)):
     return out
 
 
-def measure_batched(stc, H, npairs=4096, per_call=True):
+def measure_batched(stc, H, npairs=4096, with_per_call=True):
     """4096 independent (+,x) fp32 pairs: one batched call vs one call per pair.
     Roofline: the row-wise traffic model summed over the pairs (gustavson_bytes)
     over the batched call's time, against the measured HBM bandwidth.  npairs and
-    per_call select a smaller batch and skip the per-call loop (profiling runs)."""
+    with_per_call select a smaller batch and skip the per-call loop (profiling runs)."""
     import torch
     sizes, As, Bs = W.powerlaw_batch(npairs, 64, 16384, 2.1, 4, 64, seed=0)
     dA = [stc.DeviceCsr.from_host(a.nrows, a.ncols, a.rowptr, a.col, a.val) for a in As]
@@ -646,7 +646,7 @@ def measure_batched(stc, H, npairs=4096, per_call=True):
     def per_call():
         for a, b in zip(dA, dB):
             H.spgemm(stc.PLUS_TIMES_F32, a, b)
-    t_p = _timed(per_call, 1) if per_call else float("nan")
+    t_p = _timed(per_call, 1) if with_per_call else float("nan")
     torch.cuda.empty_cache()
     return {"unit": UNIT, "workload": f"{npairs} pairs, rows power-law [64,16384] exp 2.1, U{{4..64}}/row, N(0,1) fp32",
             "products": nprod, "nnzC": int(nnz["c"].sum()), "batched": nprod / t_b, "per_call": nprod / t_p,

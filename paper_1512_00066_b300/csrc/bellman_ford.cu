@@ -443,13 +443,17 @@ namespace {
 //   [16, 24)  int[4..5]   grid-barrier state
 //   [24, 28)  int[6]      round count
 //   [28, 32)  int[7]      device flags
+//   [32, 48)  u64[2]      CSR validation counters
 //   [64, 72)  u64         relaxation counter (written by every round, not read back)
 // then, per vertex, the two frontier slots, the round stamp and the fp32 distance key.
 constexpr size_t NOALLOC_HEADER = 256;
 constexpr size_t NOALLOC_RELAX_OFFSET = 64;
 static_assert(NOALLOC_RELAX_OFFSET + sizeof(unsigned long long) <= NOALLOC_HEADER,
               "the relaxation counter must sit inside the cleared header");
-static_assert(8 * sizeof(int) <= NOALLOC_RELAX_OFFSET, "the counters and flags must end before the relaxation counter");
+constexpr size_t NOALLOC_VAL_OFFSET = 32;
+static_assert(8 * sizeof(int) <= NOALLOC_VAL_OFFSET, "the validation counters follow the flags");
+static_assert(NOALLOC_VAL_OFFSET + 2 * sizeof(unsigned long long) <= NOALLOC_RELAX_OFFSET,
+              "the counters and flags must end before the relaxation counter");
 // per vertex: two frontier slots, a round stamp and an fp32 distance key
 constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + size_t(STC_NOALLOC_BF_MAX_VERTICES) * 16;
 
@@ -509,7 +513,10 @@ stc_status run_bf_noalloc(const stc_csr* G, int32_t source, void* dist_out, int3
 
     // the previous call's counters, barrier state and flags are left behind: clear them
     STC_CUDA_TRY(cudaMemsetAsync(base, 0, NOALLOC_HEADER, s));
-    if ((st = stc_validate_csr_flags_async(G, flags, num_sms, s)) != STC_OK) return st;
+    if ((st = stc_validate_csr_flags_async(G, flags,
+                                           reinterpret_cast<unsigned long long*>(base + NOALLOC_VAL_OFFSET), s)) !=
+        STC_OK)
+        return st;
     int64_t blocks = (n + 255) / 256;
     if (blocks > int64_t(num_sms) * 8) blocks = int64_t(num_sms) * 8;
     k_bf_init<ALG><<<unsigned(blocks), 256, 0, s>>>(a, dist, source);

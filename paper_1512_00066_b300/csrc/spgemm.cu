@@ -109,11 +109,12 @@ template <> struct Tr<ALG_PT_F64> {
     using A = double; using B = double; using C = double; using Acc = double;
     static __device__ __forceinline__ Acc empty() { return 0.0; }
     // acc[c] = fma(a, b, acc[c]) by compare-and-swap: one FP64 instruction per
-    // product.  A product rounded and then added by the shared-memory fp64 atomic add
-    // runs faster in isolation on B300 (0.82 against 0.44 updates per clock per SM,
-    // random targets, 1024 threads per SM), but measured slower inside this kernel
-    // (R-MAT 18 numeric phase 27.5 against 25.1 ms); the bits are compared, so a NaN
-    // ends the loop like any other value
+    // product.  The shared-memory fp64 add of a rounded product (atomicAdd, or
+    // red.shared.add.f64 with no return) runs faster in isolation on B300 (0.82
+    // against 0.44 updates per clock per SM; random targets, 1024 threads per SM),
+    // but was slower inside this kernel both ways (R-MAT 18 numeric phase 27.5 and
+    // 27.7 ms against 25.1-25.5 ms); the bits are compared, so a NaN ends the loop
+    // like any other value
     static __device__ __forceinline__ void combine(Acc* acc, int c, A a, B b) {
         unsigned long long* p = reinterpret_cast<unsigned long long*>(&acc[c]);
         unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(p);
@@ -1054,48 +1055,164 @@ __global__ void k_cell_offsets(SpgRows R) {
 // Row analysis over global rows (batch-aware): ub and log2 bins.  With single !=
 // null, a row with one stored entry whose B row is not empty goes to BIN_COPY and
 // its output count is final: single[gi] = ub (one product per output column).
-__global__ void k_row_ub_b(SpgRows R, int64_t NR, int64_t* __restrict__ ub, int* __restrict__ bin_count,
-                           int64_t* __restrict__ single, int32_t* __restrict__ row_mat = nullptr) {
+// Eight lanes sum a row; each 8-lane group takes a chunk of `chunk` consecutive
+// rows, so the matrix of a batch is looked up once per group and matrix.  Chunks
+// are dealt to groups in a scattered order (group g takes chunk g * UB_SPREAD mod
+// the number of chunks; UB_SPREAD is a prime above the chunk count), so that the
+// heavy rows of a power-law matrix, which sit together, spread over the grid.  A
+// group loads the row pointers of eight rows at once (lane j: row j of the window)
+// and walks a row's entries four per lane per round (its loads issued together).  Rows with more than UB_HEAVY
+// stored entries are queued and summed by the whole block at the end.
+constexpr int UB_LANES = 8;
+constexpr int UB_NT = 256;
+constexpr int UB_HEAVY = 256;
+constexpr int UB_QCAP = 128;
+constexpr int UB_UNROLL = 4;
+constexpr int64_t UB_SPREAD = 1000003;
+
+__device__ __forceinline__ void ub_finish(int64_t gi, int64_t len, int64_t sum, int64_t* __restrict__ ub,
+                                          int64_t* __restrict__ single, int* s_bins) {
+    ub[gi] = sum;
+    const bool one = single && len == 1 && sum > 0;
+    if (one) single[gi] = sum;
+    atomicAdd(&s_bins[one ? BIN_COPY : bin_of(sum)], 1);
+}
+
+__global__ void __launch_bounds__(UB_NT, 5) k_row_ub_b(SpgRows R, int64_t NR, int64_t chunk, int64_t nchunks,
+                                                    int64_t spread, int64_t* __restrict__ ub, int* __restrict__ bin_count,
+                                                    int64_t* __restrict__ single,
+                                                    int32_t* __restrict__ row_mat = nullptr) {
     __shared__ int s_bins[NBINS_ALL];
+    __shared__ int64_t s_q[UB_QCAP];
+    __shared__ int s_qb[UB_QCAP];
+    __shared__ int s_nq;
+    __shared__ int64_t s_red[UB_NT / 32];
     for (int t = threadIdx.x; t < NBINS_ALL; t += blockDim.x) s_bins[t] = 0;
+    if (threadIdx.x == 0) s_nq = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t gi = warp; gi < NR; gi += nwarps) {
-        SpgArgs g;
-        int64_t i = gi;
-        if (R.table) {
-            const int b = batch_of(R, gi);
+    const int sub = lane & (UB_LANES - 1);
+    const int lead = lane & ~(UB_LANES - 1);
+    const unsigned gmask = 0xffu << lead;
+    const int64_t grp = (int64_t(blockIdx.x) * UB_NT + threadIdx.x) / UB_LANES;
+    const int64_t ch = grp < nchunks ? (grp * spread) % nchunks : nchunks;
+    const int64_t r0 = ch * chunk;
+    const int64_t r1 = r0 + chunk < NR ? r0 + chunk : NR;
+    SpgArgs g = R.one;
+    int b = 0;
+    int64_t rlo = 0, rhi = R.table ? -1 : NR;  // global rows of the current matrix
+    for (int64_t w0 = r0; w0 < r1;) {
+        if (w0 >= rhi) {
+            b = batch_of(R, w0);
+            rlo = R.row_off[b];
+            rhi = R.row_off[b + 1];
             g = R.table[b];
-            i = gi - R.row_off[b];
-            if (row_mat && lane == 0) row_mat[gi] = b;
-        } else {
-            g = R.one;
         }
+        // a window of up to eight rows of one matrix: lane j holds row w0 + j's range
+        int64_t w1 = w0 + UB_LANES;
+        if (w1 > r1) w1 = r1;
+        if (w1 > rhi) w1 = rhi;
+        int64_t my_lo = 0, my_hi = 0;
+        if (w0 + sub < w1) {
+            const int64_t i = w0 + sub - rlo;
+            int64_t x = g.a_ptr[i], y = g.a_ptr[i + 1];
+            x = x < 0 ? 0 : (x > g.nnzA ? g.nnzA : x);
+            y = y < x ? x : (y > g.nnzA ? g.nnzA : y);
+            my_lo = x;
+            my_hi = y;
+            if (row_mat) row_mat[w0 + sub] = b;
+        }
+        for (int64_t gi = w0; gi < w1; ++gi) {
+            const int src = lead + int(gi - w0);
+            const int64_t lo = __shfl_sync(gmask, my_lo, src);
+            const int64_t hi = __shfl_sync(gmask, my_hi, src);
+            if (hi - lo > UB_HEAVY) {
+                int slot = 0;
+                if (sub == 0) slot = atomicAdd(&s_nq, 1);
+                slot = __shfl_sync(gmask, slot, lead);
+                if (slot < UB_QCAP) {
+                    if (sub == 0) {
+                        s_q[slot] = gi;
+                        s_qb[slot] = b;
+                    }
+                    continue;
+                }
+            }
+            int64_t sum = 0;
+            for (int64_t p = lo + sub; p < hi; p += UB_UNROLL * UB_LANES) {
+                int32_t k[UB_UNROLL];
+#pragma unroll
+                for (int u = 0; u < UB_UNROLL; ++u) {
+                    const int64_t q = p + int64_t(u) * UB_LANES;
+                    k[u] = q < hi ? g.a_col[q] : -1;
+                }
+                int64_t bl[UB_UNROLL], bh[UB_UNROLL];
+#pragma unroll
+                for (int u = 0; u < UB_UNROLL; ++u) {
+                    bl[u] = bh[u] = 0;
+                    if ((uint64_t)k[u] < (uint64_t)g.K) row_range(g.b_ptr, k[u], g.nnzB, bl[u], bh[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < UB_UNROLL; ++u) sum += bh[u] - bl[u];
+            }
+#pragma unroll
+            for (int o = UB_LANES / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o);
+            if (sub == 0) ub_finish(gi, hi - lo, sum, ub, single, s_bins);
+        }
+        w0 = w1;
+    }
+    __syncthreads();
+    const int nq = s_nq < UB_QCAP ? s_nq : UB_QCAP;
+    for (int q = 0; q < nq; ++q) {
+        const int64_t gi = s_q[q];
+        const SpgArgs& gq = R.table ? R.table[s_qb[q]] : R.one;
+        const int64_t i = gi - (R.table ? R.row_off[s_qb[q]] : 0);
         int64_t lo, hi;
-        row_range(g.a_ptr, i, g.nnzA, lo, hi);
+        row_range(gq.a_ptr, i, gq.nnzA, lo, hi);
         int64_t sum = 0;
-        for (int64_t p = lo + lane; p < hi; p += 32) {
-            const int32_t k = g.a_col[p];
-            if ((uint64_t)k < (uint64_t)g.K) {
+        for (int64_t p = lo + threadIdx.x; p < hi; p += UB_NT) {
+            const int32_t k = gq.a_col[p];
+            if ((uint64_t)k < (uint64_t)gq.K) {
                 int64_t bl, bh;
-                row_range(g.b_ptr, k, g.nnzB, bl, bh);
+                row_range(gq.b_ptr, k, gq.nnzB, bl, bh);
                 sum += bh - bl;
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-        if (lane == 0) {
-            ub[gi] = sum;
-            const bool one = single && hi - lo == 1 && sum > 0;
-            if (one) single[gi] = sum;
-            atomicAdd(&s_bins[one ? BIN_COPY : bin_of(sum)], 1);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) s_red[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t tot = 0;
+            for (int w = 0; w < UB_NT / 32; ++w) tot += s_red[w];
+            ub_finish(gi, hi - lo, tot, ub, single, s_bins);
         }
+        __syncthreads();
     }
     __syncthreads();
     for (int t = threadIdx.x; t < NBINS_ALL; t += blockDim.x)
         if (s_bins[t]) atomicAdd(&bin_count[t], s_bins[t]);
+}
+
+// Launch of k_row_ub_b: one 8-lane group per eight of the SMs' thread slots, each
+// with an equal chunk of consecutive rows.
+static void launch_row_ub(const stc_handle* h, const SpgRows& R, int64_t NR, int64_t* ub, int* bin_count,
+                          int64_t* single, int32_t* row_mat, cudaStream_t s) {
+    if (NR <= 0) return;
+    // one wave: as many groups as the SMs hold at once
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_row_ub_b, UB_NT, 0) != cudaSuccess || per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t groups_max = int64_t(h->num_sms) * per_sm * (UB_NT / UB_LANES);
+    int64_t chunk = (NR + groups_max - 1) / groups_max;
+    if (chunk < 1) chunk = 1;
+    const int64_t nchunks = (NR + chunk - 1) / chunk;
+    // a prime above the chunk count makes g -> g * spread mod nchunks a permutation
+    const int64_t spread = nchunks < UB_SPREAD ? UB_SPREAD : 1;
+    const int64_t blocks = (nchunks * UB_LANES + UB_NT - 1) / UB_NT;
+    k_row_ub_b<<<unsigned(blocks), UB_NT, 0, s>>>(R, NR, chunk, nchunks, spread, ub, bin_count, single, row_mat);
 }
 
 // Rows with a single stored entry a = A_ik: C_i = f(a, B_k) entry by entry, in B_k's
@@ -1162,7 +1279,8 @@ constexpr int WR_WORDS = WR_MAX_COLS / 32;  // 512 bitmap words per warp
 constexpr int WR_ROUNDS = WR_WORDS / 32;    // 16 words per lane
 constexpr int WR_U = 8;                     // products per lane in flight per step
 constexpr int WR_VCAP = 2560;               // value slots per warp of the wide numeric instance
-constexpr int WR_VCAP_S = 1024;             // value slots per warp of the narrow numeric instance
+constexpr int WR_VCAP_S = 896;              // value slots per warp of the narrow numeric instance (fp32: four
+                                            // 8-warp CTAs of 56 KB fit an SM)
 constexpr int WR_UB_LOG2 = 15;              // rows with 2^15 products or more stay on the CTA kernels
 constexpr int WR_COUNT_WARPS = 8;           // warps per CTA of the count pass
 constexpr int WR_NUM_WARPS = 4;             // warps per CTA of the wide numeric instance
@@ -1897,6 +2015,8 @@ stc_status launch_wr_numeric(stc_handle* h, const SpgRows& R, const int32_t* row
     auto kern = k_wr_numeric<ALG, WARPS, VCAP>;
     const size_t smem = WARPS * wr_warp_bytes<ALG, VCAP>();
     STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      int(cudaSharedmemCarveoutMaxShared)));
     int per_sm = 0;
     STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem));
     if (per_sm < 1) return STC_ERR_CUDA;
@@ -2052,9 +2172,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
     int* counters = ints + 2 * NBINS_ALL + 1;  // [0] symbolic, [1] numeric
     int* max_nnz = ints + 2 * NBINS_ALL + 4;
     if (NR > 0) {
-        int64_t blocks = (NR * 32 + 255) / 256;
-        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, c_ptr + 1, row_mat);
+        launch_row_ub(h, R, NR, ub, bin_count, c_ptr + 1, row_mat, s);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
         k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, c_ptr + 1, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
@@ -2623,7 +2741,7 @@ stc_status row_counts_impl(stc_handle* h, const stc_csr* A, const stc_csr* B, in
         int* nlist = ints + 2 * NBINS_ALL;
         int* counter = ints + 2 * NBINS_ALL + 1;
         int* max_nnz = ints + 2 * NBINS_ALL + 4;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, part);
+        launch_row_ub(h, R, NR, ub, bin_count, part, nullptr, s);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
         k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, part, cursor, rowlist);
         STC_LAUNCH_CHECK();
@@ -2716,9 +2834,7 @@ stc_status spgemm_slab_impl(stc_handle* h, int alg, const stc_csr* A, const stc_
         int* max_nnz = ti + 2 * NBINS_ALL + 4;
         int32_t* rowlist = rowlists + size_t(t) * NR;
         int64_t* cnt_t = cnt + size_t(t) * NR;
-        int64_t blocks = (NR * 32 + 255) / 256;
-        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, cnt_t);
+        launch_row_ub(h, R, NR, ub, bin_count, cnt_t, nullptr, s);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
         k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, cnt_t, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
@@ -2886,10 +3002,8 @@ stc_status spgemm_learned_impl(stc_handle* h, int alg, const stc_csr* A, const s
         cudaMemsetAsync(soff, 0, sizeof(int64_t), s) != cudaSuccess)
         return fail(STC_ERR_CUDA);
     if (NR > 0) {
-        int64_t blocks = (NR * 32 + 255) / 256;
-        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
         // rows with one stored entry: exact size ub into c_ptr + 1, written by the copy kernel
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, c_ptr + 1);
+        launch_row_ub(h, R, NR, ub, bin_count, c_ptr + 1, nullptr, s);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
         k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, c_ptr + 1, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
@@ -3093,9 +3207,7 @@ stc_status spgemm_learned_slab_impl(stc_handle* h, int alg, const stc_csr* A, co
         int64_t* cap_t = cap + size_t(t) * NR;
         int64_t* soff_t = soff + size_t(t) * (NR + 1);
         float* pred_t = weights ? preds + size_t(t) * NR : nullptr;
-        int64_t blocks = (NR * 32 + 255) / 256;
-        if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
-        k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, bin_count, nullptr);
+        launch_row_ub(h, R, NR, ub, bin_count, nullptr, nullptr, s);
         k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
         k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ub, nullptr, cursor, rowlist);
         if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
@@ -3359,10 +3471,8 @@ stc_status spgemm_masked_impl(stc_handle* h, int alg, const stc_csr* A, const st
     SpgRows R{};
     R.one = g;
     R.nb = 1;
-    int64_t blocks = (NR * 32 + 255) / 256;
-    if (blocks > int64_t(h->num_sms) * 16) blocks = int64_t(h->num_sms) * 16;
     const unsigned gb = unsigned(h->num_sms * 8);
-    k_row_ub_b<<<unsigned(blocks), 256, 0, s>>>(R, NR, ub, product_bins, nullptr);
+    launch_row_ub(h, R, NR, ub, product_bins, nullptr, nullptr, s);
     k_mask_ub<<<gb, 256, 0, s>>>(NR, ub, M->rowptr, M->nnz, ubm, bin_count);
     k_bin_offsets<<<1, 32, 0, s>>>(bin_count, cursor, nlist);
     k_bin_scatter<<<unsigned((NR + 511) / 512), 512, 0, s>>>(NR, ubm, nullptr, cursor, rowlist);

@@ -212,103 +212,173 @@ stc_status stc_check_csr_host(const stc_csr* m) {
     return STC_OK;
 }
 
-// One warp per row: rowptr bounds and monotonicity, column range and strict order.
-__global__ void k_validate_csr(int64_t nrows, int64_t ncols, int64_t nnz,
-                               const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                               int* flags) {
-    const int lane = threadIdx.x & 31;
-    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    if (warp == 0 && lane == 0) {
-        if (ptr[0] != 0 || ptr[nrows] != nnz) atomicOr(flags, STC_FLAG_SHAPE);
-    }
-    int bad = 0;
-    for (int64_t i = warp; i < nrows; i += nwarps) {
-        int64_t lo = ptr[i], hi = ptr[i + 1];
-        if (lo < 0 || hi < lo || hi > nnz) {
-            bad |= STC_FLAG_SHAPE;
-            continue;
-        }
-        for (int64_t p = lo + lane; p < hi; p += 32) {
-            int32_t c = col[p];
-            if (c < 0 || c >= ncols) bad |= STC_FLAG_UNSORTED;
-            if (p > lo && col[p - 1] >= c) bad |= STC_FLAG_UNSORTED;
-        }
-    }
-    bad = __reduce_or_sync(0xffffffffu, bad);
-    if (lane == 0 && bad) atomicOr(flags, bad);
-}
-
-stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s) {
-    int64_t warps_needed = m->nrows > 0 ? m->nrows : 1;
-    int64_t blocks = (warps_needed * 32 + 255) / 256;
-    int64_t cap = int64_t(h->num_sms) * 8;
-    if (blocks > cap) blocks = cap;
-    k_validate_csr<<<(unsigned)blocks, 256, 0, s>>>(m->nrows, m->ncols, m->nnz, m->rowptr, m->col,
-                                                    h->d_flags);
-    STC_LAUNCH_CHECK();
-    stc_count(h);
-    return STC_OK;
-}
-
-// Validation of many matrices in one launch: blockIdx.y selects the matrix.
+// Validation works on a flat index over each matrix's row pointers and columns:
+// element e < nrows checks row e's pointer pair (0 <= ptr[e] <= ptr[e+1] <= nnz),
+// element nrows + p checks column p (0 <= col[p] < ncols).  Order: a position p > 0
+// with col[p-1] >= col[p] (a descent) is legal only where a row opens.  Every
+// non-empty row opens at a distinct position, so the columns are strictly ascending
+// within rows exactly when the number of descents equals the number of descents
+// at row openings; elements add +1 per descent and -1 per descent at an opening
+// into a counter, and the last block to finish checks it for zero and clears it.
+// A block takes VAL_TILE consecutive elements of one matrix; `tile0` numbers each
+// matrix's first tile, and in a batch tile_mat[tile] names the tile's matrix.
 struct CsrView {
     int64_t nrows, ncols, nnz;
     const int64_t* ptr;
     const int32_t* col;
+    int64_t tile0;
 };
 
-__global__ void k_validate_many(const CsrView* __restrict__ views, int* flags) {
-    const CsrView m = views[blockIdx.y];
+constexpr int VAL_NT = 256;
+constexpr int VAL_PER = 8;
+constexpr int64_t VAL_TILE = int64_t(VAL_NT) * VAL_PER;
+
+static int64_t val_tiles(int64_t nrows, int64_t nnz) {
+    const int64_t t = (nrows + nnz + VAL_TILE - 1) / VAL_TILE;
+    return t > 0 ? t : 1;
+}
+
+// views == null: the single matrix `one` (tile0 = 0).  cnt: [0] the descent balance
+// (two's complement), [1] finished blocks; zero before the launch, zero after it.
+__global__ void __launch_bounds__(VAL_NT) k_validate_tiles(CsrView one, const CsrView* __restrict__ views,
+                                                           const int* __restrict__ tile_mat, int* flags,
+                                                           unsigned long long* cnt) {
+    __shared__ int s_net[VAL_NT / 32];
+    const CsrView m = views ? views[tile_mat[blockIdx.x]] : one;
+    const int64_t t = int64_t(blockIdx.x) - m.tile0;
     const int lane = threadIdx.x & 31;
-    int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    if (warp == 0 && lane == 0 && (m.ptr[0] != 0 || m.ptr[m.nrows] != m.nnz)) atomicOr(flags, STC_FLAG_SHAPE);
-    int bad = 0;
-    for (int64_t i = warp; i < m.nrows; i += nwarps) {
-        const int64_t lo = m.ptr[i], hi = m.ptr[i + 1];
-        if (lo < 0 || hi < lo || hi > m.nnz) {
-            bad |= STC_FLAG_SHAPE;
-            continue;
+    int bad = 0, net = 0;
+    if (t == 0 && threadIdx.x == 0 && (m.ptr[0] != 0 || m.ptr[m.nrows] != m.nnz)) bad |= STC_FLAG_SHAPE;
+    const int64_t e0 = t * VAL_TILE + threadIdx.x;  // this thread's elements: e0 + j * VAL_NT
+    const int64_t nel = m.nrows + m.nnz;
+    if (t * VAL_TILE >= m.nrows && m.nnz > 0) {
+        // a tile of entries only: every load is issued before any is used (indexes
+        // clamped into the array; out-of-range elements are masked afterwards)
+        const int64_t p0 = e0 - m.nrows;
+        int32_t c[VAL_PER], cp[VAL_PER];
+#pragma unroll
+        for (int j = 0; j < VAL_PER; ++j) {
+            int64_t p = p0 + int64_t(j) * VAL_NT;
+            p = p < m.nnz ? p : m.nnz - 1;
+            c[j] = m.col[p];
+            cp[j] = m.col[p > 0 ? p - 1 : 0];
         }
-        for (int64_t p = lo + lane; p < hi; p += 32) {
-            const int32_t c = m.col[p];
-            if (c < 0 || c >= m.ncols) bad |= STC_FLAG_UNSORTED;
-            if (p > lo && m.col[p - 1] >= c) bad |= STC_FLAG_UNSORTED;
+#pragma unroll
+        for (int j = 0; j < VAL_PER; ++j) {
+            const int64_t p = p0 + int64_t(j) * VAL_NT;
+            if (p < m.nnz) {
+                if (c[j] < 0 || c[j] >= m.ncols) bad |= STC_FLAG_UNSORTED;
+                if (p > 0 && cp[j] >= c[j]) ++net;
+            }
+        }
+    } else if ((t + 1) * VAL_TILE <= m.nrows) {
+        // a tile of row pointers only
+        int64_t lo[VAL_PER], hi[VAL_PER];
+#pragma unroll
+        for (int j = 0; j < VAL_PER; ++j) {
+            const int64_t r = e0 + int64_t(j) * VAL_NT;
+            lo[j] = m.ptr[r];
+            hi[j] = m.ptr[r + 1];
+        }
+        int32_t a[VAL_PER], c[VAL_PER];
+#pragma unroll
+        for (int j = 0; j < VAL_PER; ++j) {
+            const bool ok = lo[j] >= 0 && hi[j] >= lo[j] && hi[j] <= m.nnz;
+            if (!ok) bad |= STC_FLAG_SHAPE;
+            const bool opens = ok && lo[j] > 0 && lo[j] < hi[j];
+            a[j] = opens ? m.col[lo[j] - 1] : 0;
+            c[j] = opens ? m.col[lo[j]] : 1;
+        }
+#pragma unroll
+        for (int j = 0; j < VAL_PER; ++j)
+            if (a[j] >= c[j]) --net;
+    } else {
+        // the tile where the row pointers end and the entries begin
+        for (int j = 0; j < VAL_PER; ++j) {
+            const int64_t e = e0 + int64_t(j) * VAL_NT;
+            if (e < m.nrows) {
+                const int64_t lo = m.ptr[e], hi = m.ptr[e + 1];
+                if (lo < 0 || hi < lo || hi > m.nnz) bad |= STC_FLAG_SHAPE;
+                else if (lo > 0 && lo < hi && m.col[lo - 1] >= m.col[lo]) --net;
+            } else if (e < nel) {
+                const int64_t p = e - m.nrows;
+                const int32_t c = m.col[p];
+                if (c < 0 || c >= m.ncols) bad |= STC_FLAG_UNSORTED;
+                if (p > 0 && m.col[p - 1] >= c) ++net;
+            }
         }
     }
     bad = __reduce_or_sync(0xffffffffu, bad);
-    if (lane == 0 && bad) atomicOr(flags, bad);
+    net = __reduce_add_sync(0xffffffffu, net);
+    if (lane == 0) {
+        if (bad) atomicOr(flags, bad);
+        s_net[threadIdx.x >> 5] = net;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int w = 0; w < VAL_NT / 32; ++w) tot += s_net[w];
+        if (tot) atomicAdd(&cnt[0], static_cast<unsigned long long>(tot));
+        __threadfence();
+        if (atomicAdd(&cnt[1], 1ull) == gridDim.x - 1ull) {
+            __threadfence();
+            if (atomicAdd(&cnt[0], 0ull) != 0ull) atomicOr(flags, STC_FLAG_UNSORTED);
+            cnt[0] = 0ull;
+            cnt[1] = 0ull;
+        }
+    }
 }
 
+static CsrView view_of(const stc_csr* m) {
+    return CsrView{m->nrows, m->ncols, m->nnz, m->rowptr, m->col, 0};
+}
+
+unsigned long long* stc_val_counters(stc_handle* h) {
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(h->d_flags) +
+                                                 STC_VAL_COUNTER_OFFSET);
+}
+
+stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s) {
+    const stc_status st = stc_validate_csr_flags_async(m, h->d_flags, stc_val_counters(h), s);
+    if (st == STC_OK) stc_count(h);
+    return st;
+}
+
+// Validation of many matrices in one launch.
 stc_status stc_validate_many_async(stc_handle* h, StcScratch& sc, const stc_csr* mats, int count, stc_stream s) {
     if (count == 1) return stc_validate_csr_async(h, mats, s);
     std::vector<CsrView> v(count);
-    int64_t maxrows = 1;
+    int64_t tiles = 0;
     for (int i = 0; i < count; ++i) {
-        v[i] = CsrView{mats[i].nrows, mats[i].ncols, mats[i].nnz, mats[i].rowptr, mats[i].col};
-        if (mats[i].nrows > maxrows) maxrows = mats[i].nrows;
+        v[i] = view_of(mats + i);
+        v[i].tile0 = tiles;
+        tiles += val_tiles(mats[i].nrows, mats[i].nnz);
+    }
+    if (tiles > INT32_MAX) return STC_ERR_INVALID_ARG;
+    std::vector<int> tm(static_cast<size_t>(tiles));
+    for (int i = 0; i < count; ++i) {
+        const int64_t end = i + 1 < count ? v[i + 1].tile0 : tiles;
+        for (int64_t t = v[i].tile0; t < end; ++t) tm[size_t(t)] = i;
     }
     CsrView* d = sc.get<CsrView>(size_t(count));
-    if (!d) return STC_ERR_OOM;
+    int* d_tm = sc.get<int>(size_t(tiles));
+    if (sc.failed) return STC_ERR_OOM;
+    // copies from pageable memory return once the source has been staged, so the
+    // host vectors may go out of scope right after them
     STC_CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(CsrView) * count, cudaMemcpyHostToDevice, s));
-    int64_t bx = (maxrows * 32 + 255) / 256;
-    if (bx > 32) bx = 32;
-    k_validate_many<<<dim3(unsigned(bx), unsigned(count)), 256, 0, s>>>(d, h->d_flags);
+    STC_CUDA_TRY(cudaMemcpyAsync(d_tm, tm.data(), sizeof(int) * size_t(tiles), cudaMemcpyHostToDevice, s));
+    k_validate_tiles<<<unsigned(tiles), VAL_NT, 0, s>>>(CsrView{}, d, d_tm, h->d_flags, stc_val_counters(h));
     STC_LAUNCH_CHECK();
     stc_count(h);
-    // the host vector must outlive the copy
-    STC_CUDA_TRY(cudaStreamSynchronize(s));
     return STC_OK;
 }
 
-// Same validation with the flag word supplied by the caller (no handle).
-stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, int num_sms, stc_stream s) {
-    int64_t warps_needed = m->nrows > 0 ? m->nrows : 1;
-    int64_t blocks = (warps_needed * 32 + 255) / 256;
-    int64_t cap = int64_t(num_sms) * 8;
-    if (blocks > cap) blocks = cap;
-    k_validate_csr<<<(unsigned)blocks, 256, 0, s>>>(m->nrows, m->ncols, m->nnz, m->rowptr, m->col, flags);
+// Same validation with the flag word and the two counters supplied by the caller
+// (no handle).
+stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, unsigned long long* counters, stc_stream s) {
+    const int64_t tiles = val_tiles(m->nrows, m->nnz);
+    if (tiles > INT32_MAX) return STC_ERR_INVALID_ARG;
+    k_validate_tiles<<<unsigned(tiles), VAL_NT, 0, s>>>(view_of(m), nullptr, nullptr, flags, counters);
     STC_LAUNCH_CHECK();
     return STC_OK;
 }

@@ -18,7 +18,8 @@ struct stc_handle {
     stc_alloc_fn alloc = nullptr;
     stc_free_fn free_fn = nullptr;
     void* ctx = nullptr;
-    int* d_flags = nullptr;        // device error flags, STC_FLAG_* bits
+    int* d_flags = nullptr;        // 64 device bytes: error flags (STC_FLAG_* bits) at 0,
+                                   // the validation counters at STC_VAL_COUNTER_OFFSET
     int64_t* h_stage = nullptr;    // pinned host staging, 64 int64
     bool timing = false;           // record phase events
     cudaEvent_t ev[9] = {};        // phase boundary events (created on first use)
@@ -44,6 +45,7 @@ struct stc_handle {
 };
 
 constexpr size_t STC_PARAM_BYTES = 4096;
+constexpr size_t STC_VAL_COUNTER_OFFSET = 16;  // two u64 after the flag word
 
 // The auxiliary stream; run work on it between stc_fork and stc_join (stream order
 // of `s` is kept: the auxiliary work starts after what is queued on `s` and `s`
@@ -110,7 +112,10 @@ stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s)
 // Validation of `count` matrices (host descriptors) in one launch.
 stc_status stc_validate_many_async(stc_handle* h, StcScratch& sc, const stc_csr* mats, int count, stc_stream s);
 // The same check raising its flags in `flags` (a device int); needs no handle.
-stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, int num_sms, stc_stream s);
+// `counters` are two device u64, zero before the launch (the kernel leaves them zero).
+stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, unsigned long long* counters, stc_stream s);
+// The handle's pair of validation counters.
+unsigned long long* stc_val_counters(stc_handle* h);
 
 // ----------------------------------------------------------------- algebra ids
 
