@@ -646,11 +646,12 @@ def measure_batched(stc, H, npairs=4096, with_per_call=True):
     def per_call():
         for a, b in zip(dA, dB):
             H.spgemm(stc.PLUS_TIMES_F32, a, b)
-    t_p = _timed(per_call, 1) if with_per_call else float("nan")
+    t_p = _timed(per_call, 1) if with_per_call else None
     torch.cuda.empty_cache()
     return {"unit": UNIT, "workload": f"{npairs} pairs, rows power-law [64,16384] exp 2.1, U{{4..64}}/row, N(0,1) fp32",
-            "products": nprod, "nnzC": int(nnz["c"].sum()), "batched": nprod / t_b, "per_call": nprod / t_p,
-            "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p},
+            "products": nprod, "nnzC": int(nnz["c"].sum()), "batched": nprod / t_b,
+            "per_call": nprod / t_p if t_p else None,
+            "ms": {"batched": 1e3 * t_b, "per_call": 1e3 * t_p if t_p else None},
             "roofline": {"bound": "hbm", "algorithmic_bytes": gbytes, "achieved": gbytes / t_b / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": gbytes / t_b / 1e9 / hbm, "peak_source": peak_kind,
                          "time": "whole batched call (wall clock, device synchronised)"}}

@@ -78,7 +78,11 @@ typedef enum {
  * Operand element types are given as A / B / C.
  *
  *  STC_PLUS_TIMES_F32   (+,x) field. float / float / float.  Products rounded to
- *                       fp32, summed in fp32 in an unspecified order.
+ *                       fp32, summed in fp32 in an unspecified order; in SpGEMM
+ *                       the entries of a row of A with more than 1024 stored
+ *                       entries are summed with compensation (the exact rounding
+ *                       errors of products and adds collected beside each sum),
+ *                       except in the masked product and in forced column windows.
  *  STC_PLUS_TIMES_F64   (+,x) field. double / double / double.
  *  STC_MIN_PLUS_I32     tropical semiring, (+) = min, f = integer +, additive
  *                       identity INT_MAX/2 = 1073741823 (Section 3.1: half of the

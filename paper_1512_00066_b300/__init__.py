@@ -231,24 +231,32 @@ class DeviceCsr:
     def nnz(self) -> int:
         return int(self.col.numel())
 
+    # The C descriptor and its bytes are kept in the instance (_cd, _cb) and dropped
+    # whenever a field is assigned, so that batched calls, which marshal thousands
+    # of descriptors, read one attribute per matrix.
+    def __setattr__(self, name, value):
+        object.__setattr__(self, name, value)
+        if name in ("nrows", "ncols", "rowptr", "col", "val"):
+            self.__dict__.pop("_cd", None)
+            self.__dict__.pop("_cb", None)
+
     def _c(self) -> _Csr:
-        """The C descriptor, rebuilt only when a field changed (batched calls marshal
-        thousands of them)."""
-        return self._cached()[1]
+        """The C descriptor."""
+        c = self.__dict__.get("_cd")
+        return c if c is not None else self._build_c()[0]
 
     def _c_bytes(self) -> bytes:
         """The C descriptor's bytes (for building descriptor arrays of batched calls)."""
-        return self._cached()[2]
+        b = self.__dict__.get("_cb")
+        return b if b is not None else self._build_c()[1]
 
-    def _cached(self):
-        key = (self.nrows, self.ncols, id(self.rowptr), id(self.col), id(self.val))
-        cached = self.__dict__.get("_c_cache")
-        if cached is not None and cached[0] == key:
-            return cached
+    def _build_c(self):
         c = _Csr(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
                  self.val.data_ptr() if self.val is not None and self.val.numel() else None)
-        cached = self.__dict__["_c_cache"] = (key, c, bytes(c))
-        return cached
+        b = bytes(c)
+        self.__dict__["_cd"] = c
+        self.__dict__["_cb"] = b
+        return c, b
 
     @staticmethod
     def from_host(nrows, ncols, rowptr, col, val=None, device="cuda") -> "DeviceCsr":
@@ -442,8 +450,8 @@ class Handle:
         """
         nb = len(As)
         assert nb == len(Bs) and nb > 0
-        A = (_Csr * nb).from_buffer_copy(b"".join([a._c_bytes() for a in As]))
-        B = (_Csr * nb).from_buffer_copy(b"".join([b._c_bytes() for b in Bs]))
+        A = (_Csr * nb).from_buffer_copy(b"".join([a.__dict__.get("_cb") or a._c_bytes() for a in As]))
+        B = (_Csr * nb).from_buffer_copy(b"".join([b.__dict__.get("_cb") or b._c_bytes() for b in Bs]))
         C = (_Csr * nb)()
         opts = _Opts(1 if skip_validation else 0, 0, int(light_rows))
         st = lib().stc_contract_spgemm_batched(self._h, alg, nb, A, B, C, ctypes.byref(opts), _stream_ptr(stream))

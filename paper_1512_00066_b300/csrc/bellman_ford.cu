@@ -514,8 +514,8 @@ stc_status run_bf_noalloc(const stc_csr* G, int32_t source, void* dist_out, int3
     // the previous call's counters, barrier state and flags are left behind: clear them
     STC_CUDA_TRY(cudaMemsetAsync(base, 0, NOALLOC_HEADER, s));
     if ((st = stc_validate_csr_flags_async(G, flags,
-                                           reinterpret_cast<unsigned long long*>(base + NOALLOC_VAL_OFFSET), s)) !=
-        STC_OK)
+                                           reinterpret_cast<unsigned long long*>(base + NOALLOC_VAL_OFFSET), num_sms,
+                                           s)) != STC_OK)
         return st;
     int64_t blocks = (n + 255) / 256;
     if (blocks > int64_t(num_sms) * 8) blocks = int64_t(num_sms) * 8;

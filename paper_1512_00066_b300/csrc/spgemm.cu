@@ -610,6 +610,17 @@ constexpr int RK_SYM_NT = 256;  // symbolic kernel: more rows in flight per SM
 constexpr size_t RK_SMEM_TARGET = 224 * 1024;  // one CTA per SM
 constexpr double RK_RECORD_BUDGET = 24e9;        // bytes of stored rank records
 constexpr int RK_SPARSE_MAX_WORDS = 4096;         // sparse record: at most this many non-zero words
+// (+,x) fp32: a row of A with more than F32_WIDE_ROW stored entries can give an
+// output entry more terms than plain fp32 summation serves well, so such rows are
+// summed with compensation: beside each fp32 accumulator an fp32 correction
+// collects the exact rounding errors of the products (fma) and of the accumulating
+// adds (two-sum on the value the atomic add returns), and the entry is the rounded
+// sum of the two.  In the CTA numeric kernel the corrections take the
+// column-per-rank buffer, and the row's output columns are expanded from its
+// bitmap at write-out; the warp-per-row kernels leave such rows to it.
+constexpr int64_t F32_WIDE_ROW = 1024;
+constexpr int64_t NO_WIDE_ROWS = INT64_MAX;
+__host__ __device__ constexpr int64_t wide_len_of(int alg) { return alg == ALG_PT_F32 ? F32_WIDE_ROW : NO_WIDE_ROWS; }
 
 template <int NT>
 struct TaskSmem {
@@ -1550,8 +1561,11 @@ k_wr_numeric(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __re
 // Rows of the list [0, *nlist) split for the numeric pass into three lists
 // (order inside a list follows the row list): out[0] rows with at most WR_VCAP_S
 // output entries, out[1] rows with at most WR_VCAP, out[2] the heavy prefix
-// [0, *heavy_ptr) (too many products for one warp) and the rest; n[0..2] sizes.
-__global__ void k_split_by_count(const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
+// [0, *heavy_ptr) (too many products for one warp), rows of A with more than
+// wide_len stored entries (compensated sums, CTA kernels only) and the rest;
+// n[0..2] sizes.
+__global__ void k_split_by_count(SpgRows R, const int32_t* __restrict__ row_mat, int64_t wide_len,
+                                 const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
                                  const int* __restrict__ heavy_ptr, const int64_t* __restrict__ c_ptr,
                                  int32_t* __restrict__ out0, int32_t* __restrict__ out1, int32_t* __restrict__ out2,
                                  int* __restrict__ n) {
@@ -1564,7 +1578,15 @@ __global__ void k_split_by_count(const int32_t* __restrict__ rowlist, const int*
         if (r < nlist) {
             gi = rowlist[r];
             const int64_t c = c_ptr[gi + 1] - c_ptr[gi];
-            cls = r < heavy ? 2 : c <= WR_VCAP_S ? 0 : c <= WR_VCAP ? 1 : 2;
+            bool wide = false;
+            if (wide_len != NO_WIDE_ROWS) {
+                const int b = row_mat ? row_mat[gi] : 0;
+                const SpgArgs& g = R.table ? R.table[b] : R.one;
+                int64_t lo, hi;
+                row_range(g.a_ptr, gi - (R.table ? R.row_off[b] : 0), g.nnzA, lo, hi);
+                wide = hi - lo > wide_len;
+            }
+            cls = (r < heavy || wide) ? 2 : c <= WR_VCAP_S ? 0 : c <= WR_VCAP ? 1 : 2;
         }
         const unsigned below = (1u << lane) - 1u;
 #pragma unroll
@@ -1659,6 +1681,8 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
         const BT* __restrict__ bval = static_cast<const BT*>(g.b_val);
         int64_t alo, ahi;
         row_range(g.a_ptr, i, g.nnzA, alo, ahi);
+        // compensated fp32 sums for this row (the column buffer holds the corrections)
+        const bool wide = ALG == ALG_PT_F32 && !MASKED && ahi - alo > F32_WIDE_ROW;
         const int64_t o0 = out.ptr[gi];
         const int64_t o1 = out.cap ? o0 + out.cap[gi] : out.ptr[gi + 1];
 
@@ -1796,6 +1820,51 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                     if (!((e.x >> (col & 31)) & 1u)) return -1;  // not in the mask
                 return int(e.y) + __popc(e.x & ((1u << (col & 31)) - 1u)) - rb;
             };
+            bool done = false;
+            if constexpr (ALG == ALG_PT_F32 && !MASKED) {
+                if (wide) {
+                    // compensated sums: comp (the column buffer) collects, per entry, the
+                    // exact rounding error of every accumulating add (from the value the
+                    // atomic add returns) and of every product (fma); the entry is the
+                    // rounded acc + comp.  Columns come from the bitmap at write-out.
+                    float* comp = reinterpret_cast<float*>(scol);
+                    for (int r = threadIdx.x; r < rcount; r += NT) comp[r] = 0.0f;
+                    __syncthreads();
+                    for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
+                        const int ntasks = load_tasks<NT, AT, true, VSUB>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
+                        walk_tasks_rank<NT, AT, BT, VSUB>(
+                            g, ts, ntasks, s_aval, bval, rcount, rank_of, [&](int, int) {},
+                            [&](int r, int, const BT& bb, const AT aa) {
+                                const float pr = __fmul_rn(aa, bb);
+                                const float ep = __fmaf_rn(aa, bb, -pr);  // aa * bb - pr, exactly
+                                const float old = atomicAdd(&vals[r], pr);
+                                const float sm = __fadd_rn(old, pr);  // what the atomic stored
+                                const float bv = __fsub_rn(sm, old);
+                                const float e = __fadd_rn(__fsub_rn(old, __fsub_rn(sm, bv)), __fsub_rn(pr, bv));
+                                atomicAdd(&comp[r], __fadd_rn(e, ep));
+                            });
+                        __syncthreads();
+                    }
+                    if (fits) {
+                        // each non-zero word's columns, in order, from the rank of its first column
+                        for (int w = cl * 32 + int(threadIdx.x); w < ch * 32; w += NT) {
+                            uint32_t bits = wb[w].x;
+                            if (!bits) continue;
+                            int r = int(wb[w].y) - rb;
+                            while (bits) {
+                                c_col[od + rb + r++] = w * 32 + __ffs(bits) - 1 + g.col_base;
+                                bits &= bits - 1;
+                            }
+                        }
+                    }
+                    for (int r = threadIdx.x; r < rcount; r += NT) {
+                        if (fits) cval[od + rb + r] = __fadd_rn(vals[r], comp[r]);
+                        vals[r] = T::empty();
+                    }
+                    done = true;
+                }
+            }
+            if (!done) {
             for (int64_t p0 = alo; p0 < ahi; p0 += NT) {
                 const int ntasks = load_tasks<NT, AT, true, VSUB>(g, tab, ncell, p0, ahi, cl, ch, ts, s_aval);
                 walk_tasks_rank<NT, AT, BT, VSUB>(g, ts, ntasks, s_aval, bval, rcount, rank_of,
@@ -1834,6 +1903,7 @@ k_numeric_rank(SpgRows R, int ncell_max, int vcap, int maxwin,
                     }
                 }
                 vals[r] = T::empty();
+            }
             }
             __syncthreads();
         }
@@ -2323,7 +2393,9 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         int* wcounter = ints + 2 * NBINS_ALL + 11;  // [0] narrow warp instance, [1] wide, [2] CTA kernel
         int64_t wr_heavy_rows = 0;
         for (int b = WR_UB_LOG2 + 1; b < NBINS; ++b) wr_heavy_rows += stage_bins[b];
-        if (max_row <= WR_VCAP_S && wr_heavy_rows == 0) {
+        // (+,x) fp32: rows with compensated sums may exist, and only the CTA kernel has them
+        const bool maybe_wide = wide_len_of(alg) != NO_WIDE_ROWS;
+        if (max_row <= WR_VCAP_S && wr_heavy_rows == 0 && !maybe_wide) {
             if ((st = run_wr_numeric(h, alg, false, R, row_mat, rowlist, nlist, wcounter, c_ptr, c_col, c_val, NR,
                                      bm, s)) != STC_OK)
                 return fail(st);
@@ -2332,11 +2404,11 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
             if (!lists) return fail(STC_ERR_OOM);
             int64_t blocks = (NR + 255) / 256;
             if (blocks > int64_t(h->num_sms) * 8) blocks = int64_t(h->num_sms) * 8;
-            k_split_by_count<<<unsigned(blocks), 256, 0, s>>>(rowlist, nlist, wr_heavy, c_ptr, lists, lists + NR,
-                                                              lists + 2 * NR, nsplit);
+            k_split_by_count<<<unsigned(blocks), 256, 0, s>>>(R, row_mat, wide_len_of(alg), rowlist, nlist, wr_heavy,
+                                                              c_ptr, lists, lists + NR, lists + 2 * NR, nsplit);
             if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
             stc_count(h);
-            if (max_row > WR_VCAP || wr_heavy_rows > 0) {
+            if (max_row > WR_VCAP || wr_heavy_rows > 0 || maybe_wide) {
                 if ((st = run_numeric_any(h, alg, R, ncell_max, cfg, lists + 2 * NR, nsplit + 2, wcounter + 2, out,
                                           c_col, c_val, NR, s, rec, rec_meta)) != STC_OK)
                     return fail(st);

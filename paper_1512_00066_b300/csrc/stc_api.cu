@@ -238,16 +238,15 @@ static int64_t val_tiles(int64_t nrows, int64_t nnz) {
     return t > 0 ? t : 1;
 }
 
-// views == null: the single matrix `one` (tile0 = 0).  cnt: [0] the descent balance
-// (two's complement), [1] finished blocks; zero before the launch, zero after it.
-__global__ void __launch_bounds__(VAL_NT) k_validate_tiles(CsrView one, const CsrView* __restrict__ views,
-                                                           const int* __restrict__ tile_mat, int* flags,
-                                                           unsigned long long* cnt) {
-    __shared__ int s_net[VAL_NT / 32];
-    const CsrView m = views ? views[tile_mat[blockIdx.x]] : one;
-    const int64_t t = int64_t(blockIdx.x) - m.tile0;
-    const int lane = threadIdx.x & 31;
-    int bad = 0, net = 0;
+// Eight blocks per SM at most, striding over the tiles.
+static unsigned val_grid(int64_t tiles, int num_sms) {
+    const int64_t cap = int64_t(num_sms > 0 ? num_sms : 1) * 8;
+    return unsigned(tiles < cap ? tiles : cap);
+}
+
+// Tile t of matrix m: raises flag bits in `bad`, adds descents minus descents at row
+// openings to `net`.
+__device__ __forceinline__ void val_tile(const CsrView& m, int64_t t, int& bad, long long& net) {
     if (t == 0 && threadIdx.x == 0 && (m.ptr[0] != 0 || m.ptr[m.nrows] != m.nnz)) bad |= STC_FLAG_SHAPE;
     const int64_t e0 = t * VAL_TILE + threadIdx.x;  // this thread's elements: e0 + j * VAL_NT
     const int64_t nel = m.nrows + m.nnz;
@@ -308,9 +307,25 @@ __global__ void __launch_bounds__(VAL_NT) k_validate_tiles(CsrView one, const Cs
             }
         }
     }
+}
+
+// views == null: the single matrix `one` (tile0 = 0).  Blocks stride over the
+// `tiles` tiles (one counter update per block).  cnt: [0] the descent balance (two's
+// complement), [1] finished blocks; zero before the launch, zero after it.
+__global__ void __launch_bounds__(VAL_NT) k_validate_tiles(CsrView one, const CsrView* __restrict__ views,
+                                                           const int* __restrict__ tile_mat, int64_t tiles,
+                                                           int* flags, unsigned long long* cnt) {
+    __shared__ long long s_net[VAL_NT / 32];
+    int bad = 0;
+    long long net = 0;
+    for (int64_t tg = blockIdx.x; tg < tiles; tg += gridDim.x) {
+        const CsrView m = views ? views[tile_mat[tg]] : one;
+        val_tile(m, tg - m.tile0, bad, net);
+    }
     bad = __reduce_or_sync(0xffffffffu, bad);
-    net = __reduce_add_sync(0xffffffffu, net);
-    if (lane == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) net += __shfl_xor_sync(0xffffffffu, net, o);
+    if ((threadIdx.x & 31) == 0) {
         if (bad) atomicOr(flags, bad);
         s_net[threadIdx.x >> 5] = net;
     }
@@ -339,7 +354,7 @@ unsigned long long* stc_val_counters(stc_handle* h) {
 }
 
 stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s) {
-    const stc_status st = stc_validate_csr_flags_async(m, h->d_flags, stc_val_counters(h), s);
+    const stc_status st = stc_validate_csr_flags_async(m, h->d_flags, stc_val_counters(h), h->num_sms, s);
     if (st == STC_OK) stc_count(h);
     return st;
 }
@@ -367,7 +382,8 @@ stc_status stc_validate_many_async(stc_handle* h, StcScratch& sc, const stc_csr*
     // host vectors may go out of scope right after them
     STC_CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(CsrView) * count, cudaMemcpyHostToDevice, s));
     STC_CUDA_TRY(cudaMemcpyAsync(d_tm, tm.data(), sizeof(int) * size_t(tiles), cudaMemcpyHostToDevice, s));
-    k_validate_tiles<<<unsigned(tiles), VAL_NT, 0, s>>>(CsrView{}, d, d_tm, h->d_flags, stc_val_counters(h));
+    k_validate_tiles<<<val_grid(tiles, h->num_sms), VAL_NT, 0, s>>>(CsrView{}, d, d_tm, tiles, h->d_flags,
+                                                                     stc_val_counters(h));
     STC_LAUNCH_CHECK();
     stc_count(h);
     return STC_OK;
@@ -375,10 +391,12 @@ stc_status stc_validate_many_async(stc_handle* h, StcScratch& sc, const stc_csr*
 
 // Same validation with the flag word and the two counters supplied by the caller
 // (no handle).
-stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, unsigned long long* counters, stc_stream s) {
+stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, unsigned long long* counters, int num_sms,
+                                        stc_stream s) {
     const int64_t tiles = val_tiles(m->nrows, m->nnz);
     if (tiles > INT32_MAX) return STC_ERR_INVALID_ARG;
-    k_validate_tiles<<<unsigned(tiles), VAL_NT, 0, s>>>(view_of(m), nullptr, nullptr, flags, counters);
+    k_validate_tiles<<<val_grid(tiles, num_sms), VAL_NT, 0, s>>>(view_of(m), nullptr, nullptr, tiles, flags,
+                                                                  counters);
     STC_LAUNCH_CHECK();
     return STC_OK;
 }

@@ -113,7 +113,8 @@ stc_status stc_validate_csr_async(stc_handle* h, const stc_csr* m, stc_stream s)
 stc_status stc_validate_many_async(stc_handle* h, StcScratch& sc, const stc_csr* mats, int count, stc_stream s);
 // The same check raising its flags in `flags` (a device int); needs no handle.
 // `counters` are two device u64, zero before the launch (the kernel leaves them zero).
-stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, unsigned long long* counters, stc_stream s);
+stc_status stc_validate_csr_flags_async(const stc_csr* m, int* flags, unsigned long long* counters, int num_sms,
+                                        stc_stream s);
 // The handle's pair of validation counters.
 unsigned long long* stc_val_counters(stc_handle* h);
 

@@ -43,3 +43,19 @@ def test_algebra_without_bellman_ford_is_rejected():
     G = _graph()
     with pytest.raises(ValueError, match="algebra"):
         stc._check_dist(stc.PLUS_TIMES_F32, G, torch.empty(8, dtype=torch.float32), "bellman_ford")
+
+
+def test_descriptor_follows_field_assignment():
+    """The cached C descriptor (and its bytes, used by batched calls) is rebuilt
+    after any field is assigned."""
+    G = _graph()
+    c0 = G._c()
+    assert (c0.nrows, c0.ncols, c0.nnz) == (8, 8, 0)
+    assert G._c() is c0 and G._c_bytes() == bytes(c0)
+    G.col = torch.zeros(5, dtype=torch.int32)
+    G.rowptr = torch.tensor([0, 5, 5, 5, 5, 5, 5, 5, 5], dtype=torch.int64)
+    c1 = G._c()
+    assert c1 is not c0 and c1.nnz == 5 and c1.col == G.col.data_ptr() and c1.rowptr == G.rowptr.data_ptr()
+    assert G._c_bytes() == bytes(c1)
+    G.nrows = 3
+    assert G._c().nrows == 3 and bytes(G._c()) == G._c_bytes()

@@ -453,3 +453,61 @@ def test_masked_errors(H):
     E = W.Csr(10, 9, np.zeros(11, np.int64), np.zeros(0, np.int32), None)
     C = H.spgemm_masked(O.MP_I32, to_dev(A), to_dev(B), to_dev(E))
     assert C.nnz == 0
+
+
+def _hub_case(K, ncols, per_b, hub_lens, light_rows, light_len, seed):
+    """A with the given hub row lengths (stored entries) followed by light rows;
+    B with per_b distinct columns a row; positive values U[0.5, 2) (no cancellation:
+    the relative error of a sum is its rounding error)."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    lens = list(hub_lens) + [light_len] * light_rows
+    for i, n in enumerate(lens):
+        rows.append(np.full(n, i))
+        cols.append(rng.choice(K, n, replace=False))
+    A = W.csr_from_coo(np.concatenate(rows), np.concatenate(cols), len(lens), K)
+    A.val = rng.uniform(0.5, 2.0, A.nnz).astype(np.float32)
+    br = np.repeat(np.arange(K), per_b)
+    bc = np.concatenate([rng.choice(ncols, per_b, replace=False) for _ in range(K)])
+    B = W.csr_from_coo(br, bc, K, ncols)
+    B.val = rng.uniform(0.5, 2.0, B.nnz).astype(np.float32)
+    return A, B
+
+
+def _check_wide_rows(A, B, rp, col, val, wide_len=1024):
+    """Rows of A with more than wide_len stored entries (summed with compensation):
+    within one fp32 ulp (2^-23 relative) of the fp64 oracle, which plain fp32
+    summation of their hundreds of terms per entry misses; the other rows within
+    the fp32 tolerance."""
+    ptr, rcol, rval, rabs = O.spgemm(O.PT_F32, A, B, want_abs=True)
+    assert np.array_equal(rp, ptr) and np.array_equal(col, rcol)
+    alen = np.diff(A.rowptr)
+    wide = np.repeat(alen > wide_len, np.diff(ptr))
+    got = val.astype(np.float64)
+    rel = np.abs(got - rval) / rval
+    assert wide.any()
+    assert rel[wide].max() <= 2.0 ** -23, rel[wide].max()
+    compare_values(O.PT_F32, val[~wide], rval[~wide], rabs[~wide], "narrow rows")
+
+
+def test_fp32_hub_rows_are_summed_with_compensation(H):
+    import paper_1512_00066_b300 as stc
+    # narrow output (warp-per-row path, hub rows split off to the CTA kernel):
+    # row 0 has 3000 entries (about 375 terms per output entry), row 2 has 1025
+    A, B = _hub_case(4096, 64, 8, [3000, 1024, 1025], 200, 40, seed=3)
+    C = H.spgemm(stc.PLUS_TIMES_F32, to_dev(A), to_dev(B))
+    _check_wide_rows(A, B, *C.to_host())
+    # the same pair in a batch, and through the learned single pass
+    Cs = H.spgemm_batched(stc.PLUS_TIMES_F32, [to_dev(A)] * 3, [to_dev(B)] * 3)
+    _check_wide_rows(A, B, *Cs[1].to_host())
+    C2, _ = H.spgemm_learned(stc.PLUS_TIMES_F32, to_dev(A), to_dev(B))
+    _check_wide_rows(A, B, *C2.to_host())
+    # a wide output (2^17 columns): the hub rows' outputs span several half-width
+    # rank windows
+    A, B = _hub_case(20000, 1 << 17, 16, [3000, 6000], 100, 30, seed=4)
+    C = H.spgemm(stc.PLUS_TIMES_F32, to_dev(A), to_dev(B))
+    rp, col, val = C.to_host()
+    assert np.diff(rp)[1] > 40000
+    _check_wide_rows(A, B, rp, col, val)
+    C2, _ = H.spgemm_learned(stc.PLUS_TIMES_F32, to_dev(A), to_dev(B))
+    _check_wide_rows(A, B, *C2.to_host())
