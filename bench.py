@@ -36,8 +36,8 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM bytes (read + write) per output entry of the fp64 numeric rank kernel, from
 # one ncu capture of that kernel at R-MAT scale 16.
 # Traffic grows with the output (B stays in L2), so a full launch is scaled by its
-# nnz(C): 0.349 GB read + 1.848 GB written for 163,809,247 entries.
-NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = (0.348871e9 + 1.848168e9) / 163809247
+# nnz(C): 0.346 GB read + 1.848 GB written for 163,809,247 entries.
+NUMERIC_FP64_DRAM_BYTES_PER_ENTRY = (0.346040e9 + 1.848326e9) / 163809247
 # FP64 peak of the B300 part: 2 FP64 instructions (DADD, DMUL or DFMA) per clock per SM,
 # 148 SMs, 2032 MHz maximum clock.  FP64_PEAK_TFLOPS is that instruction rate (in units
 # of 1e12 instructions per second); FP64_FMA_PEAK_TFLOPS counts a DFMA as two flops
