@@ -529,13 +529,16 @@ __global__ void k_mf_check_len(const int32_t* __restrict__ w, int64_t nnz, int* 
 //
 // Backward, level by level from the deepest: for a vertex v at level l of source s,
 // delta_s(v) = sigma_s(v) * sum over out-edges v -> w with d_s(w) = l + 1 of
-// (1 + delta_s(w)) / sigma_s(w).  Block per work item of level l, thread per source,
-// pulling the successors' coefficients (no successor counts); items of one vertex
-// add their partial sums atomically, then each vertex's sum becomes delta and its
-// coefficient.
+// (1 + delta_s(w)) / sigma_s(w).  Warp per work item of level l, eight sources per
+// lane, pulling the successors' coefficients (no successor counts) where a byte
+// table of BFS levels, written by the forward, says d_s(w) = l + 1; items of one
+// vertex add their partial sums atomically, then each vertex's sum becomes delta
+// and its coefficient.
 
 constexpr int MU_W = 8;                  // mask words per vertex (MF_NT = 256 sources)
-constexpr int MU_MAX_ROUNDS = 4096;      // rounds recorded; deeper searches use the general kernels
+constexpr int MU_MAX_ROUNDS = 254;       // levels recorded (one byte each, 255 = unreached); deeper
+                                         // searches use the general kernels
+constexpr int MU_LS = MF_NT;             // bytes per vertex of the level table
 enum : int {
     MU_C_ITEMS = 0,   // items appended by the current round's update
     MU_C_ROUND = 1,   // forward round / backward level
@@ -549,6 +552,7 @@ struct MuState {
     uint32_t* vis;
     uint32_t* nxt;
     uint32_t* fm;
+    uint8_t* lvl;      // [v][MU_LS] BFS level of v from each source (255: not reached)
     int2* items;       // all rounds' work items, round r at [off[r], off[r + 1])
     int64_t item_cap;
     int* off;          // MU_MAX_ROUNDS + 2 offsets
@@ -570,6 +574,7 @@ __global__ void k_mu_seed(MfGraph g, MfState st, MuState u, const int32_t* __res
         const int64_t i = int64_t(v) * st.S + s;
         st.d[i] = 0;
         st.sig[i] = 1.0;
+        u.lvl[int64_t(v) * MU_LS + s] = 0;
         atomicOr(&u.vis[int64_t(v) * MU_W + (s >> 5)], 1u << (s & 31));
         atomicOr(&u.fm[int64_t(v) * MU_W + (s >> 5)], 1u << (s & 31));
         if (atomicExch(&st.stamp[v], -2) != -2) {
@@ -647,6 +652,7 @@ __global__ void __launch_bounds__(256) k_mu_update(MfGraph g, MfState st, MuStat
             const int s = k * 32 + lane;
             if ((N[k] >> lane) & 1u) {
                 const int64_t i = int64_t(v) * S + s;
+                u.lvl[int64_t(v) * MU_LS + s] = uint8_t(r + 1);
                 st.d[i] = r + 1;
                 st.sig[i] = st.dln[i];
                 st.dln[i] = 0.0;
@@ -697,61 +703,109 @@ __global__ void k_mu_back_init(MuState u) {
     if (threadIdx.x == 0 && blockIdx.x == 0) u.cnt[MU_C_ROUND] = u.cnt[MU_C_FAIL] ? -1 : u.cnt[MU_C_LAST];
 }
 
+// Backward: a warp per work item, eight sources per lane (sources 8j .. 8j + 7 on
+// lane j), the level table read eight bytes a lane: one coalesced 256-byte read per
+// out-edge covers every source, and the byte compares pick the sources for which
+// the edge lies on a shortest path.
+constexpr int MU_PULL_UNR = 4;  // out-edges whose successors' levels are in flight together
+
+// Bit j set where byte j of v equals x (x < 256).
+__device__ __forceinline__ unsigned mu_byte_eq8(uint2 v, unsigned x) {
+    const unsigned rep = x * 0x01010101u;
+    const unsigned a = __vcmpeq4(v.x, rep), b = __vcmpeq4(v.y, rep);
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m |= ((a >> (8 * j + 7)) & 1u) << j | ((b >> (8 * j + 7)) & 1u) << (j + 4);
+    return m;
+}
+
+__device__ __forceinline__ uint2 mu_levels8(const MuState& u, int32_t v, int s0) {
+    return *reinterpret_cast<const uint2*>(u.lvl + int64_t(v) * MU_LS + s0);
+}
+
 // Partial sums of level l's items: acc (st.dl) += sum over the item's out-edges
-// v -> w with d_s(w) = l + 1 of coef_s(w) (st.dln of level l + 1).
-__global__ void __launch_bounds__(MF_NT) k_mu_pull(MfGraph g, MfState st, MuState u) {
+// v -> w with d_s(w) = l + 1 of coef_s(w) (st.dln of level l + 1).  The warp reads 32
+// of the item's columns at once and shares them by shuffles.
+__global__ void __launch_bounds__(256) k_mu_pull(MfGraph g, MfState st, MuState u) {
     const int S = st.S;
-    const int s = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int l = u.cnt[MU_C_ROUND];
     if (l < 0) return;
+    const int s0 = lane * 8;
+    const unsigned valid = S - s0 >= 8 ? 0xffu : (S > s0 ? (1u << (S - s0)) - 1u : 0u);
     const int i0 = u.off[l], i1 = u.off[l + 1];
-    for (int t = i0 + blockIdx.x; t < i1; t += gridDim.x) {
+    const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+    for (int t = i0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); t < i1; t += nwarps) {
         const int2 it = u.items[t];
         const int32_t v = it.x;
+        const unsigned act = valid ? mu_byte_eq8(mu_levels8(u, v, s0), unsigned(l)) & valid : 0u;
+        if (!__any_sync(0xffffffffu, act != 0u)) continue;
         int64_t e0, e1;
         mf_item_edges(g, it, e0, e1);
-        const bool act = s < S && st.d[int64_t(v) * S + s] == l;
-        if (!act) continue;  // a warp whose sources are all elsewhere skips the item
-        double acc = 0.0;
-        for (int64_t p0 = e0; p0 < e1; p0 += MF_UNR) {
-            int32_t w[MF_UNR];
-            int dw[MF_UNR];
+        double acc[8];
 #pragma unroll
-            for (int k = 0; k < MF_UNR; ++k) {
-                const int64_t p = p0 + k;
-                w[k] = -1;
-                if (p < e1) {
-                    const int32_t y = g.col[p];
-                    if ((uint64_t)y < (uint64_t)g.n) w[k] = y;
+        for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+        for (int64_t c0 = e0; c0 < e1; c0 += 32) {
+            const int nc = int(e1 - c0 < 32 ? e1 - c0 : 32);
+            int32_t wl = -1;
+            if (lane < nc) {
+                const int32_t y = g.col[c0 + lane];
+                if ((uint64_t)y < (uint64_t)g.n) wl = y;
+            }
+            for (int k0 = 0; k0 < nc; k0 += MU_PULL_UNR) {
+                int32_t w[MU_PULL_UNR];
+                uint2 lw[MU_PULL_UNR];
+#pragma unroll
+                for (int k = 0; k < MU_PULL_UNR; ++k) {
+                    w[k] = __shfl_sync(0xffffffffu, wl, (k0 + k) & 31);
+                    if (k0 + k >= nc) w[k] = -1;
+                }
+#pragma unroll
+                for (int k = 0; k < MU_PULL_UNR; ++k)
+                    lw[k] = (act && w[k] >= 0) ? mu_levels8(u, w[k], s0) : make_uint2(~0u, ~0u);
+#pragma unroll
+                for (int k = 0; k < MU_PULL_UNR; ++k) {
+                    const unsigned m = mu_byte_eq8(lw[k], unsigned(l + 1)) & act;
+                    if (m) {
+                        const double* cw = st.dln + int64_t(w[k]) * S + s0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if ((m >> j) & 1u) acc[j] += cw[j];
+                    }
                 }
             }
-#pragma unroll
-            for (int k = 0; k < MF_UNR; ++k) dw[k] = w[k] >= 0 ? st.d[int64_t(w[k]) * S + s] : -1;
-#pragma unroll
-            for (int k = 0; k < MF_UNR; ++k)
-                if (dw[k] == l + 1) acc += st.dln[int64_t(w[k]) * S + s];
         }
-        if (acc != 0.0) atomicAdd(&st.dl[int64_t(v) * S + s], acc);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (((act >> j) & 1u) && acc[j] != 0.0) atomicAdd(&st.dl[int64_t(v) * S + s0 + j], acc[j]);
     }
 }
 
 // Level l's sums become delta_s(v) = sigma_s(v) * sum and coef_s(v) = (1 + delta) /
-// sigma (one block per vertex: its chunk-0 item); then the next level up.
-__global__ void __launch_bounds__(MF_NT) k_mu_final(MfState st, MuState u) {
+// sigma (a warp per vertex: its chunk-0 item); then the next level up.
+__global__ void __launch_bounds__(256) k_mu_final(MfState st, MuState u) {
     const int S = st.S;
-    const int s = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int l = u.cnt[MU_C_ROUND];
     if (l < 0) return;
+    const int s0 = lane * 8;
+    const unsigned valid = S - s0 >= 8 ? 0xffu : (S > s0 ? (1u << (S - s0)) - 1u : 0u);
     const int i0 = u.off[l], i1 = u.off[l + 1];
-    for (int t = i0 + blockIdx.x; t < i1; t += gridDim.x) {
+    const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+    for (int t = i0 + int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); t < i1; t += nwarps) {
         const int2 it = u.items[t];
-        if (it.y != 0 || s >= S) continue;
-        const int64_t i = int64_t(it.x) * S + s;
-        if (st.d[i] != l) continue;
-        const double sg = st.sig[i];
-        const double dlt = sg * st.dl[i];
-        st.dl[i] = dlt;
-        st.dln[i] = (1.0 + dlt) / sg;
+        if (it.y != 0 || !valid) continue;
+        const unsigned m = mu_byte_eq8(mu_levels8(u, it.x, s0), unsigned(l)) & valid;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if ((m >> j) & 1u) {
+                const int64_t i = int64_t(it.x) * S + s0 + j;
+                const double sg = st.sig[i];
+                const double dlt = sg * st.dl[i];
+                st.dl[i] = dlt;
+                st.dln[i] = (1.0 + dlt) / sg;
+            }
+        }
     }
 }
 
@@ -962,6 +1016,7 @@ stc_status mu_alloc(StcScratch& sc, const MfGraph& g, MuState& u) {
     u.vis = sc.get<uint32_t>(n * MU_W);
     u.nxt = sc.get<uint32_t>(n * MU_W);
     u.fm = sc.get<uint32_t>(n * MU_W);
+    u.lvl = sc.get<uint8_t>(n * MU_LS);
     // every vertex on a few levels: eight times one round's worth of items
     u.item_cap = 8 * (int64_t(g.n) + g.nnz / MF_ITEM_EDGES + 1) + 1024;
     if (u.item_cap > int64_t(INT32_MAX)) u.item_cap = INT32_MAX;
@@ -976,6 +1031,7 @@ stc_status mu_clear(stc_handle* h, const MfBatch& b, const MuState& u, stc_strea
     STC_CUDA_TRY(cudaMemsetAsync(u.vis, 0, n * MU_W * 4, s));
     STC_CUDA_TRY(cudaMemsetAsync(u.nxt, 0, n * MU_W * 4, s));
     STC_CUDA_TRY(cudaMemsetAsync(u.fm, 0, n * MU_W * 4, s));
+    STC_CUDA_TRY(cudaMemsetAsync(u.lvl, 0xff, n * MU_LS, s));
     STC_CUDA_TRY(cudaMemsetAsync(u.cnt, 0, MU_C_NUM * sizeof(int), s));
     (void)h;
     return STC_OK;
@@ -987,7 +1043,7 @@ unsigned mu_warp_grid(stc_handle* h) { return unsigned(h->num_sms * 8); }  // 25
 stc_status mu_run_host(stc_handle* h, const MfBatch& b, const MuState& u, stc_stream s) {
     const MfGraph& g = b.g;
     const MfState& st = b.st;
-    const unsigned rg = mf_round_grid(h), wg = mu_warp_grid(h);
+    const unsigned wg = mu_warp_grid(h);
     const cudaGraphConditionalHandle none = 0;
     int* go = reinterpret_cast<int*>(&h->h_stage[4]);
     stc_status e;
@@ -1011,8 +1067,8 @@ stc_status mu_run_host(stc_handle* h, const MfBatch& b, const MuState& u, stc_st
     STC_LAUNCH_CHECK();
     stc_count(h);
     for (;;) {
-        k_mu_pull<<<rg, MF_NT, 0, s>>>(g, st, u);
-        k_mu_final<<<rg, MF_NT, 0, s>>>(st, u);
+        k_mu_pull<<<wg, 256, 0, s>>>(g, st, u);
+        k_mu_final<<<wg, 256, 0, s>>>(st, u);
         k_mu_back_check<<<1, 1, 0, s>>>(st, u, 0, none);
         STC_LAUNCH_CHECK();
         stc_count(h, 3);
@@ -1038,7 +1094,7 @@ stc_status mu_run_host(stc_handle* h, const MfBatch& b, const MuState& u, stc_st
 cudaError_t mu_build_graph(stc_handle* h, MfBatch b, MuState u, MfGraphExec& x) {
     x.reset();
     MF_G(cudaGraphCreate(&x.graph, 0));
-    const unsigned rg = mf_round_grid(h), wg = mu_warp_grid(h);
+    const unsigned wg = mu_warp_grid(h);
     int in_graph = 1;
     int64_t n = b.g.n;
     cudaGraphNode_t n_seed, n_fw;
@@ -1067,8 +1123,8 @@ cudaError_t mu_build_graph(stc_handle* h, MfBatch b, MuState u, MfGraphExec& x) 
         void* a_pull[] = {&b.g, &b.st, &u};
         void* a_fin[] = {&b.st, &u};
         void* a_chk[] = {&b.st, &u, &in_graph, &hb};
-        MF_G(mf_add_kernel(bb, &k1, nullptr, (const void*)k_mu_pull, rg, MF_NT, a_pull));
-        MF_G(mf_add_kernel(bb, &k2, &k1, (const void*)k_mu_final, rg, MF_NT, a_fin));
+        MF_G(mf_add_kernel(bb, &k1, nullptr, (const void*)k_mu_pull, wg, 256, a_pull));
+        MF_G(mf_add_kernel(bb, &k2, &k1, (const void*)k_mu_final, wg, 256, a_fin));
         MF_G(mf_add_kernel(bb, &k3, &k2, (const void*)k_mu_back_check, 1, 1, a_chk));
         const int* skip = &u.cnt[MU_C_FAIL];
         void* a_bc[] = {&b.st, &n, &b.src, &b.bc, &skip};
