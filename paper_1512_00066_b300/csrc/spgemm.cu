@@ -1558,46 +1558,45 @@ k_wr_numeric(SpgRows R, const int32_t* __restrict__ row_mat, const int32_t* __re
     }
 }
 
-// Rows of the list [0, *nlist) split for the numeric pass into three lists
-// (order inside a list follows the row list): out[0] rows with at most WR_VCAP_S
-// output entries, out[1] rows with at most WR_VCAP, out[2] the heavy prefix
-// [0, *heavy_ptr) (too many products for one warp), rows of A with more than
-// wide_len stored entries (compensated sums, CTA kernels only) and the rest;
-// n[0..2] sizes.
-__global__ void k_split_by_count(SpgRows R, const int32_t* __restrict__ row_mat, int64_t wide_len,
-                                 const int32_t* __restrict__ rowlist, const int* __restrict__ nlist_ptr,
-                                 const int* __restrict__ heavy_ptr, const int64_t* __restrict__ c_ptr,
-                                 int32_t* __restrict__ out0, int32_t* __restrict__ out1, int32_t* __restrict__ out2,
-                                 int* __restrict__ n) {
-    const int nlist = *nlist_ptr, heavy = *heavy_ptr;
-    const int lane = threadIdx.x & 31;
-    for (int r0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; r0 < nlist; r0 += gridDim.x * blockDim.x) {
-        const int r = r0 + lane;
-        int32_t gi = -1;
-        int cls = 3;
-        if (r < nlist) {
-            gi = rowlist[r];
+// Rows [0, NR) with output entries, split for the numeric pass into three lists
+// in row order, so that the rows of one matrix of a batch run together while its B
+// stays in L2: out[0] rows with at most WR_VCAP_S output entries, out[1] at most
+// WR_VCAP, out[2] the rest: rows with 2^WR_UB_LOG2 products or more (too many for
+// one warp), rows of A with more than wide_len stored entries (compensated sums,
+// CTA kernels only) and wider outputs.  Rows with one stored entry (the copy
+// kernel's) are left out; n[0..2] sizes.  A block takes 256 consecutive rows.
+__global__ void __launch_bounds__(256) k_split_by_count(SpgRows R, const int32_t* __restrict__ row_mat,
+                                                        int64_t wide_len, int64_t NR,
+                                                        const int64_t* __restrict__ ub,
+                                                        const int64_t* __restrict__ c_ptr,
+                                                        int32_t* __restrict__ out0, int32_t* __restrict__ out1,
+                                                        int32_t* __restrict__ out2, int* __restrict__ n) {
+    __shared__ int s_cnt[3], s_base[3];
+    for (int64_t r0 = int64_t(blockIdx.x) * blockDim.x; r0 < NR; r0 += int64_t(gridDim.x) * blockDim.x) {
+        if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t gi = r0 + threadIdx.x;
+        int cls = 3, local = 0;
+        if (gi < NR) {
+            const int64_t u = ub[gi];
             const int64_t c = c_ptr[gi + 1] - c_ptr[gi];
-            bool wide = false;
-            if (wide_len != NO_WIDE_ROWS) {
+            if (u > 0 && c > 0) {
                 const int b = row_mat ? row_mat[gi] : 0;
                 const SpgArgs& g = R.table ? R.table[b] : R.one;
                 int64_t lo, hi;
                 row_range(g.a_ptr, gi - (R.table ? R.row_off[b] : 0), g.nnzA, lo, hi);
-                wide = hi - lo > wide_len;
+                if (hi - lo != 1) {
+                    const bool heavy = bin_of(u) > WR_UB_LOG2;
+                    cls = (heavy || hi - lo > wide_len) ? 2 : c <= WR_VCAP_S ? 0 : c <= WR_VCAP ? 1 : 2;
+                }
             }
-            cls = (r < heavy || wide) ? 2 : c <= WR_VCAP_S ? 0 : c <= WR_VCAP ? 1 : 2;
         }
-        const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const unsigned m = __ballot_sync(0xffffffffu, cls == k);
-            int b = 0;
-            if (lane == 0 && m) b = atomicAdd(&n[k], __popc(m));
-            b = __shfl_sync(0xffffffffu, b, 0);
-            int32_t* out = k == 0 ? out0 : k == 1 ? out1 : out2;
-            if (cls == k) out[b + __popc(m & below)] = gi;
-        }
+        if (cls < 3) local = atomicAdd(&s_cnt[cls], 1);
+        __syncthreads();
+        if (threadIdx.x < 3) s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&n[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+        __syncthreads();
+        if (cls < 3) (cls == 0 ? out0 : cls == 1 ? out1 : out2)[s_base[cls] + local] = int32_t(gi);
+        __syncthreads();
     }
 }
 
@@ -2404,8 +2403,8 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
             if (!lists) return fail(STC_ERR_OOM);
             int64_t blocks = (NR + 255) / 256;
             if (blocks > int64_t(h->num_sms) * 8) blocks = int64_t(h->num_sms) * 8;
-            k_split_by_count<<<unsigned(blocks), 256, 0, s>>>(R, row_mat, wide_len_of(alg), rowlist, nlist, wr_heavy,
-                                                              c_ptr, lists, lists + NR, lists + 2 * NR, nsplit);
+            k_split_by_count<<<unsigned(blocks), 256, 0, s>>>(R, row_mat, wide_len_of(alg), NR, ub, c_ptr, lists,
+                                                              lists + NR, lists + 2 * NR, nsplit);
             if (cudaGetLastError() != cudaSuccess) return fail(STC_ERR_CUDA);
             stc_count(h);
             if (max_row > WR_VCAP || wr_heavy_rows > 0 || maybe_wide) {
