@@ -174,6 +174,76 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_min(MfGraph g, MfState st) {
     }
 }
 
+// Batches of at most MF_WARP_UNITS_MAX sources run the relax and backward kernels
+// by work units (item, group of 32 sources), one warp each, lane per source: a unit
+// whose sources are all idle at the item's vertex ends after one vote, no block-wide
+// barrier is needed, and a block's threads are not left idle by a small batch.  A
+// warp reads 32 edges' targets and lengths at once (one per lane) and hands them
+// round by shuffles.  Larger batches keep a block per item (the eight warps of an
+// item share its edge loads).
+constexpr int MF_WARP_UNITS_MAX = 128;
+__device__ __forceinline__ int mf_groups(int S) { return (S + 31) >> 5; }
+
+// Edges [c0, c0 + 32) of [c0, e1): lane j's target (or -1) and length.
+__device__ __forceinline__ void mf_edge_chunk(const MfGraph& g, int64_t c0, int64_t e1, int lane, int32_t& v,
+                                              int& w) {
+    v = -1;
+    w = 0;
+    if (c0 + lane < e1) {
+        const int32_t x = g.col[c0 + lane];
+        if ((uint64_t)x < (uint64_t)g.n) v = x;
+        w = edge_len(g, c0 + lane);
+    }
+}
+
+// k_mf_relax_min by warp units; a target is listed (once) as touched when some
+// source's candidate reaches or lowers its distance.
+__global__ void __launch_bounds__(MF_NT) k_mf_relax_min_w(MfGraph g, MfState st) {
+    const int S = st.S;
+    const int lane = threadIdx.x & 31;
+    const int ng = mf_groups(S);
+    const int r = st.cnt[MF_C_FROUND];
+    const int nitems = st.cnt[MF_C_ITEMS + (r & 1)];
+    const int2* __restrict__ F = mf_pick(st.items, r);
+    const int units = nitems * ng;
+    const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+    for (int q = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); q < units; q += nwarps) {
+        const int2 it = F[q / ng];
+        const int s = (q % ng) * 32 + lane;
+        const int32_t u = it.x;
+        const bool act = s < S && st.dl[int64_t(u) * S + s] > 0.0;
+        if (!__any_sync(0xffffffffu, act)) continue;
+        const int du = act ? st.d[int64_t(u) * S + s] : 0;
+        int64_t e0, e1;
+        mf_item_edges(g, it, e0, e1);
+        for (int64_t c0 = e0; c0 < e1; c0 += 32) {
+            int32_t vl;
+            int wl;
+            mf_edge_chunk(g, c0, e1, lane, vl, wl);
+            const int nc = int(e1 - c0 < 32 ? e1 - c0 : 32);
+            for (int k0 = 0; k0 < nc; k0 += MF_UNR) {
+                int32_t v[MF_UNR];
+                int w[MF_UNR], cur[MF_UNR];
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) {
+                    v[k] = __shfl_sync(0xffffffffu, vl, (k0 + k) & 31);
+                    w[k] = __shfl_sync(0xffffffffu, wl, (k0 + k) & 31);
+                    if (k0 + k >= nc) v[k] = -1;
+                }
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) cur[k] = (act && v[k] >= 0) ? st.dn[int64_t(v[k]) * S + s] : 0;
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) {
+                    const bool near = act && v[k] >= 0 && du + w[k] <= cur[k];
+                    if (near && du + w[k] < cur[k]) atomicMin(&st.dn[int64_t(v[k]) * S + s], du + w[k]);
+                    if (__any_sync(0xffffffffu, near) && lane == 0)
+                        mf_touch(st.stamp, st.list[1], &st.cnt[MF_C_TOUCHED], v[k], r);
+                }
+            }
+        }
+    }
+}
+
 // Phases A and B in one pass for unit lengths (g.w == null): every source's
 // frontier in round r is its BFS level r (all sources start together), so every
 // candidate of the round is r + 1 and none can lower a target below a tie; the
@@ -259,6 +329,50 @@ __global__ void __launch_bounds__(MF_NT) k_mf_relax_add(MfGraph g, MfState st) {
 #pragma unroll
             for (int k = 0; k < MF_UNR; ++k)
                 if (v[k] >= 0 && du + w[k] == cur[k]) atomicAdd(&st.dln[int64_t(v[k]) * S + s], m);
+        }
+    }
+}
+
+// k_mf_relax_add by warp units.
+__global__ void __launch_bounds__(MF_NT) k_mf_relax_add_w(MfGraph g, MfState st) {
+    const int S = st.S;
+    const int lane = threadIdx.x & 31;
+    const int ng = mf_groups(S);
+    const int r = st.cnt[MF_C_FROUND];
+    const int nitems = st.cnt[MF_C_ITEMS + (r & 1)];
+    const int2* __restrict__ F = mf_pick(st.items, r);
+    const int units = nitems * ng;
+    const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+    for (int q = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); q < units; q += nwarps) {
+        const int2 it = F[q / ng];
+        const int s = (q % ng) * 32 + lane;
+        const int32_t u = it.x;
+        const double m = s < S ? st.dl[int64_t(u) * S + s] : 0.0;
+        const bool act = m > 0.0;
+        if (!__any_sync(0xffffffffu, act)) continue;
+        const int du = act ? st.d[int64_t(u) * S + s] : 0;
+        int64_t e0, e1;
+        mf_item_edges(g, it, e0, e1);
+        for (int64_t c0 = e0; c0 < e1; c0 += 32) {
+            int32_t vl;
+            int wl;
+            mf_edge_chunk(g, c0, e1, lane, vl, wl);
+            const int nc = int(e1 - c0 < 32 ? e1 - c0 : 32);
+            for (int k0 = 0; k0 < nc; k0 += MF_UNR) {
+                int32_t v[MF_UNR];
+                int w[MF_UNR], cur[MF_UNR];
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) {
+                    v[k] = __shfl_sync(0xffffffffu, vl, (k0 + k) & 31);
+                    w[k] = __shfl_sync(0xffffffffu, wl, (k0 + k) & 31);
+                    if (k0 + k >= nc) v[k] = -1;
+                }
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) cur[k] = (act && v[k] >= 0) ? st.dn[int64_t(v[k]) * S + s] : 0;
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k)
+                    if (act && v[k] >= 0 && du + w[k] == cur[k]) atomicAdd(&st.dln[int64_t(v[k]) * S + s], m);
+            }
         }
     }
 }
@@ -418,6 +532,67 @@ __global__ void __launch_bounds__(MF_NT) k_mf_back(MfGraph gt, MfState st) {
                     // the source whose count reaches zero lists v (once per round)
                     if (atomicSub(&st.dn[iv], 1) == 1 && atomicExch(&st.stamp[v[k]], stamp) != stamp)
                         next[atomicAdd(nnext, 1)] = v[k];
+                }
+            }
+        }
+    }
+}
+
+// k_mf_back by warp units: a warp per (ready vertex, group of 32 sources).
+__global__ void __launch_bounds__(MF_NT) k_mf_back_w(MfGraph gt, MfState st) {
+    const int S = st.S;
+    const int lane = threadIdx.x & 31;
+    const int ng = mf_groups(S);
+    const int r = st.cnt[MF_C_BROUND];
+    const int cur_l = r & 1;
+    const int nR = st.cnt[MF_C_READY + cur_l];
+    const int32_t* __restrict__ ready = mf_pick(st.list, cur_l);
+    int32_t* __restrict__ next = mf_pick(st.list, cur_l ^ 1);
+    int* nnext = &st.cnt[MF_C_READY + (cur_l ^ 1)];
+    const int stamp = r + (1 << 30);  // disjoint from the forward rounds' stamps
+    const int units = nR * ng;
+    const int nwarps = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+    for (int q = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); q < units; q += nwarps) {
+        const int32_t w = ready[q / ng];
+        const int s = (q % ng) * 32 + lane;
+        const int64_t iw = int64_t(w) * S + s;
+        bool go = false;
+        double coef = 0.0;
+        int dw = 0;
+        if (s < S && st.dn[iw] == 0) {
+            go = true;
+            st.dn[iw] = -1;  // processed
+            coef = (1.0 + st.dl[iw]) / st.sig[iw];
+            dw = st.d[iw];
+        }
+        if (!__any_sync(0xffffffffu, go)) continue;
+        int64_t lo, hi;
+        row_range(gt.ptr, w, gt.nnz, lo, hi);
+        for (int64_t c0 = lo; c0 < hi; c0 += 32) {
+            int32_t vl;
+            int ll;
+            mf_edge_chunk(gt, c0, hi, lane, vl, ll);
+            const int nc = int(hi - c0 < 32 ? hi - c0 : 32);
+            for (int k0 = 0; k0 < nc; k0 += MF_UNR) {
+                int32_t v[MF_UNR];
+                int len[MF_UNR], dv[MF_UNR];
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) {
+                    v[k] = __shfl_sync(0xffffffffu, vl, (k0 + k) & 31);
+                    len[k] = __shfl_sync(0xffffffffu, ll, (k0 + k) & 31);
+                    if (k0 + k >= nc) v[k] = -1;
+                }
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) dv[k] = (go && v[k] >= 0) ? st.d[int64_t(v[k]) * S + s] : 0;
+#pragma unroll
+                for (int k = 0; k < MF_UNR; ++k) {
+                    if (go && v[k] >= 0 && dv[k] + len[k] == dw) {
+                        const int64_t iv = int64_t(v[k]) * S + s;
+                        atomicAdd(&st.dl[iv], st.sig[iv] * coef);
+                        // the source whose count reaches zero lists v (once per round)
+                        if (atomicSub(&st.dn[iv], 1) == 1 && atomicExch(&st.stamp[v[k]], stamp) != stamp)
+                            next[atomicAdd(nnext, 1)] = v[k];
+                    }
                 }
             }
         }
@@ -848,7 +1023,10 @@ stc_status mf_run_host(stc_handle* h, const MfBatch& b, stc_stream s) {
     STC_LAUNCH_CHECK();
     stc_count(h, 2);
     for (;;) {
-        if (g.w) {
+        if (g.w && st.S <= MF_WARP_UNITS_MAX) {
+            k_mf_relax_min_w<<<rg, MF_NT, 0, s>>>(g, st);
+            k_mf_relax_add_w<<<rg, MF_NT, 0, s>>>(g, st);
+        } else if (g.w) {
             k_mf_relax_min<<<rg, MF_NT, 0, s>>>(g, st);
             k_mf_relax_add<<<rg, MF_NT, 0, s>>>(g, st);
         } else {
@@ -868,7 +1046,10 @@ stc_status mf_run_host(stc_handle* h, const MfBatch& b, stc_stream s) {
     STC_LAUNCH_CHECK();
     stc_count(h);
     for (;;) {
-        k_mf_back<<<rg, MF_NT, 0, s>>>(b.gt, st);
+        if (st.S <= MF_WARP_UNITS_MAX)
+            k_mf_back_w<<<rg, MF_NT, 0, s>>>(b.gt, st);
+        else
+            k_mf_back<<<rg, MF_NT, 0, s>>>(b.gt, st);
         k_mf_back_check<<<1, 1, 0, s>>>(st, g.n, h->d_flags, 0, none);
         STC_LAUNCH_CHECK();
         stc_count(h, 2);
@@ -959,11 +1140,12 @@ cudaError_t mf_build_graph(stc_handle* h, MfBatch b, MfGraphExec& x) {
         void* a_gs[] = {&b.g, &b.st};
         void* a_st[] = {&b.st};
         void* a_chk[] = {&b.st, &n, &flags, &in_graph, &hf};
-        MF_G(mf_add_kernel(fb, &k1, nullptr,
-                           b.g.w ? (const void*)k_mf_relax_min : (const void*)k_mf_relax_unit, rg,
-                           MF_NT, a_gs));
+        const bool wu = b.st.S <= MF_WARP_UNITS_MAX;
+        const void* relax_min = wu ? (const void*)k_mf_relax_min_w : (const void*)k_mf_relax_min;
+        const void* relax_add = wu ? (const void*)k_mf_relax_add_w : (const void*)k_mf_relax_add;
+        MF_G(mf_add_kernel(fb, &k1, nullptr, b.g.w ? relax_min : (const void*)k_mf_relax_unit, rg, MF_NT, a_gs));
         k2 = k1;
-        if (b.g.w) MF_G(mf_add_kernel(fb, &k2, &k1, (const void*)k_mf_relax_add, rg, MF_NT, a_gs));
+        if (b.g.w) MF_G(mf_add_kernel(fb, &k2, &k1, relax_add, rg, MF_NT, a_gs));
         MF_G(mf_add_kernel(fb, &k3, &k2, (const void*)k_mf_clear_frontier, rg, MF_NT, a_st));
         MF_G(mf_add_kernel(fb, &k4, &k3, (const void*)k_mf_update, rg, MF_NT, a_gs));
         MF_G(mf_add_kernel(fb, &k5, &k4, (const void*)k_mf_fwd_check, 1, 1, a_chk));
@@ -979,7 +1161,8 @@ cudaError_t mf_build_graph(stc_handle* h, MfBatch b, MfGraphExec& x) {
         cudaGraphNode_t k1, k2;
         void* a_back[] = {&b.gt, &b.st};
         void* a_chk[] = {&b.st, &n, &flags, &in_graph, &hb};
-        MF_G(mf_add_kernel(bb, &k1, nullptr, (const void*)k_mf_back, rg, MF_NT, a_back));
+        const void* back = b.st.S <= MF_WARP_UNITS_MAX ? (const void*)k_mf_back_w : (const void*)k_mf_back;
+        MF_G(mf_add_kernel(bb, &k1, nullptr, back, rg, MF_NT, a_back));
         MF_G(mf_add_kernel(bb, &k2, &k1, (const void*)k_mf_back_check, 1, 1, a_chk));
         const int* no_skip = nullptr;
         void* a_bc[] = {&b.st, &n, &b.src, &b.bc, &no_skip};
