@@ -607,6 +607,7 @@ constexpr int RK_CELL = 1 << RK_CELL_SHIFT;
 constexpr int RK_MAX_COLS = 1 << 18;        // 32 KB bitmap
 constexpr int RK_NT = 1024;     // numeric kernel: one CTA per SM, large value buffer
 constexpr int RK_SYM_NT = 256;  // symbolic kernel: more rows in flight per SM
+constexpr int RK_SYM_MINB = 5;  // its CTAs per SM (34 KB of shared memory each at 2^18 columns)
 constexpr size_t RK_SMEM_TARGET = 224 * 1024;  // one CTA per SM
 constexpr double RK_RECORD_BUDGET = 24e9;        // bytes of stored rank records
 constexpr int RK_SPARSE_MAX_WORDS = 4096;         // sparse record: at most this many non-zero words
@@ -819,10 +820,11 @@ __host__ __device__ inline RankLayout rank_layout(int ncell, int vcap, int maxwi
     return L;
 }
 
-// Shared-memory layout of the symbolic rank kernel: compact bitmap, summary, per
-// word prefix inside its cell, cell prefix.
+// Shared-memory layout of the symbolic rank kernel: compact bitmap, summary, cell
+// prefix.  (A word's rank inside its cell is a warp scan when the record is written:
+// a cell is 32 words, one per lane.)
 struct SymLayout {
-    size_t bits, summ, wpre, cellbase, total;
+    size_t bits, summ, cellbase, total;
 };
 
 __host__ __device__ inline SymLayout sym_layout(int ncell) {
@@ -830,10 +832,20 @@ __host__ __device__ inline SymLayout sym_layout(int ncell) {
     const size_t NW = size_t(ncell) * 32;
     L.bits = 0;
     L.summ = rk_align(NW * 4);
-    L.wpre = rk_align(L.summ + size_t(ncell) * 4);
-    L.cellbase = rk_align(L.wpre + NW * 2);
+    L.cellbase = rk_align(L.summ + size_t(ncell) * 4);
     L.total = rk_align(L.cellbase + (size_t(ncell) + 1) * 4);
     return L;
+}
+
+// Exclusive prefix of x over the warp's lanes.
+__device__ __forceinline__ int warp_exclusive_sum(int x, int lane) {
+    int y = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += t;
+    }
+    return y - x;
 }
 
 // Persistent-CTA row loop over a row list of global rows.  Thread 0 claims rows
@@ -894,13 +906,14 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem_raw);
     uint32_t* bits = reinterpret_cast<uint32_t*>(sm + L.bits);
     uint32_t* summ = reinterpret_cast<uint32_t*>(sm + L.summ);  // one summary word per cell
-    uint16_t* wpre = reinterpret_cast<uint16_t*>(sm + L.wpre);
     int* cellbase = reinterpret_cast<int*>(sm + L.cellbase);
     const int64_t rec_bytes = int64_t(LR.winfirst);
     __shared__ TaskSmem<NT> ts;
     __shared__ SpgArgs s_args;
     __shared__ int64_t s_row[3];
     __shared__ int s_red[NT / 32 + 1];
+    __shared__ int s_zb[RK_MAX_COLS / RK_CELL];  // sparse record: first slot of each cell's words
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int w = threadIdx.x; w < NWmax; w += NT) bits[w] = 0u;
     for (int c = threadIdx.x; c < ncell_max; c += NT) summ[c] = 0u;
     const int nlist = *nlist_ptr;
@@ -923,16 +936,14 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
         int tot;
         if (rec) {
             // summary bits: one ballot per 32 words
-            {
-                const int lane = threadIdx.x & 31;
-                for (int c = threadIdx.x >> 5; c < g.ncell; c += NT / 32) {
-                    const unsigned m = __ballot_sync(0xffffffffu, bits[c * 32 + lane] != 0u);
-                    if (lane == 0) summ[c] = m;
-                }
-                __syncthreads();
+            for (int c = wid; c < g.ncell; c += NT / 32) {
+                const unsigned m = __ballot_sync(0xffffffffu, bits[c * 32 + lane] != 0u);
+                if (lane == 0) summ[c] = m;
             }
-            // ranks: word prefix inside each cell and the cells' exclusive prefix;
-            // the whole rank structure is stored for the numeric pass
+            __syncthreads();
+            // ranks: the cells' exclusive prefix (a word's rank inside its cell is
+            // taken by a warp scan when the record is written); the whole rank
+            // structure is stored for the numeric pass
             constexpr int CPT = (RK_MAX_COLS / RK_CELL + NT - 1) / NT;
             int cnt[CPT];
             int ctot = 0;
@@ -945,7 +956,6 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
                     while (sw) {
                         const int w = c * 32 + __ffs(sw) - 1;
                         sw &= sw - 1;
-                        wpre[w] = uint16_t(n);
                         n += __popc(bits[w]);
                     }
                 }
@@ -976,32 +986,38 @@ k_symbolic_rank(SpgRows R, int ncell_max, const int32_t* __restrict__ rowlist, c
                 int zex = block_exclusive_scan<NT, int>(nz, s_red, nzt);
                 if (nzt <= RK_SPARSE_MAX_WORDS) {
                     sparse = true;
-                    uint2* dsp = reinterpret_cast<uint2*>(dst);
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
                         const int c = threadIdx.x * CPT + q;
                         if (c < g.ncell) {
-                            uint32_t sw = summ[c];
-                            while (sw) {
-                                const int w = c * 32 + __ffs(sw) - 1;
-                                sw &= sw - 1;
-                                dsp[zex++] = make_uint2(bits[w], (uint32_t(w) << 18) | uint32_t(cellbase[c] + wpre[w]));
-                            }
+                            s_zb[c] = zex;
+                            zex += __popc(summ[c]);
                         }
+                    }
+                    __syncthreads();
+                    // a warp per cell, a lane per word: the non-zero words in order
+                    uint2* dsp = reinterpret_cast<uint2*>(dst);
+                    for (int c = wid; c < g.ncell; c += NT / 32) {
+                        const uint32_t sw = summ[c];
+                        if (!sw) continue;
+                        const uint32_t b = bits[c * 32 + lane];
+                        const int ex = warp_exclusive_sum(__popc(b), lane);
+                        if (b)
+                            dsp[s_zb[c] + __popc(sw & ((1u << lane) - 1u))] =
+                                make_uint2(b, (uint32_t(c * 32 + lane) << 18) | uint32_t(cellbase[c] + ex));
                     }
                     if (threadIdx.x == 0) rec_meta[gi] = make_int2(nzt, tot);
                 }
             }
             if (!sparse) {
                 // the dense record, in the numeric kernel's layout: (bits, rank of the
-                // word) pairs, the summary and the cell prefix
-                uint4* dwb = reinterpret_cast<uint4*>(dst + LR.wb);
-                for (int q = threadIdx.x; q < NWmax / 2; q += NT) {
-                    const int w = 2 * q;
-                    const uint32_t b0 = bits[w], b1 = bits[w + 1];
-                    const int c = w >> 5;  // w and w + 1 share a cell
-                    dwb[q] = make_uint4(b0, b0 ? uint32_t(cellbase[c] + wpre[w]) : 0u, b1,
-                                        b1 ? uint32_t(cellbase[c] + wpre[w + 1]) : 0u);
+                // word) pairs, the summary and the cell prefix; a warp per cell
+                uint2* dwb = reinterpret_cast<uint2*>(dst + LR.wb);
+                for (int c = wid; c < ncell_max; c += NT / 32) {
+                    const int w = c * 32 + lane;
+                    const uint32_t b = bits[w];
+                    const int ex = warp_exclusive_sum(__popc(b), lane);
+                    dwb[w] = make_uint2(b, b ? uint32_t(cellbase[c] + ex) : 0u);
                 }
                 uint32_t* dsumm = reinterpret_cast<uint32_t*>(dst + LR.summ);
                 for (int c = threadIdx.x; c < ncell_max; c += NT) dsumm[c] = summ[c];
@@ -2275,7 +2291,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         stc_count(h);
         {
             const size_t smem = sym_layout(ncell_max).total;
-            auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+            auto kern = k_symbolic_rank<RK_SYM_NT, RK_SYM_MINB>;
             STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
             int per_sm = 0;
             STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
@@ -2299,7 +2315,7 @@ stc_status spgemm_rank_impl(stc_handle* h, int alg, int nb, const SpgArgs* args_
         stc_count(h);
     } else if (NR > 0) {
         const size_t smem = sym_layout(ncell_max).total;
-        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        auto kern = k_symbolic_rank<RK_SYM_NT, RK_SYM_MINB>;
         STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         int per_sm = 0;
         STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
@@ -2818,7 +2834,7 @@ stc_status row_counts_impl(stc_handle* h, const stc_csr* A, const stc_csr* B, in
         STC_LAUNCH_CHECK();
         stc_count(h, 3);
         const size_t smem = sym_layout(ncell).total;
-        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        auto kern = k_symbolic_rank<RK_SYM_NT, RK_SYM_MINB>;
         int per_sm = 0;
         STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
@@ -2917,7 +2933,7 @@ stc_status spgemm_slab_impl(stc_handle* h, int alg, const stc_csr* A, const stc_
             if (!recs[t] || !metas[t]) return fail(STC_ERR_OOM);
         }
         const size_t smem = sym_layout(ncells[t]).total;
-        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        auto kern = k_symbolic_rank<RK_SYM_NT, RK_SYM_MINB>;
         int per_sm = 0;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem) != cudaSuccess || per_sm < 1)
@@ -3567,7 +3583,7 @@ stc_status spgemm_masked_impl(stc_handle* h, int alg, const stc_csr* A, const st
     RM.nb = 1;
     {
         const size_t smem = sym_layout(ncell_max).total;
-        auto kern = k_symbolic_rank<RK_SYM_NT, 4>;
+        auto kern = k_symbolic_rank<RK_SYM_NT, RK_SYM_MINB>;
         STC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         int per_sm = 0;
         STC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RK_SYM_NT, smem));
