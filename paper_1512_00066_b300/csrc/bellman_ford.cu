@@ -23,6 +23,7 @@
 namespace {
 
 constexpr int BF_NT = 512;
+constexpr int BF_U = 4;  // out-edges per lane whose atomic minima are in flight together
 constexpr long long BARRIER_SPIN_LIMIT = 1ll << 22;  // iterations of ~0.5 us each (~2 s)
 
 template <int ALG> struct BfT;
@@ -89,14 +90,30 @@ __device__ __forceinline__ void relax_round(const BfArgs& a, typename BfT<ALG>::
         row_range(a.ptr, u, a.nnz, lo, hi);
         nrelax += (unsigned long long)(hi - lo);
         typename T::D du = *(volatile typename T::D*)&dist[u];
-        for (int64_t p = lo + lane; p < hi; p += 32) {
-            int32_t v = a.col[p];
-            if ((uint64_t)v >= (uint64_t)a.n) continue;
-            typename T::D cand = T::relax(du, W[p]);
-            typename T::D old = T::amin(&dist[v], cand);
-            if (T::less(cand, old)) {
-                if (atomicExch(&a.stamp[v], r) != r) next[atomicAdd(cnt_next, 1)] = v;
+        // BF_U edges a lane at a time, their atomics issued together (a hub's row
+        // is long and sets the round's length)
+        for (int64_t p0 = lo + lane; p0 < hi; p0 += 32 * BF_U) {
+            int32_t v[BF_U];
+            typename T::D cand[BF_U], old[BF_U];
+#pragma unroll
+            for (int k = 0; k < BF_U; ++k) {
+                const int64_t p = p0 + 32 * k;
+                v[k] = -1;
+                if (p < hi) {
+                    const int32_t x = a.col[p];
+                    if ((uint64_t)x < (uint64_t)a.n) {
+                        v[k] = x;
+                        cand[k] = T::relax(du, W[p]);
+                    }
+                }
             }
+#pragma unroll
+            for (int k = 0; k < BF_U; ++k)
+                if (v[k] >= 0) old[k] = T::amin(&dist[v[k]], cand[k]);
+#pragma unroll
+            for (int k = 0; k < BF_U; ++k)
+                if (v[k] >= 0 && T::less(cand[k], old[k]) && atomicExch(&a.stamp[v[k]], r) != r)
+                    next[atomicAdd(cnt_next, 1)] = v[k];
         }
     }
     if (lane == 0 && nrelax) atomicAdd(a.relax, nrelax);
