@@ -23,7 +23,7 @@
 namespace {
 
 constexpr int BF_NT = 512;
-constexpr int BF_U = 4;  // out-edges per lane whose atomic minima are in flight together
+constexpr int BF_U = 8;  // out-edges per lane whose atomic minima are in flight together
 constexpr long long BARRIER_SPIN_LIMIT = 1ll << 22;  // iterations of ~0.5 us each (~2 s)
 
 template <int ALG> struct BfT;
