@@ -767,6 +767,8 @@ __global__ void k_mu_seed(MfGraph g, MfState st, MuState u, const int32_t* __res
     }
 }
 
+constexpr int MU_PUSH_UNR = 2;
+
 // One round: warp per item of the frontier, lane per out-edge.
 __global__ void __launch_bounds__(256) k_mu_push(MfGraph g, MfState st, MuState u) {
     const int S = st.S;
@@ -782,25 +784,41 @@ __global__ void __launch_bounds__(256) k_mu_push(MfGraph g, MfState st, MuState 
         uint32_t F[MU_W];
         mu_load_mask(u.fm, x, F);
         const double* __restrict__ sx = st.sig + int64_t(x) * S;
-        for (int64_t p = e0 + lane; p < e1; p += 32) {
-            const int32_t v = g.col[p];
-            if ((uint64_t)v >= (uint64_t)g.n) continue;
-            uint32_t V[MU_W];
-            mu_load_mask(u.vis, v, V);
-            bool any = false;
+        // MU_PUSH_UNR of a lane's edges at a time: their targets' masks are loaded
+        // together before any is used
+        for (int64_t p0 = e0 + lane; p0 < e1; p0 += 32 * MU_PUSH_UNR) {
+            int32_t v[MU_PUSH_UNR];
+            uint32_t V[MU_PUSH_UNR][MU_W];
 #pragma unroll
-            for (int k = 0; k < MU_W; ++k) {
-                uint32_t c = F[k] & ~V[k];
-                if (!c) continue;
-                any = true;
-                atomicOr(&u.nxt[int64_t(v) * MU_W + k], c);
-                while (c) {
-                    const int s = k * 32 + __ffs(c) - 1;
-                    c &= c - 1;
-                    atomicAdd(&st.dln[int64_t(v) * S + s], sx[s]);
+            for (int j = 0; j < MU_PUSH_UNR; ++j) {
+                const int64_t p = p0 + 32 * j;
+                v[j] = -1;
+                if (p < e1) {
+                    const int32_t y = g.col[p];
+                    if ((uint64_t)y < (uint64_t)g.n) v[j] = y;
                 }
             }
-            if (any) mf_touch(st.stamp, st.list[1], &st.cnt[MF_C_TOUCHED], v, r);
+#pragma unroll
+            for (int j = 0; j < MU_PUSH_UNR; ++j)
+                if (v[j] >= 0) mu_load_mask(u.vis, v[j], V[j]);
+#pragma unroll
+            for (int j = 0; j < MU_PUSH_UNR; ++j) {
+                if (v[j] < 0) continue;
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < MU_W; ++k) {
+                    uint32_t c = F[k] & ~V[j][k];
+                    if (!c) continue;
+                    any = true;
+                    atomicOr(&u.nxt[int64_t(v[j]) * MU_W + k], c);
+                    while (c) {
+                        const int s = k * 32 + __ffs(c) - 1;
+                        c &= c - 1;
+                        atomicAdd(&st.dln[int64_t(v[j]) * S + s], sx[s]);
+                    }
+                }
+                if (any) mf_touch(st.stamp, st.list[1], &st.cnt[MF_C_TOUCHED], v[j], r);
+            }
         }
     }
 }
