@@ -1061,21 +1061,24 @@ __global__ void k_cell_offsets(SpgRows R) {
     const SpgArgs g = R.table ? R.table[blockIdx.y] : R.one;
     int32_t* ctab = const_cast<int32_t*>(g.ctab);
     if (!ctab) return;
+    // a warp per row of B, lanes over the cells (coalesced writes); each lane's
+    // binary search reads the row's columns, which stay in L1 across the lanes
+    const int lane = threadIdx.x & 31;
     const int64_t stride = int64_t(g.ncell) + 1;
-    const int64_t total = g.K * stride;
-    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t k = idx / stride;
-        const int64_t c = idx - k * stride;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; k < g.K; k += nwarps) {
         int64_t lo, hi;
         row_range(g.b_ptr, k, g.nnzB, lo, hi);
-        const int64_t target = c << RK_CELL_SHIFT;
-        int64_t a = lo, b = hi;
-        while (a < b) {
-            const int64_t m = (a + b) >> 1;
-            if (int64_t(g.b_col[m]) < target) a = m + 1; else b = m;
+        int32_t* t = ctab + k * stride;
+        for (int c = lane; c <= g.ncell; c += 32) {
+            const int64_t target = int64_t(c) << RK_CELL_SHIFT;
+            int64_t x = lo, y = hi;
+            while (x < y) {
+                const int64_t m = (x + y) >> 1;
+                if (int64_t(g.b_col[m]) < target) x = m + 1; else y = m;
+            }
+            t[c] = int32_t(x - lo);
         }
-        ctab[idx] = int32_t(a - lo);
     }
 }
 
