@@ -767,7 +767,7 @@ __global__ void k_mu_seed(MfGraph g, MfState st, MuState u, const int32_t* __res
     }
 }
 
-constexpr int MU_PUSH_UNR = 2;
+constexpr int MU_PUSH_UNR = 4;
 
 // One round: warp per item of the frontier, lane per out-edge.
 __global__ void __launch_bounds__(256) k_mu_push(MfGraph g, MfState st, MuState u) {
