@@ -215,6 +215,20 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def aggregate_ranks(ops, seconds, dist=None, device="cpu"):
+    """Whole-job throughput of N replicas: the semiring operations of every rank over
+    the slowest rank's timed span.  Returns (ops/s, max seconds, summed ops); with no
+    process group, this rank's own figures."""
+    if dist is None:
+        return ops / seconds, seconds, ops
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    o = torch.tensor([float(ops)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(o, op=dist.ReduceOp.SUM)
+    return o.item() / t.item(), t.item(), o.item()
+
+
 def run_stc(args):
     import torch
     import paper_1512_00066_b300 as stc
@@ -302,12 +316,7 @@ def run_stc(args):
         barrier()
     launches = H.kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = world * ops_total / t_total
+    value, t_total, _ = aggregate_ranks(ops_total, sum(step_ms) / 1e3, dist, dev)
 
     # roofline of the dominant kernel: the numeric phase of the first SpGEMM of the
     # step.  Algorithmic bytes follow the row-wise (Gustavson) traffic model: read A,
@@ -367,7 +376,7 @@ def run_stc(args):
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32" if wl["scale"] else "int32",
             "data": "synthetic",
